@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the D-iteration hot path on GB300.
+
+One step = one complete solve of X = P X + B (PageRank form, d = 0.85) by the
+threshold-frontier D-iteration, from F = B to the exact FP64 stop
+|B + P H - H|_1 <= 1e-8 |B|_1, on a seeded synthetic web-like graph.
+Metric: edge diffusions per second (the paper's elementary cost unit,
+Sec. 2.5) and time to tolerance.
+
+Default workload: N = 1,000,000 nodes, mean out-degree 10 (non-dangling),
+10% dangling, +-64 locality window, FP32 fluid with FP64 history, exact
+FP64 residual every 8 levels.  Inputs are resident in HBM for the device
+timing; L2 is flushed (256 MiB write) before every timed step.
+
+Arms:
+  --impl native     (default) the CUDA library through its C ABI;
+  --impl reference  the CPU oracle, timed as it stands on the host cores.
+Multi-GPU (torchrun): independent replicas, one solve per rank per step,
+no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+if REPO not in sys.path:
+    sys.path.insert(0, REPO)
+
+from paper_1202_6168_gb300 import graphgen as gg  # noqa: E402
+
+D = 0.85
+WORKLOADS = {
+    "web-1m": (gg.WEB_1M, "web-like N=1e6, m=10, +-64 window, seed 0"),
+    "stress-16m": (gg.STRESS_16M, "web-like N=2^24, m=16, +-256 window, seed 0"),
+    "web-10k": (gg.SMALL_10K, "web-like N=1e4, m=8, +-64 window, seed 0"),
+}
+# algorithmic bytes of the push kernel (per edge / per node diffusion)
+EDGE_BYTES = {"f32": 12, "f64": 20}   # 4 B column index + fluid read + fluid write
+NODE_BYTES = {"f32": 40, "f64": 52}   # row_ptr pair, fluid exchange, FP64 history RMW, frontier, scale
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="web-1m")
+    p.add_argument("--fp64", action="store_true", help="FP64 fluid instead of FP32")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, roofline and CPU baseline legs")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(REPO, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(rp, col, b, tol):
+    """The CPU oracle as it stands, on one host core, one full solve."""
+    from oracle import diter as od
+    t0 = time.perf_counter()
+    r = od.d_iteration(rp, col, b, D, tol=tol)
+    dt = time.perf_counter() - t0
+    return {"value": r.edge_diffusions / dt, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full sequential FP64 solve of the same graph to the same tol "
+                      f"({r.levels} levels, {r.edge_diffusions} edge diffusions, {dt:.2f} s)",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    spec, desc = WORKLOADS[args.workload]
+    rp, col = gg.generate(spec)
+    b = gg.uniform_b(spec.n, D)
+    tol = 1e-8 * b.sum()
+    from oracle import diter as od
+    for _ in range(args.warmup):
+        od.d_iteration(rp, col, b, D, tol=tol)
+    edges, secs = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = od.d_iteration(rp, col, b, D, tol=tol)
+        secs += time.perf_counter() - t0
+        edges += r.edge_diffusions
+    value = edges / secs
+    line = {"impl": "reference", "metric": "edge_diffusions_per_s", "value": value,
+            "unit": "edge_diffusions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": spec.n, "nnz": int(len(col)), "tol": tol,
+                       "oracle": "sequential cyclic-threshold D-iteration, FP64, 1 core"},
+            "cpu_baseline": {"value": value, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the workload"},
+            "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1202_6168_gb300 import binding as di
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec, desc = WORKLOADS[args.workload]
+    rp, col = gg.generate(spec)
+    n, nnz = spec.n, int(len(col))
+    b = gg.uniform_b(n, D)
+    tol = 1e-8 * b.sum()
+    prec = "f64" if args.fp64 else "f32"
+    stream = torch.cuda.current_stream()
+    opts = di.opts_default(fluid_fp64=1 if args.fp64 else 0, stream=stream.cuda_stream)
+
+    g = di.Graph.create(rp, col, stream=stream)
+    B = torch.from_numpy(b).cuda()
+    H = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+
+    for _ in range(max(args.warmup, 0)):
+        di.di_solve(g, B, D, tol, H, None, opts)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    edges = nodes = launches = 0
+    levels = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        _, st = di.di_solve(g, B, D, tol, H, None, opts)
+        ev1[k].record(stream)
+        edges += st.edge_diffusions
+        nodes += st.node_diffusions
+        launches += st.gpu_launches
+        levels.append(st.levels)
+    barrier()
+    clocks = sampler.stop()
+    secs = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) * 1e-3
+    last = st
+
+    if world > 1:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([edges], dtype=torch.float64, device="cuda")
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        secs_max, edges_all = float(t.item()), float(e.item())
+    else:
+        secs_max, edges_all = secs, float(edges)
+    value = edges_all / secs_max
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # roofline of the dominant kernel (the push), from CUDA events around
+        # every push launch of instrumented solves (host-driven levels)
+        topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1)
+        te = tn = 0
+        tpush = tscan = trec = 0.0
+        npush = 0
+        reps = min(3, max(args.steps, 1))
+        for _ in range(reps):
+            flush.zero_()
+            _, ts = di.di_solve(g, B, D, tol, H, None, topt)
+            te += ts.edge_diffusions
+            tn += ts.node_diffusions
+            tpush += ts.push_seconds
+            tscan += ts.scan_seconds
+            trec += ts.recompute_seconds
+            npush += ts.push_launches
+        alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn
+        achieved = alg_bytes / tpush / 1e9
+        peak, peak_src = measured_hbm_peak()
+        traffic = None
+        prof = os.path.join(REPO, "profiles", "push_traffic.json")
+        if os.path.exists(prof):
+            try:
+                with open(prof) as f:
+                    pt = json.load(f)
+                if pt.get("workload") == args.workload and pt.get("precision") == prec:
+                    traffic = pt.get("dram_bytes_per_launch")
+            except (OSError, ValueError):
+                traffic = None
+        extras["roofline"] = {"bound": "hbm", "kernel": f"k_push<{'double' if args.fp64 else 'float'}>",
+                              "achieved": achieved, "peak": peak, "unit": "GB/s",
+                              "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
+                              "traffic": traffic,
+                              "alg_bytes_per_launch": alg_bytes / max(npush, 1),
+                              "avg_launch_us": 1e6 * tpush / max(npush, 1),
+                              "time_share": {"push": tpush, "scan": tscan, "recompute_and_control": trec}}
+        # end to end through the host-buffer entry point: H2D of B, D2H of H
+        Bh = torch.from_numpy(b).pin_memory()
+        Hh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            di.di_solve_host(g, Bh.data_ptr(), D, tol, Hh.data_ptr(), None, opts)
+        torch.cuda.synchronize()
+        e_edges, e_secs = 0, 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, es = di.di_solve_host(g, Bh.data_ptr(), D, tol, Hh.data_ptr(), None, opts)
+            e_secs += time.perf_counter() - t0
+            e_edges += es.edge_diffusions
+        extras["e2e"] = {"value": e_edges / e_secs, "unit": "edge_diffusions/s",
+                         "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                         "ms_per_step": 1e3 * e_secs / args.steps,
+                         "api": "di_solve_host (pinned host B in, H out; graph resident)"}
+        # error of the result against the exact residual bound, and the CPU oracle
+        h = H.cpu().numpy()
+        from oracle import diter as od
+        _, r_cpu = od.residual(rp, col, b, D, h)
+        extras["check"] = {"resid_l1_oracle_fp64": r_cpu, "tol": tol, "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
+                           "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
+        extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol)
+
+    if rank == 0:
+        info = g.info()
+        line = {"metric": "edge_diffusions_per_s", "value": value, "unit": "edge_diffusions/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": prec, "data": "synthetic",
+                "config": {"workload": desc, "n": n, "nnz": nnz, "n_dangling": info["n_dangling"],
+                           "n_hot_targets": info["n_hot"], "d": D, "tol": tol, "tol_rel_b_l1": 1e-8,
+                           "fluid": prec, "history": "f64", "recompute_every": opts.recompute_every,
+                           "alpha": opts.alpha, "l2": "flushed (256 MiB write) before each timed step",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "time_to_tol_ms": 1e3 * secs_max / args.steps,
+                "edge_diffusions_per_step": edges / args.steps,
+                "normalised_iterations": edges / args.steps / nnz,
+                "levels": levels[-1], "recomputes": last.recomputes,
+                "gpu_launches": launches, "clocks": clocks}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_native(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * di.h - C ABI of the GB300 D-iteration library (libdi.so).
+ *
+ * The library solves X = P X + B (Eq. 1) for a sparse contractive P of the
+ * PageRank form P = d Q (Eq. 2), q_kj = 1/#out_j for every edge j -> k and a
+ * zero column for a dangling j (Sec. 2.2), by fluid diffusion (D-iteration,
+ * Eqs. defF/defH): diffusing node i moves its fluid F_i into its history H_i
+ * and adds p_ki F_i to the fluid of every child k.  Nodes are chosen by the
+ * cyclic threshold rule of Sec. 2.4: every node with |F_i| >= T diffuses,
+ * then T <- T / alpha.  H converges to X with |X - H|_1 <= |F|_1 / (1 - d)
+ * (Sec. 2, error bound).
+ *
+ * Conventions
+ *   - Every call returns a di_status; nothing aborts the process.  On an
+ *     error, di_last_error() returns a message for the calling thread.
+ *   - Node ids are int32 (N <= 2^31 - 1); the graph must have fewer than
+ *     2^31 edges.
+ *   - "device pointer" arguments are CUDA global-memory addresses on the
+ *     current device; the caller owns and keeps them alive for the call.
+ *     "host pointer" arguments are ordinary (pageable or pinned) memory.
+ *   - The library owns di_graph objects and everything it allocates for
+ *     them; di_graph_destroy frees it all.
+ *   - All calls are made on the stream in di_opts.stream (or the one passed
+ *     explicitly); NULL means the legacy default stream.  Calls that return
+ *     results in host memory synchronise that stream before returning.
+ *   - A di_graph is not thread-safe: concurrent solves on one graph object
+ *     must be serialised by the caller (its scratch memory is shared).
+ */
+#ifndef DI_H
+#define DI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DI_API __attribute__((visibility("default")))
+#else
+#define DI_API
+#endif
+
+typedef enum {
+    DI_OK = 0,
+    DI_EINVAL = 1,    /* invalid argument (validated before any GPU work) */
+    DI_ENOMEM = 2,    /* device or host allocation failed */
+    DI_ECUDA = 3,     /* a CUDA call failed; di_last_error() names it */
+    DI_ENOCONV = 4,   /* the level cap was reached before |F|_1 <= tol */
+    DI_ETIMEOUT = 5,  /* a bounded device wait gave up (no GPU fault) */
+    DI_ENONFINITE = 6 /* the residual became NaN or Inf (bad B or H0) */
+} di_status;
+
+typedef struct di_graph di_graph;
+
+/* Solver options.  Fill with di_opts_default() and change what you need. */
+typedef struct {
+    double alpha;          /* threshold decay T <- T/alpha, > 1; default 1.5 (Sec. 2.4) */
+    int fluid_fp64;        /* 1: fluid F in FP64; 0: FP32 fluid, FP64 history (default) */
+    int recompute_every;   /* FP32 fluid: exact FP64 residual F = B + P H - H every this
+                              many levels; 0 = only to confirm the stop.  default 8 */
+    int max_levels;        /* level cap -> DI_ENOCONV; default 100000 */
+    int warm_start;        /* 1: H holds H0 on entry and F0 = B + P H0 - H0 */
+    int warm_fallback;     /* with warm_start: fall back to H0 = 0 when |F0|_1 > |B|_1 */
+    int l2_window;         /* 1: keep the fluid vector L2-resident (access-policy window) */
+    int timing;            /* 1: run the levels host-driven with a CUDA event around every
+                              kernel and fill the per-kernel times of di_stats (slower) */
+    long long spin_limit;  /* iteration limit of every bounded device wait */
+    void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
+} di_opts;
+
+/* Statistics of one solve. */
+typedef struct {
+    int32_t levels;            /* threshold levels with a non-empty frontier */
+    int32_t recomputes;        /* exact FP64 residual recomputations */
+    int64_t node_diffusions;   /* nodes diffused (F_i moved into H_i) */
+    int64_t edge_diffusions;   /* elementary node-to-node diffusions (Sec. 2.5 cost) */
+    double resid_l1;           /* final |B + P H - H|_1, recomputed exactly in FP64 */
+    double err_bound;          /* resid_l1 / (1 - d): bound on |X - H|_1 */
+    double b_l1;               /* |B|_1 */
+    double f0_l1;              /* |F0|_1 of the start actually used */
+    double seconds;            /* device time of the solve (CUDA events) */
+    int32_t warm_used;         /* 1 if the warm start was kept, 0 if plain/fallback */
+    int32_t status;            /* the di_status the call returned */
+    int64_t gpu_launches;      /* kernels this call launched */
+    /* per-kernel CUDA-event times, filled only when opts.timing = 1 */
+    double scan_seconds, push_seconds, recompute_seconds;
+    int32_t scan_launches, push_launches, recompute_launches, body_iterations;
+} di_stats;
+
+/* Library version string. */
+DI_API const char *di_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+DI_API const char *di_last_error(void);
+
+/* Defaults: alpha 1.5, FP32 fluid, recompute_every 8, max_levels 100000,
+ * cold start (fallback on when warm), L2 window on, timing off,
+ * spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+DI_API di_status di_opts_default(di_opts *o);
+
+/*
+ * Builds the device form of P's sparsity from a CSR of out-edges (Sec. 2.2):
+ * row j of (row_ptr, col) lists the targets k of the edges j -> k, i.e. the
+ * support of column j of P.  Duplicates count with their multiplicity and a
+ * self-loop j -> j is the entry p_jj; a row with no entry is a dangling node
+ * (zero column).  n >= 1 nodes, nnz >= 0 edges; row_ptr has n+1 entries
+ * (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz), col has nnz entries in
+ * [0, n).  on_device = 0: row_ptr/col are host pointers; 1: device pointers.
+ * The arrays are copied; the caller keeps ownership.  Validation failures
+ * return DI_EINVAL (nothing allocated).  The library also derives the
+ * transpose (in-edges) used by the exact residual and the node features.
+ * stream: cudaStream_t or NULL.  *out receives the new graph.
+ */
+DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr,
+                                 const int32_t *col, int on_device, void *stream,
+                                 di_graph **out);
+
+/* Frees a graph and all its device memory (NULL is a no-op). */
+DI_API void di_graph_destroy(di_graph *g);
+
+/* Shape of a graph; any output pointer may be NULL. */
+DI_API di_status di_graph_info(const di_graph *g, int64_t *n, int64_t *nnz,
+                               int64_t *n_dangling, int64_t *max_outdeg, int64_t *max_indeg,
+                               int64_t *n_hot);
+
+/*
+ * Solves X = P X + B by D-iteration on one GPU until the exactly recomputed
+ * residual satisfies |B + P H - H|_1 <= tol (the paper's stop rule
+ * r/(1-d) <= Target_Error of Sec. 2.1 is tol = (1-d) Target_Error).
+ *   B  device pointer, n doubles, finite (non-finite -> DI_ENONFINITE).
+ *   d  damping factor in (0, 1) (P = d Q, Eq. 2).
+ *   tol > 0, absolute L1 tolerance.
+ *   H  device pointer, n doubles: in = H0 when opts->warm_start, out = H ~ X.
+ *   F  device pointer, n doubles, or NULL: out = B + P H - H in FP64.
+ *   opts NULL = defaults.  stats may be NULL.
+ * Synchronous: returns after the solve completed on opts->stream.
+ * Returns DI_OK, DI_ENOCONV (level cap; H and stats still valid),
+ * DI_ENONFINITE, DI_EINVAL, DI_ENOMEM or DI_ECUDA.
+ */
+DI_API di_status di_solve(di_graph *g, const double *B, double d, double tol, double *H,
+                          double *F, const di_opts *opts, di_stats *stats);
+
+/*
+ * di_solve with HOST buffers: copies B (and H0 when warm) to the device,
+ * solves, and copies H (and F when non-NULL) back.  B, H, F are host
+ * pointers of n doubles.  Uses library-owned device buffers.
+ */
+DI_API di_status di_solve_host(di_graph *g, const double *B, double d, double tol, double *H,
+                               double *F, const di_opts *opts, di_stats *stats);
+
+/*
+ * Exact residual (the invariant F_n = B + P H_n - H_n that Eqs. defF/defH
+ * imply): F = B + P H - H in FP64 for device vectors B, H (n doubles) into
+ * the device vector F (n doubles); *r_l1 (host, may be NULL) receives
+ * |F|_1.  Gathers over in-edges, no atomics.  Synchronous when r_l1 != NULL.
+ */
+DI_API di_status di_residual(di_graph *g, const double *B, double d, const double *H,
+                             double *F, double *r_l1, void *stream);
+
+/*
+ * Frontier selection of one threshold level (Sec. 2.4): writes to the
+ * device array list (capacity n) the ids of all nodes with |F_i| >= T, in
+ * no guaranteed order, and returns through host pointers the count, the
+ * L1 norm sum |F_i| and max |F_i|.  F is a device vector of n floats
+ * (fluid_fp64 = 0) or doubles (fluid_fp64 = 1).  The comparison is made in
+ * the fluid's precision.  Synchronous.
+ */
+DI_API di_status di_frontier(di_graph *g, const void *F, int fluid_fp64, double T,
+                             int32_t *list, int64_t *count, double *r_l1, double *max_abs,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DI_H */

@@ -34,8 +34,6 @@ CU_SOURCES = [
     "graph.cu",
     "solve.cu",
     "residual.cu",
-    "batched.cu",
-    "warmstart.cu",
 ]
 
 

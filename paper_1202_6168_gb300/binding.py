@@ -1,0 +1,198 @@
+"""Thin ctypes binding of the C ABI in ``include/di.h`` (libdi.so).
+
+Argument marshalling only: every step of the D-iteration runs in the CUDA
+library.  There is no CPU fallback; if ``libdi.so`` has not been built the
+first call raises.  Device buffers are passed as raw pointers (for example
+``tensor.data_ptr()`` of a CUDA ``torch.Tensor``); streams as the
+``cudaStream_t`` value (``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+c_i32, c_i64, c_dbl, c_int, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+
+DI_OK, DI_EINVAL, DI_ENOMEM, DI_ECUDA, DI_ENOCONV, DI_ETIMEOUT, DI_ENONFINITE = range(7)
+STATUS_NAMES = {0: "DI_OK", 1: "DI_EINVAL", 2: "DI_ENOMEM", 3: "DI_ECUDA", 4: "DI_ENOCONV",
+                5: "DI_ETIMEOUT", 6: "DI_ENONFINITE"}
+
+
+class di_opts(ctypes.Structure):
+    _fields_ = [("alpha", c_dbl), ("fluid_fp64", c_int), ("recompute_every", c_int),
+                ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
+                ("l2_window", c_int), ("timing", c_int), ("spin_limit", ctypes.c_longlong),
+                ("stream", c_vp)]
+
+
+class di_stats(ctypes.Structure):
+    _fields_ = [("levels", c_i32), ("recomputes", c_i32), ("node_diffusions", c_i64),
+                ("edge_diffusions", c_i64), ("resid_l1", c_dbl), ("err_bound", c_dbl),
+                ("b_l1", c_dbl), ("f0_l1", c_dbl), ("seconds", c_dbl), ("warm_used", c_i32),
+                ("status", c_i32), ("gpu_launches", c_i64), ("scan_seconds", c_dbl),
+                ("push_seconds", c_dbl), ("recompute_seconds", c_dbl), ("scan_launches", c_i32),
+                ("push_launches", c_i32), ("recompute_launches", c_i32), ("body_iterations", c_i32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class DiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+# name -> (restype, argtypes); every function declared in include/di.h
+SIGNATURES = {
+    "di_version": (ctypes.c_char_p, []),
+    "di_last_error": (ctypes.c_char_p, []),
+    "di_opts_default": (c_int, [ctypes.POINTER(di_opts)]),
+    "di_graph_create": (c_int, [c_i64, c_i64, c_vp, c_vp, c_int, c_vp, ctypes.POINTER(c_vp)]),
+    "di_graph_destroy": (None, [c_vp]),
+    "di_graph_info": (c_int, [c_vp] + [ctypes.POINTER(c_i64)] * 6),
+    "di_solve": (c_int, [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts),
+                         ctypes.POINTER(di_stats)]),
+    "di_solve_host": (c_int, [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts),
+                              ctypes.POINTER(di_stats)]),
+    "di_residual": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
+    "di_frontier": (c_int, [c_vp, c_vp, c_int, c_dbl, c_vp, ctypes.POINTER(c_i64),
+                            ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.DI_SO
+
+
+def lib():
+    """The loaded libdi.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdi.so not found at {path}: build it first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            handle = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = handle
+    return _LIB
+
+
+def last_error() -> str:
+    return lib().di_last_error().decode()
+
+
+def check(status: int, allow=(DI_OK,)) -> int:
+    if status not in allow:
+        raise DiError(status, last_error())
+    return status
+
+
+def opts_default(**overrides) -> di_opts:
+    o = di_opts()
+    check(lib().di_opts_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(x) -> int | None:
+    """Raw address of a torch tensor, numpy array, int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Owner of a ``di_graph`` handle (freed by ``close`` or garbage collection)."""
+
+    def __init__(self, handle: int, n: int, nnz: int):
+        self.handle = handle
+        self.n = n
+        self.nnz = nnz
+
+    @classmethod
+    def create(cls, row_ptr, col, on_device: bool = False, stream=None) -> "Graph":
+        n = len(row_ptr) - 1
+        nnz = len(col)
+        h = c_vp()
+        check(lib().di_graph_create(n, nnz, _ptr(row_ptr), _ptr(col) if nnz else None,
+                                    1 if on_device else 0, _stream(stream), ctypes.byref(h)))
+        return cls(h.value, n, nnz)
+
+    def info(self) -> dict:
+        vals = [c_i64() for _ in range(6)]
+        check(lib().di_graph_info(self.handle, *[ctypes.byref(v) for v in vals]))
+        keys = ["n", "nnz", "n_dangling", "max_outdeg", "max_indeg", "n_hot"]
+        return {k: v.value for k, v in zip(keys, vals)}
+
+    def close(self) -> None:
+        if self.handle:
+            lib().di_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def di_solve(graph: Graph, B, d: float, tol: float, H, F=None, opts: di_opts | None = None,
+             allow=(DI_OK,)) -> tuple[int, di_stats]:
+    st = di_stats()
+    rc = lib().di_solve(graph.handle, _ptr(B), d, tol, _ptr(H), _ptr(F),
+                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    check(rc, allow)
+    return rc, st
+
+
+def di_solve_host(graph: Graph, B, d: float, tol: float, H, F=None, opts: di_opts | None = None,
+                  allow=(DI_OK,)) -> tuple[int, di_stats]:
+    st = di_stats()
+    rc = lib().di_solve_host(graph.handle, _ptr(B), d, tol, _ptr(H), _ptr(F),
+                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    check(rc, allow)
+    return rc, st
+
+
+def di_residual(graph: Graph, B, d: float, H, F, stream=None) -> float:
+    r = c_dbl()
+    check(lib().di_residual(graph.handle, _ptr(B), d, _ptr(H), _ptr(F), ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def di_frontier(graph: Graph, F, fluid_fp64: bool, T: float, out_list, stream=None) -> tuple[int, float, float]:
+    cnt, r, mx = c_i64(), c_dbl(), c_dbl()
+    check(lib().di_frontier(graph.handle, _ptr(F), 1 if fluid_fp64 else 0, T, _ptr(out_list),
+                            ctypes.byref(cnt), ctypes.byref(r), ctypes.byref(mx), _stream(stream)))
+    return cnt.value, r.value, mx.value
+
+
+def version() -> str:
+    return lib().di_version().decode()

@@ -1,0 +1,232 @@
+// di_internal.cuh - internal types and helpers of libdi.so (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "di.h"
+
+namespace di {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define DI_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::di::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),    \
+                            __FILE__, __LINE__);                                       \
+            return e_ == cudaErrorMemoryAllocation ? DI_ENOMEM : DI_ECUDA;             \
+        }                                                                              \
+    } while (0)
+
+#define DI_TRY(expr)                                                                   \
+    do {                                                                               \
+        di_status s_ = (expr);                                                         \
+        if (s_ != DI_OK) return s_;                                                    \
+    } while (0)
+
+// ------------------------------------------------------------------ tuning constants
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;                                // per thread per chunk
+constexpr int kScanChunk = kScanThreads * kScanItems;       // nodes per block iteration
+constexpr int kPushThreads = 256;                            // = frontier tile size
+constexpr int kThreadMaxDeg = 16;   // out-degree <= this: one thread pushes the row
+constexpr int kWarpMaxDeg = 512;    // <= this: one warp; above: the whole CTA
+constexpr int kResThreads = 256;
+constexpr int kResSeg = 8192;       // in-rows longer than this are split in segments
+constexpr int kMaxHot = 2048;       // privatised hot targets (shared-memory slots)
+constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
+
+// ------------------------------------------------------------------ solver state
+
+// Everything a level kernel needs beyond its fixed graph arrays: written by
+// the host before each solve (pointers change from call to call, the
+// instantiated CUDA graph does not).
+struct SolveDesc {
+    const double *B;
+    double *H;
+    double *F_out;        // optional FP64 residual output
+    void *F;              // internal fluid (float or double)
+    double d, tol, alpha;
+    int max_levels;
+    int recompute_every;  // FP32 fluid: exact recompute period (levels)
+    int fluid_fp64;
+    int max_body_iters;   // absolute cap on loop iterations (safety net)
+};
+
+// Device-resident level-loop state (one per graph object).
+struct SolveState {
+    double T;             // threshold of the next scan
+    double r_scan;        // sum |F| seen by the last scan
+    double max_scan;      // max |F| seen by the last scan
+    double r_exact;       // last exact FP64 residual
+    double max_exact;
+    double b_l1;          // |B|_1
+    double f0_l1;         // |F_0|_1 of the start in use
+    unsigned long long node_diff, edge_diff;
+    int level;            // levels with a non-empty push
+    int since_recompute;  // levels since the last exact recompute
+    int recomputes;
+    int nfront;           // frontier size written by the scan (reset by its control)
+    int push_count;       // frontier size to push this level (0 = no push)
+    int do_recompute;     // exact recompute at the end of this level
+    int confirming;       // the recompute confirms a stop request
+    int force_push;       // a stop request was refuted: push at least once
+    int done;             // 0 running, 1 converged, 2 level cap, 3 non-finite
+    int body_iters;
+    unsigned int tile_ctr;      // dynamic tile scheduling of the push
+    unsigned int scan_blocks;   // last-block counters
+    unsigned int res_blocks;
+    unsigned int init_blocks;
+    int pad;
+};
+
+enum ResMode : int {
+    RES_STANDALONE = 0,   // di_residual: FP64 F out, sum
+    RES_LEVEL = 1,        // inside the level loop: only when do_recompute; control
+    RES_WARM_INIT = 2,    // warm start: F0 = B + P H0 - H0 into the fluid, T0 = max
+    RES_FINAL = 3         // after the loop: refresh F_out and r_exact
+};
+
+struct SolverGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle h_while = 0, h_if = 0;
+    bool built = false;
+};
+
+struct Workspace {
+    bool ready = false;
+    float *F32 = nullptr;
+    double *F64 = nullptr;
+    int32_t *front = nullptr;      // frontier list [n]
+    double *g = nullptr;           // s_j H_j for the exact residual [n]
+    double *seg_part = nullptr;    // per-segment partial sums
+    double *part_sum = nullptr;    // per-block partial sums
+    double *part_max = nullptr;
+    SolveDesc *desc = nullptr;     // device
+    SolveState *st = nullptr;      // device
+    SolveDesc *desc_h = nullptr;   // pinned host mirror
+    SolveState *st_h = nullptr;
+    double *hostB = nullptr, *hostH = nullptr, *hostF = nullptr;   // di_solve_host buffers
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t tev[64] = {};       // timing mode: 4 per level, 16 levels per batch
+};
+
+}  // namespace di
+
+struct di_graph {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0, nnz = 0;
+    int64_t n_dangling = 0, max_outdeg = 0, max_indeg = 0;
+    int n_hot = 0;
+    int n_seg = 0;            // segments of the long in-rows
+    int n_long_rows = 0;      // in-rows split in segments
+    int32_t *rp = nullptr;        // out-CSR offsets [n+1]
+    int32_t *pcol = nullptr;      // push targets [nnz]: k, or -1-slot for a hot target
+    int32_t *hot_node = nullptr;  // [n_hot]
+    int32_t *in_rp = nullptr;     // in-CSR offsets [n+1]
+    int32_t *in_col = nullptr;    // in-CSR sources [nnz]
+    int32_t *long_rows = nullptr; // [n_long_rows] ids of split in-rows
+    int32_t *long_seg0 = nullptr; // [n_long_rows + 1] first segment of each
+    int32_t *seg_row = nullptr;   // [n_seg] in-row of each segment (index in long_rows)
+    int64_t *seg_beg = nullptr;   // [n_seg] first in-edge of each segment
+    // d / outdeg, cached for the last damping factor used
+    double scale_d = -1.0;
+    float *s32 = nullptr;
+    double *s64 = nullptr;
+    // grid sizes (persistent kernels)
+    int grid_scan = 0, grid_push = 0, grid_res = 0;
+    di::Workspace ws;
+    di::SolverGraph sg[2];        // [fluid_fp64]
+};
+
+namespace di {
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ void red_add(float *addr, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double *addr, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ float atomic_exch_fluid(float *p, float v) { return atomicExch(p, v); }
+__device__ __forceinline__ double atomic_exch_fluid(double *p, double v) {
+    unsigned long long old = atomicExch(reinterpret_cast<unsigned long long *>(p),
+                                        static_cast<unsigned long long>(__double_as_longlong(v)));
+    return __longlong_as_double(static_cast<long long>(old));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum and max of one double per thread; result valid in thread 0.
+template <int THREADS>
+__device__ __forceinline__ void block_sum_max(double &s, double &m) {
+    __shared__ double ss[THREADS / 32], sm[THREADS / 32];
+    s = warp_sum(s);
+    m = warp_max(m);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { ss[w] = s; sm[w] = m; }
+    __syncthreads();
+    if (w == 0) {
+        s = l < THREADS / 32 ? ss[l] : 0.0;
+        m = l < THREADS / 32 ? sm[l] : 0.0;
+        s = warp_sum(s);
+        m = warp_max(m);
+    }
+    __syncthreads();
+}
+
+// Marks this block done; returns true in every thread of the last block to
+// finish (the one that sees all partials).  counter must start at 0 and is
+// reset to 0 by the last block.
+__device__ __forceinline__ bool last_block(unsigned int *counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int prev = atomicAdd(counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+        if (is_last) *counter = 0;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// ------------------------------------------------------------------ cross-TU entry points
+
+// graph.cu: (re)compute d / outdeg for damping d
+di_status ensure_scale(di_graph *g, double d, cudaStream_t s);
+// solve.cu
+di_status ensure_workspace(di_graph *g);
+// residual.cu: launch the exact-residual kernels (prep, segments, rows)
+void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s);
+int residual_grid(int sms);
+int residual_kernels(const di_graph *g);
+// batched / warm-start modules register nothing here yet
+
+inline cudaStream_t as_stream(void *p) { return reinterpret_cast<cudaStream_t>(p); }
+
+}  // namespace di

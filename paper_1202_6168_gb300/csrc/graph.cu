@@ -1,0 +1,422 @@
+// graph.cu - device form of P (Sec. 2.2): out-CSR for the push, in-CSR
+// (transpose) for the exact residual, d/outdeg scales, hot-target slots.
+#include <algorithm>
+#include <vector>
+
+#include "di_internal.cuh"
+
+namespace di {
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(int64_t items, int per_block, int cap) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return static_cast<int>(b);
+}
+
+// Validation: row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz, col in [0, n).
+__global__ void k_validate(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n,
+                           int64_t nnz, unsigned long long *bad) {
+    unsigned long long b = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (rp[i + 1] < rp[i]) ++b;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rp[0] != 0) ++b;
+        if (rp[n] != nnz) ++b;
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int32_t c = col[e];
+        if (c < 0 || c >= n) ++b;
+    }
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(bad, b);
+}
+
+// int64 offsets -> int32, plus out-degree statistics.
+__global__ void k_offsets32(const int64_t *__restrict__ rp64, int32_t *__restrict__ rp32, int64_t n,
+                            unsigned long long *n_dangling, int *max_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long dang = 0;
+    int mx = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        rp32[i] = static_cast<int32_t>(rp64[i]);
+        if (i < n) {
+            int deg = static_cast<int>(rp64[i + 1] - rp64[i]);
+            if (deg == 0) ++dang;
+            mx = max(mx, deg);
+        }
+    }
+    dang = warp_sum(dang);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) {
+        if (dang) atomicAdd(n_dangling, dang);
+        atomicMax(max_out, mx);
+    }
+}
+
+// In-degree histogram over all edges.
+__global__ void k_indeg(const int32_t *__restrict__ col, int64_t nnz, int32_t *__restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+        atomicAdd(&cnt[col[e]], 1);
+}
+
+__global__ void k_count_ge(const int32_t *__restrict__ cnt, int64_t n, int t, unsigned long long *out,
+                           int *max_in) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    int mx = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int v = cnt[i];
+        if (v >= t) ++c;
+        mx = max(mx, v);
+    }
+    c = warp_sum(c);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd(out, c);
+        if (max_in) atomicMax(max_in, mx);
+    }
+}
+
+// Exclusive scan of int32 counts in chunks: per-chunk sums, host scan of the
+// chunk sums, then a per-chunk scan that adds the chunk offset.
+constexpr int kScanChunkElems = 4096;   // per block: 256 threads x 16
+
+__global__ void k_chunk_sums(const int32_t *__restrict__ cnt, int64_t n, int64_t *__restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanChunkElems;
+    int64_t s = 0;
+    for (int k = threadIdx.x; k < kScanChunkElems; k += blockDim.x) {
+        int64_t i = base + k;
+        if (i < n) s += cnt[i];
+    }
+    s = warp_sum(s);
+    __shared__ int64_t ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_chunk_scan(const int32_t *__restrict__ cnt, int64_t n, const int64_t *__restrict__ offs,
+                             int32_t *__restrict__ out) {
+    // each thread owns 16 consecutive elements of the chunk
+    constexpr int kPer = kScanChunkElems / kThreads;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunkElems + (int64_t)threadIdx.x * kPer;
+    int32_t v[kPer];
+    int64_t local = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        int64_t i = base + k;
+        v[k] = i < n ? cnt[i] : 0;
+        local += v[k];
+    }
+    // exclusive scan of `local` across the block
+    __shared__ int64_t sh[kThreads];
+    sh[threadIdx.x] = local;
+    __syncthreads();
+    for (int o = 1; o < kThreads; o <<= 1) {
+        int64_t add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int64_t run = offs[blockIdx.x] + sh[threadIdx.x] - local;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = static_cast<int32_t>(run);
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kThreads - 1) out[n] = static_cast<int32_t>(run);
+}
+
+// Fill the transpose: edge j -> k becomes in-edge k <- j.  One thread per row.
+__global__ void k_fill_in(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n,
+                          int32_t *__restrict__ cursor, int32_t *__restrict__ in_col) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) {
+            int32_t pos = atomicAdd(&cursor[col[e]], 1);
+            in_col[pos] = static_cast<int32_t>(j);
+        }
+    }
+}
+
+__global__ void k_assign_hot(const int32_t *__restrict__ cnt, int64_t n, int t, int32_t *__restrict__ slot_of,
+                             int32_t *__restrict__ hot_node, int *n_hot) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int s = -1;
+        if (cnt[i] >= t) {
+            s = atomicAdd(n_hot, 1);
+            hot_node[s] = static_cast<int32_t>(i);
+        }
+        slot_of[i] = s;
+    }
+}
+
+__global__ void k_encode_hot(int32_t *__restrict__ pcol, int64_t nnz, const int32_t *__restrict__ slot_of) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int s = slot_of[pcol[e]];
+        if (s >= 0) pcol[e] = -1 - s;
+    }
+}
+
+// d / outdeg (0 for a dangling node) in FP64 and its FP32 rounding.
+__global__ void k_scale(const int32_t *__restrict__ rp, int64_t n, double d, double *__restrict__ s64,
+                        float *__restrict__ s32) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int deg = rp[i + 1] - rp[i];
+        double s = deg > 0 ? d / (double)deg : 0.0;
+        s64[i] = s;
+        s32[i] = (float)s;
+    }
+}
+
+struct DevPtrs {
+    std::vector<void *> p;
+    ~DevPtrs() {
+        for (void *q : p) cudaFree(q);
+    }
+    template <typename T>
+    cudaError_t alloc(T **out, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) p.push_back(q);
+        *out = static_cast<T *>(q);
+        return e;
+    }
+    void release(void *q) {
+        auto it = std::find(p.begin(), p.end(), q);
+        if (it != p.end()) p.erase(it);
+    }
+};
+
+void free_graph(di_graph *g) {
+    if (!g) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != g->device) cudaSetDevice(g->device);
+    for (auto &sg : g->sg) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        if (sg.graph) cudaGraphDestroy(sg.graph);
+    }
+    void *dev[] = {g->rp, g->pcol, g->hot_node, g->in_rp, g->in_col, g->long_rows, g->long_seg0,
+                   g->seg_row, g->seg_beg, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.front, g->ws.g,
+                   g->ws.seg_part, g->ws.part_sum, g->ws.part_max, g->ws.desc, g->ws.st,
+                   g->ws.hostB, g->ws.hostH, g->ws.hostF};
+    for (void *q : dev)
+        if (q) cudaFree(q);
+    if (g->ws.desc_h) cudaFreeHost(g->ws.desc_h);
+    if (g->ws.st_h) cudaFreeHost(g->ws.st_h);
+    if (g->ws.ev0) cudaEventDestroy(g->ws.ev0);
+    if (g->ws.ev1) cudaEventDestroy(g->ws.ev1);
+    for (cudaEvent_t e : g->ws.tev)
+        if (e) cudaEventDestroy(e);
+    if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
+    delete g;
+}
+
+}  // namespace
+
+di_status ensure_scale(di_graph *g, double d, cudaStream_t s) {
+    if (g->s64 && g->scale_d == d) return DI_OK;
+    if (!g->s64) {
+        DI_CUDA_TRY(cudaMalloc(&g->s64, std::max<int64_t>(g->n, 1) * sizeof(double)));
+        DI_CUDA_TRY(cudaMalloc(&g->s32, std::max<int64_t>(g->n, 1) * sizeof(float)));
+    }
+    k_scale<<<grid_for(g->n, kThreads, 4 * g->num_sms * 8), kThreads, 0, s>>>(g->rp, g->n, d, g->s64, g->s32);
+    DI_CUDA_TRY(cudaGetLastError());
+    g->scale_d = d;
+    return DI_OK;
+}
+
+}  // namespace di
+
+using namespace di;
+
+extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                                           int on_device, void *stream, di_graph **out) {
+    clear_error();
+    if (!out) { set_error("di_graph_create: out is NULL"); return DI_EINVAL; }
+    *out = nullptr;
+    if (n < 1 || n > INT32_MAX) { set_error("di_graph_create: n = %lld outside [1, 2^31-1]", (long long)n); return DI_EINVAL; }
+    if (nnz < 0 || nnz > INT32_MAX) { set_error("di_graph_create: nnz = %lld outside [0, 2^31-1]", (long long)nnz); return DI_EINVAL; }
+    if (!row_ptr || (nnz > 0 && !col)) { set_error("di_graph_create: NULL row_ptr or col"); return DI_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+
+    di_graph *g = new (std::nothrow) di_graph();
+    if (!g) { set_error("di_graph_create: host allocation failed"); return DI_ENOMEM; }
+    struct Guard {
+        di_graph *g;
+        bool keep = false;
+        ~Guard() { if (!keep) free_graph(g); }
+    } guard{g};
+
+    DI_CUDA_TRY(cudaGetDevice(&g->device));
+    DI_CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    g->n = n;
+    g->nnz = nnz;
+    const int cap = g->num_sms * 16;
+
+    DevPtrs tmp;
+    int64_t *rp64 = nullptr;
+    unsigned long long *cnt64 = nullptr;   // [0] bad, [1] dangling, [2] count_ge
+    int *ints = nullptr;                   // [0] max_out, [1] max_in, [2] n_hot
+    int32_t *cnt = nullptr, *slot_of = nullptr;
+    DI_CUDA_TRY(tmp.alloc(&rp64, n + 1));
+    DI_CUDA_TRY(tmp.alloc(&cnt64, 4));
+    DI_CUDA_TRY(tmp.alloc(&ints, 4));
+    DI_CUDA_TRY(cudaMalloc(&g->rp, (n + 1) * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(&g->pcol, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(&g->in_rp, (n + 1) * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(&g->in_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DI_CUDA_TRY(cudaMemcpyAsync(rp64, row_ptr, (n + 1) * sizeof(int64_t), kind, s));
+    if (nnz > 0) DI_CUDA_TRY(cudaMemcpyAsync(g->pcol, col, nnz * sizeof(int32_t), kind, s));
+    DI_CUDA_TRY(cudaMemsetAsync(cnt64, 0, 4 * sizeof(unsigned long long), s));
+    DI_CUDA_TRY(cudaMemsetAsync(ints, 0, 4 * sizeof(int), s));
+
+    // 1. validate
+    k_validate<<<grid_for(std::max(n, nnz), kThreads, cap), kThreads, 0, s>>>(rp64, g->pcol, n, nnz, cnt64);
+    unsigned long long bad = 0;
+    DI_CUDA_TRY(cudaMemcpyAsync(&bad, cnt64, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("di_graph_create: %llu violation(s) of the CSR contract (row_ptr[0]=0, non-decreasing, "
+                  "row_ptr[n]=nnz, 0<=col<n)", bad);
+        return DI_EINVAL;
+    }
+    // 2. int32 offsets and out-degree statistics
+    k_offsets32<<<grid_for(n + 1, kThreads, cap), kThreads, 0, s>>>(rp64, g->rp, n, cnt64 + 1, ints);
+    // 3. in-degrees
+    DI_CUDA_TRY(tmp.alloc(&cnt, n));
+    DI_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int32_t), s));
+    if (nnz > 0) k_indeg<<<grid_for(nnz, kThreads, cap), kThreads, 0, s>>>(g->pcol, nnz, cnt);
+    // 4. in-CSR offsets
+    const int nchunks = static_cast<int>((n + kScanChunkElems - 1) / kScanChunkElems);
+    int64_t *chunk = nullptr;
+    DI_CUDA_TRY(tmp.alloc(&chunk, nchunks));
+    k_chunk_sums<<<nchunks, kThreads, 0, s>>>(cnt, n, chunk);
+    std::vector<int64_t> hchunk(nchunks);
+    DI_CUDA_TRY(cudaMemcpyAsync(hchunk.data(), chunk, nchunks * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t run = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        int64_t v = hchunk[c];
+        hchunk[c] = run;
+        run += v;
+    }
+    if (run != nnz) { set_error("di_graph_create: in-degree total %lld != nnz", (long long)run); return DI_ECUDA; }
+    DI_CUDA_TRY(cudaMemcpyAsync(chunk, hchunk.data(), nchunks * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_chunk_scan<<<nchunks, kThreads, 0, s>>>(cnt, n, chunk, g->in_rp);
+    // 5. fill the transpose (cursor = copy of in_rp)
+    int32_t *cursor = nullptr;
+    DI_CUDA_TRY(tmp.alloc(&cursor, n + 1));
+    DI_CUDA_TRY(cudaMemcpyAsync(cursor, g->in_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    k_fill_in<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, g->pcol, n, cursor, g->in_col);
+
+    // 6. hot targets: the smallest threshold t >= kHotMinIndeg with at most
+    //    kMaxHot nodes of in-degree >= t (binary search on t)
+    int lo = kHotMinIndeg, hi = INT32_MAX;
+    auto count_ge = [&](int t, unsigned long long *res, int *mx) -> di_status {
+        DI_CUDA_TRY(cudaMemsetAsync(cnt64 + 2, 0, sizeof(unsigned long long), s));
+        k_count_ge<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(cnt, n, t, cnt64 + 2, mx);
+        DI_CUDA_TRY(cudaMemcpyAsync(res, cnt64 + 2, sizeof(*res), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        return DI_OK;
+    };
+    unsigned long long c_lo = 0;
+    DI_TRY(count_ge(lo, &c_lo, ints + 1));
+    int hstats[3] = {0, 0, 0};
+    unsigned long long hdang = 0;
+    DI_CUDA_TRY(cudaMemcpy(hstats, ints, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    DI_CUDA_TRY(cudaMemcpy(&hdang, cnt64 + 1, sizeof(hdang), cudaMemcpyDeviceToHost));
+    g->max_outdeg = hstats[0];
+    g->max_indeg = hstats[1];
+    g->n_dangling = static_cast<int64_t>(hdang);
+    int t_hot = lo;
+    if (c_lo > (unsigned long long)kMaxHot) {
+        hi = std::max(lo, hstats[1]) + 1;   // count_ge(hi) == 0
+        while (hi - lo > 1) {
+            int mid = lo + (hi - lo) / 2;
+            unsigned long long c = 0;
+            DI_TRY(count_ge(mid, &c, nullptr));
+            if (c > (unsigned long long)kMaxHot) lo = mid; else hi = mid;
+        }
+        t_hot = hi;
+    }
+    DI_CUDA_TRY(cudaMalloc(&g->hot_node, kMaxHot * sizeof(int32_t)));
+    DI_CUDA_TRY(tmp.alloc(&slot_of, n));
+    k_assign_hot<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(cnt, n, t_hot, slot_of, g->hot_node, ints + 2);
+    if (nnz > 0) k_encode_hot<<<grid_for(nnz, kThreads, cap), kThreads, 0, s>>>(g->pcol, nnz, slot_of);
+    int nh = 0;
+    DI_CUDA_TRY(cudaMemcpyAsync(&nh, ints + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    g->n_hot = nh;
+
+    // 7. segments of the long in-rows (exact residual load balance)
+    {
+        std::vector<int32_t> hin(n + 1);
+        // only the long rows matter; copying the offsets once is cheap next to the graph upload
+        DI_CUDA_TRY(cudaMemcpy(hin.data(), g->in_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        std::vector<int32_t> rows, seg0, segrow;
+        std::vector<int64_t> segbeg;
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t len = (int64_t)hin[k + 1] - hin[k];
+            if (len > kResSeg) {
+                seg0.push_back(static_cast<int32_t>(segrow.size()));
+                for (int64_t b = hin[k]; b < hin[k + 1]; b += kResSeg) {
+                    segrow.push_back(static_cast<int32_t>(rows.size()));
+                    segbeg.push_back(b);
+                }
+                rows.push_back(static_cast<int32_t>(k));
+            }
+        }
+        seg0.push_back(static_cast<int32_t>(segrow.size()));
+        g->n_long_rows = static_cast<int>(rows.size());
+        g->n_seg = static_cast<int>(segrow.size());
+        DI_CUDA_TRY(cudaMalloc(&g->long_rows, std::max<size_t>(rows.size(), 1) * sizeof(int32_t)));
+        DI_CUDA_TRY(cudaMalloc(&g->long_seg0, seg0.size() * sizeof(int32_t)));
+        DI_CUDA_TRY(cudaMalloc(&g->seg_row, std::max<size_t>(segrow.size(), 1) * sizeof(int32_t)));
+        DI_CUDA_TRY(cudaMalloc(&g->seg_beg, std::max<size_t>(segbeg.size(), 1) * sizeof(int64_t)));
+        if (!rows.empty()) {
+            DI_CUDA_TRY(cudaMemcpy(g->long_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            DI_CUDA_TRY(cudaMemcpy(g->seg_row, segrow.data(), segrow.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            DI_CUDA_TRY(cudaMemcpy(g->seg_beg, segbeg.data(), segbeg.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        }
+        DI_CUDA_TRY(cudaMemcpy(g->long_seg0, seg0.data(), seg0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    DI_CUDA_TRY(cudaGetLastError());
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    guard.keep = true;
+    *out = g;
+    return DI_OK;
+}
+
+extern "C" DI_API void di_graph_destroy(di_graph *g) { free_graph(g); }
+
+extern "C" DI_API di_status di_graph_info(const di_graph *g, int64_t *n, int64_t *nnz, int64_t *n_dangling,
+                                         int64_t *max_outdeg, int64_t *max_indeg, int64_t *n_hot) {
+    clear_error();
+    if (!g) { set_error("di_graph_info: NULL graph"); return DI_EINVAL; }
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (n_dangling) *n_dangling = g->n_dangling;
+    if (max_outdeg) *max_outdeg = g->max_outdeg;
+    if (max_indeg) *max_indeg = g->max_indeg;
+    if (n_hot) *n_hot = g->n_hot;
+    return DI_OK;
+}

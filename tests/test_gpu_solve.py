@@ -1,0 +1,312 @@
+"""Parity of the CUDA D-iteration (through the C ABI) with the CPU oracle.
+
+Tolerances (written here, derived from the error bound |X - H|_1 <=
+|F|_1 / (1 - d) of Sec. 2):
+  * FP64 fluid: |H - X|_1 <= 1e-11 |X|_1, solving to tol = 1e-11 (1-d) |B|_1
+    (|X|_1 >= |B|_1, so the bound gives 1e-11 |X|_1);
+  * FP32 fluid / FP64 history: |H - X|_1 <= 1e-6 |X|_1 at tol = 1e-8 |B|_1;
+  * the stop: the oracle's FP64 residual |B + P H - H|_1 of the returned H is
+    <= tol and equals the reported residual.
+X is the oracle's D-iteration run to 1e-14 |B|_1, itself pinned to exact and
+dense solves on CPU.  Frontier sets (an integer decision) are compared
+exactly, in the fluid's precision.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import diter as od
+from paper_1202_6168_gb300 import binding as di
+from paper_1202_6168_gb300 import graphgen as gg
+
+from graphs_util import csr_from_edges, random_graph
+
+pytestmark = pytest.mark.gpu
+D = 0.85
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def solve(rp, col, b, tol, fp64=False, h0=None, want_f=True, allow=(di.DI_OK,), **opt):
+    g = di.Graph.create(rp, col)
+    B = dev(b)
+    H = dev(h0) if h0 is not None else torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    F = torch.zeros_like(H) if want_f else None
+    o = di.opts_default(fluid_fp64=1 if fp64 else 0, warm_start=1 if h0 is not None else 0, **opt)
+    rc, st = di.di_solve(g, B, D, tol, H, F, o, allow=allow)
+    torch.cuda.synchronize()
+    out = (H.cpu().numpy(), st, F.cpu().numpy() if want_f else None, rc)
+    g.close()
+    return out
+
+
+def oracle_x(rp, col, b):
+    r = od.d_iteration(rp, col, b, D, tol=1e-14 * max(np.abs(b).sum(), 1e-300))
+    assert r.status == 0
+    return r.H
+
+
+def check_stop(rp, col, b, h, st, tol):
+    """The oracle's FP64 residual of the returned H is within tol, and equals
+    the reported one.  Each F_k = B_k + (P H)_k - H_k cancels terms far larger
+    than F_k, so two FP64 evaluations of |F|_1 (different summation orders)
+    differ by up to ~eps (|B|_1 + 2 |H|_1): that floor is allowed for."""
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    floor = 64 * np.finfo(np.float64).eps * (np.abs(b).sum() + 2 * np.abs(h).sum())
+    assert r_cpu <= tol * (1 + 1e-9) + floor
+    assert abs(st.resid_l1 - r_cpu) <= 1e-9 * max(r_cpu, tol) + floor
+    return f_cpu
+
+
+@pytest.fixture(scope="module")
+def web10k():
+    rp, col = gg.generate(gg.SMALL_10K)
+    b = gg.uniform_b(gg.SMALL_10K.n, D)
+    return rp, col, b, oracle_x(rp, col, b)
+
+
+@pytest.fixture(scope="module")
+def web1m():
+    rp, col = gg.generate(gg.WEB_1M)
+    b = gg.uniform_b(gg.WEB_1M.n, D)
+    return rp, col, b, oracle_x(rp, col, b)
+
+
+# ---------------------------------------------------------------- single kernels
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_frontier_set_is_exact(web10k, fp64):
+    rp, col, _, _ = web10k
+    n = len(rp) - 1
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(n) * np.exp(rng.uniform(-20, 0, n))
+    f = f.astype(np.float64 if fp64 else np.float32)
+    g = di.Graph.create(rp, col)
+    lst = torch.empty(n, dtype=torch.int32, device="cuda")
+    for T in (0.0, 1e-9, np.quantile(np.abs(f), 0.5), float(np.abs(f).max()), 2.0):
+        cnt, r, mx = di.di_frontier(g, dev(f), fp64, float(T), lst)
+        got = np.sort(lst[:cnt].cpu().numpy())
+        if fp64:
+            want = np.nonzero(np.abs(f) >= T)[0]
+        else:   # comparison in FP32: |F_i| >= T  <=>  |F_i| >= T rounded up to a float
+            want = np.nonzero(np.abs(f).astype(np.float64) >= T)[0]
+        np.testing.assert_array_equal(got, want)
+        assert r == pytest.approx(np.abs(f.astype(np.float64)).sum(), rel=1e-5 if not fp64 else 1e-12)
+        assert mx == float(np.abs(f).max())
+    g.close()
+
+
+def test_exact_residual_matches_oracle(web10k):
+    rp, col, b, _ = web10k
+    rng = np.random.default_rng(2)
+    h = rng.standard_normal(len(b)) * 1e-4
+    g = di.Graph.create(rp, col)
+    F = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    r = di.di_residual(g, dev(b), D, dev(h), F)
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    scale = np.abs(h).max()
+    assert np.abs(F.cpu().numpy() - f_cpu).max() <= 1e-14 * scale
+    assert r == pytest.approx(r_cpu, rel=1e-13)
+    g.close()
+
+
+def test_residual_with_long_in_rows():
+    # a star: node 0 receives an edge from every other node (in-degree 19999)
+    n = 20000
+    rp, col = csr_from_edges(n, [(j, 0) for j in range(1, n)] + [(0, 1)])
+    rng = np.random.default_rng(3)
+    h, b = rng.random(n), rng.random(n)
+    g = di.Graph.create(rp, col)
+    assert g.info()["max_indeg"] == n - 1
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = di.di_residual(g, dev(b), D, dev(h), F)
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    np.testing.assert_allclose(F.cpu().numpy(), f_cpu, rtol=1e-13, atol=1e-12)
+    assert r == pytest.approx(r_cpu, rel=1e-13)
+    g.close()
+
+
+# ---------------------------------------------------------------- full solves vs the oracle
+
+def test_fp64_parity_web10k(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-11 * (1 - D) * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, fp64=True)
+    assert np.abs(h - x).sum() <= 1e-11 * np.abs(x).sum()
+    f_cpu = check_stop(rp, col, b, h, st, tol)
+    np.testing.assert_allclose(f, f_cpu, rtol=0, atol=1e-15 * np.abs(x).max())
+    assert st.levels > 10 and st.edge_diffusions > len(col)
+
+
+def test_fp32_parity_web10k(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    assert st.recomputes >= 1
+
+
+def test_config_tolerance_1e10_web10k(web10k):
+    # the small workload's own stop rule: |F|_1 <= 1e-10, FP64
+    rp, col, b, x = web10k
+    h, st, _, _ = solve(rp, col, b, 1e-10, fp64=True, want_f=False)
+    check_stop(rp, col, b, h, st, 1e-10)
+    assert np.abs(h - x).sum() <= st.resid_l1 / (1 - D) * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_parity_web1m(web1m, fp64):
+    rp, col, b, x = web1m
+    tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+    h, st, _, _ = solve(rp, col, b, tol, fp64=fp64, want_f=False)
+    assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+
+
+def test_host_buffer_entry_point_matches(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    g = di.Graph.create(rp, col)
+    H = np.zeros(len(b))
+    F = np.zeros(len(b))
+    rc, st = di.di_solve_host(g, b, D, tol, H, F)
+    assert np.abs(H - x).sum() <= 1e-6 * np.abs(x).sum()
+    f_cpu = check_stop(rp, col, b, H, st, tol)
+    np.testing.assert_allclose(F, f_cpu, rtol=0, atol=1e-13 * np.abs(x).max())
+    g.close()
+
+
+# ---------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("case", ["single", "two_cycle", "all_dangling", "path", "ragged", "selfloop_dups",
+                                  "personalised", "complete"])
+def test_edge_cases(case, fp64):
+    rng = np.random.default_rng(hash(case) % 1000)
+    if case == "single":
+        rp, col = csr_from_edges(1, [])
+        b = np.array([0.15])
+    elif case == "two_cycle":
+        rp, col = csr_from_edges(2, [(0, 1), (1, 0)])
+        b = np.array([0.15, 0.15])
+    elif case == "all_dangling":
+        rp, col = csr_from_edges(5000, [])
+        b = rng.random(5000)
+    elif case == "path":
+        rp, col = csr_from_edges(300, [(k, k + 1) for k in range(299)])
+        b = np.full(300, 0.01)
+    elif case == "ragged":
+        rp, col = gg.generate(gg.GraphSpec(n=2048 * 3 + 1, mean_deg=9, seed=5))
+        b = gg.uniform_b(len(rp) - 1)
+    elif case == "selfloop_dups":
+        rp, col = random_graph(3000, rng, max_deg=40)
+        b = rng.random(3000) * 1e-3
+    elif case == "personalised":
+        rp, col = gg.generate(gg.GraphSpec(n=20000, mean_deg=8, seed=6))
+        b = gg.personalised_b(20000, 123)
+    else:
+        n = 40
+        rp, col = csr_from_edges(n, [(i, j) for i in range(n) for j in range(n) if i != j])
+        b = np.full(n, (1 - D) / n)
+    x = oracle_x(rp, col, b)
+    tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64)
+    assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+
+
+def test_empty_edge_set_and_zero_b():
+    rp, col = csr_from_edges(100, [])
+    h, st, _, rc = solve(rp, col, np.zeros(100), 1e-12)
+    assert rc == di.DI_OK and st.node_diffusions == 0 and np.all(h == 0)
+
+
+def test_hot_targets_are_privatised_and_exact():
+    # every node links to node 0 and to a neighbour: node 0 is a hot target
+    n = 50000
+    edges = [(j, 0) for j in range(1, n)] + [(j, (j + 1) % n) for j in range(n)]
+    rp, col = csr_from_edges(n, edges)
+    b = gg.uniform_b(n)
+    g = di.Graph.create(rp, col)
+    assert g.info()["n_hot"] >= 1
+    g.close()
+    x = oracle_x(rp, col, b)
+    for fp64 in (False, True):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        h, st, _, _ = solve(rp, col, b, tol, fp64=fp64)
+        assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+
+
+# ---------------------------------------------------------------- warm start and statuses
+
+def test_warm_start_at_solution_does_no_work(web10k):
+    rp, col, b, x = web10k
+    h, st, _, _ = solve(rp, col, b, 1e-10 * b.sum(), fp64=True, h0=x)
+    assert st.warm_used == 1 and st.node_diffusions == 0
+    assert st.f0_l1 <= 1e-12
+
+
+def test_warm_start_near_solution_converges(web10k):
+    rp, col, b, x = web10k
+    rng = np.random.default_rng(4)
+    h0 = x * (1 + 0.2 * rng.standard_normal(len(x)))
+    for fp64 in (False, True):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        h, st, _, _ = solve(rp, col, b, tol, fp64=fp64, h0=h0)
+        assert st.warm_used == 1 and st.f0_l1 < st.b_l1
+        assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+        check_stop(rp, col, b, h, st, tol)
+
+
+def test_warm_start_fallback_on_garbage(web10k):
+    rp, col, b, x = web10k
+    h0 = np.full(len(b), 1.0)
+    h, st, _, _ = solve(rp, col, b, 1e-8 * b.sum(), h0=h0)
+    assert st.warm_used == 0 and st.f0_l1 == pytest.approx(st.b_l1)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+
+
+def test_level_cap_reports_no_convergence(web10k):
+    rp, col, b, x = web10k
+    h, st, f, rc = solve(rp, col, b, 1e-12, max_levels=3, allow=(di.DI_ENOCONV,))
+    assert rc == di.DI_ENOCONV and st.levels == 3
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    assert st.resid_l1 == pytest.approx(r_cpu, rel=1e-12)
+    np.testing.assert_allclose(f, f_cpu, rtol=0, atol=1e-15)
+
+
+def test_non_finite_b_is_reported(web10k):
+    rp, col, b, _ = web10k
+    bad = b.copy()
+    bad[17] = np.nan
+    _, _, _, rc = solve(rp, col, bad, 1e-8, allow=(di.DI_ENONFINITE,))
+    assert rc == di.DI_ENONFINITE
+
+
+def test_invalid_inputs_are_rejected():
+    rp, col = csr_from_edges(3, [(0, 1), (1, 2)])
+    with pytest.raises(di.DiError) as e:
+        di.Graph.create(rp, np.array([0, 5], dtype=np.int32))
+    assert e.value.status == di.DI_EINVAL
+    with pytest.raises(di.DiError):
+        di.Graph.create(np.array([0, 2, 1, 2], dtype=np.int64), col)
+    g = di.Graph.create(rp, col)
+    B = dev(np.ones(3))
+    H = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for d, tol in ((1.0, 1e-8), (0.0, 1e-8), (0.85, 0.0), (0.85, -1.0), (0.85, float("nan"))):
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, B, d, tol, H)
+        assert e.value.status == di.DI_EINVAL
+    g.close()
+
+
+def test_device_resident_csr_input(web10k):
+    rp, col, b, x = web10k
+    g = di.Graph.create(dev(rp), dev(col), on_device=True)
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    di.di_solve(g, dev(b), D, 1e-8 * b.sum(), H)
+    assert np.abs(H.cpu().numpy() - x).sum() <= 1e-6 * np.abs(x).sum()
+    g.close()

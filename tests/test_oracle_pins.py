@@ -13,36 +13,9 @@ import pytest
 from oracle import diter as od
 from paper_1202_6168_gb300 import graphgen as gg
 
+from graphs_util import csr_from_edges, random_graph, transpose
+
 D = 0.85
-
-
-def csr_from_edges(n, edges):
-    """CSR of out-edges from a list of (src, dst); keeps duplicates/self-loops."""
-    rows = [[] for _ in range(n)]
-    for s, t in edges:
-        rows[s].append(t)
-    rp = np.zeros(n + 1, dtype=np.int64)
-    col = []
-    for j in range(n):
-        col.extend(rows[j])
-        rp[j + 1] = len(col)
-    return rp, np.array(col, dtype=np.int32)
-
-
-def random_graph(n, rng, p_dangling=0.15, max_deg=6, self_loops=True, dups=True):
-    edges = []
-    for j in range(n):
-        if rng.random() < p_dangling:
-            continue
-        deg = int(rng.integers(1, max_deg + 1))
-        for _ in range(deg):
-            t = int(rng.integers(0, n))
-            if t == j and not self_loops:
-                continue
-            edges.append((j, t))
-            if dups and rng.random() < 0.1:
-                edges.append((j, t))
-    return csr_from_edges(n, edges)
 
 
 def exact_solve(rp, col, b, d=Fraction(17, 20)):
@@ -304,12 +277,8 @@ def test_pin_detects_a_transposed_operand():
     b = rng.random(30) * 0.01
     x = np.linalg.solve(np.eye(30) - od.dense_p(rp, col, D), b)
     # the transposed graph (in-edges taken as out-edges) gives another X
-    src = np.repeat(np.arange(30), np.diff(rp))
-    order = np.argsort(col, kind="stable")
-    rpt = np.zeros(31, dtype=np.int64)
-    np.add.at(rpt, col.astype(np.int64) + 1, 1)
-    rpt = np.cumsum(rpt)
-    wrong = od.d_iteration(rpt, src[order].astype(np.int32), b, D, tol=1e-15)
+    rpt, colt = transpose(rp, col)
+    wrong = od.d_iteration(rpt, colt, b, D, tol=1e-15)
     assert np.abs(wrong.H - x).sum() > 1e-6 * np.abs(x).sum()
 
 
