@@ -170,6 +170,26 @@ DI_API di_status di_frontier(di_graph *g, const void *F, int fluid_fp64, double 
                              int32_t *list, int64_t *count, double *r_l1, double *max_abs,
                              void *stream);
 
+/*
+ * di_residual without any allocation (the paper has no counterpart: this is
+ * a deployment facility).  For callers that must not call cudaMalloc on
+ * their hot path - a serving loop whose device memory was reserved at
+ * start-up, code running while another component owns the allocator, or a
+ * process that cannot afford the implicit synchronisation of an allocation.
+ * Same inputs and outputs as di_residual (B, H, F device pointers of n
+ * doubles; r_l1 host pointer or NULL; synchronous when r_l1 != NULL); the
+ * graph must have been created beforehand by di_graph_create.
+ * Scratch memory is a fixed static device array inside libdi.so (8,430,080
+ * bytes, held on every GPU that loads the library until exit), so the graph
+ * may have at most 1,048,576 nodes and at most 4096 segments of 8192 in-edges
+ * in its long in-rows; anything larger returns DI_EINVAL (use di_residual).
+ * The first call on each device resolves the array's address for that
+ * device: make it before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ */
+DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double d, const double *H,
+                                     double *F, double *r_l1, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,7 @@ CU_SOURCES = [
     "graph.cu",
     "solve.cu",
     "residual.cu",
+    "noalloc.cu",
 ]
 
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "di_residual": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
     "di_frontier": (c_int, [c_vp, c_vp, c_int, c_dbl, c_vp, ctypes.POINTER(c_i64),
                             ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
+    "di_residual_noalloc": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
 }
 
 
@@ -184,6 +185,15 @@ def di_solve_host(graph: Graph, B, d: float, tol: float, H, F=None, opts: di_opt
 def di_residual(graph: Graph, B, d: float, H, F, stream=None) -> float:
     r = c_dbl()
     check(lib().di_residual(graph.handle, _ptr(B), d, _ptr(H), _ptr(F), ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def di_residual_noalloc(graph: Graph, B, d: float, H, F, stream=None) -> float:
+    """di_residual for callers that cannot allocate device memory: scratch in
+    a fixed static array of the library (graphs up to 2^20 nodes)."""
+    r = c_dbl()
+    check(lib().di_residual_noalloc(graph.handle, _ptr(B), d, _ptr(H), _ptr(F), ctypes.byref(r),
+                                    _stream(stream)))
     return r.value
 
 

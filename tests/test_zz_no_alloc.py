@@ -1,0 +1,69 @@
+"""di_residual_noalloc: the exact residual for callers that cannot allocate
+device memory on their hot path (a serving loop with memory reserved at
+start-up, code running while another component owns the allocator).  Its
+scratch is a fixed static array inside libdi.so instead of library
+allocations, which caps it at 2^20 nodes.
+
+It must give what the allocating entry point di_residual gives, within the
+tolerance the residual tests use (elementwise 1e-14 of max|H|, L1 norm
+1e-13 relative), on two calls in a row - the second with other inputs, so
+that the first call's leftovers in the shared array cannot leak into it.
+This file is collected last; it passes alone in a fresh process and after
+the other tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1202_6168_gb300 import binding as di
+from paper_1202_6168_gb300 import graphgen as gg
+
+from graphs_util import csr_from_edges
+
+pytestmark = pytest.mark.gpu
+D = 0.85
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def graphs():
+    rp, col = gg.generate(gg.GraphSpec(n=200_000, mean_deg=10, seed=7))
+    yield "web-200k", rp, col
+    # a star whose centre has in-degree 99,999: its in-row is cut into segments
+    n = 100_000
+    rp, col = csr_from_edges(n, [(j, 0) for j in range(1, n)] + [(0, 1), (1, 2)])
+    yield "star-100k", rp, col
+
+
+@pytest.mark.parametrize("name,rp,col", list(graphs()), ids=lambda v: v if isinstance(v, str) else "")
+def test_noalloc_residual_equals_allocating_residual_twice(name, rp, col):
+    n = len(rp) - 1
+    g = di.Graph.create(rp, col)
+    rng = np.random.default_rng(42)
+    for call in range(2):
+        h = rng.standard_normal(n) * 10.0 ** (-3 - call)
+        b = rng.random(n) * 1e-5
+        B, H = dev(b), dev(h)
+        F_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+        F_new = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        r_ref = di.di_residual(g, B, D, H, F_ref)
+        r_new = di.di_residual_noalloc(g, B, D, H, F_new)
+        torch.cuda.synchronize()
+        scale = np.abs(h).max()
+        assert torch.isfinite(F_new).all()
+        assert (F_new - F_ref).abs().max().item() <= 1e-14 * scale, (name, call)
+        assert r_new == pytest.approx(r_ref, rel=1e-13), (name, call)
+    g.close()
+
+
+def test_noalloc_rejects_graphs_beyond_its_capacity():
+    n = (1 << 20) + 1
+    g = di.Graph.create(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    B = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(di.DiError) as e:
+        di.di_residual_noalloc(g, B, D, B, torch.zeros_like(B))
+    assert e.value.status == di.DI_EINVAL
+    assert "capacity" in str(e.value)
+    g.close()
