@@ -43,9 +43,11 @@ WORKLOADS = {
     "stress-16m": (gg.STRESS_16M, "web-like N=2^24, m=16, +-256 window, seed 0"),
     "web-10k": (gg.SMALL_10K, "web-like N=1e4, m=8, +-64 window, seed 0"),
 }
-# algorithmic bytes of the push kernel (per edge / per node diffusion)
-EDGE_BYTES = {"f32": 12, "f64": 20}   # 4 B column index + fluid read + fluid write
-NODE_BYTES = {"f32": 40, "f64": 52}   # row_ptr pair, fluid exchange, FP64 history RMW, frontier, scale
+# algorithmic bytes of the level kernel: per edge diffusion, per node
+# diffusion, and per node scanned (the fluid read of the selection)
+EDGE_BYTES = {"f32": 12, "f64": 20}   # 4 B column index + target fluid read + write
+NODE_BYTES = {"f32": 36, "f64": 48}   # row_ptr pair, fluid exchange, FP64 history RMW, scale
+SCAN_BYTES = {"f32": 4, "f64": 8}     # fluid read of every node, every level
 
 
 def parse():
@@ -57,6 +59,15 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="web-1m")
     p.add_argument("--fp64", action="store_true", help="FP64 fluid instead of FP32")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, roofline and CPU baseline legs")
+    p.add_argument("--alpha", type=float, default=None, help="threshold decay (library default if unset)")
+    p.add_argument("--recompute-every", type=int, default=None, help="exact FP64 residual period (levels)")
+    p.add_argument("--no-l2-window", action="store_true", help="no L2 access-policy windows")
+    p.add_argument("--propagation", type=int, default=None,
+                   help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push")
+    p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
+    p.add_argument("--host-loop", action="store_true",
+                   help="host-driven levels with per-kernel events (profilers cannot see kernels in "
+                        "graphs with conditional nodes)")
     return p.parse_args()
 
 
@@ -190,7 +201,16 @@ def run_native(args, world, rank, local):
     tol = 1e-8 * b.sum()
     prec = "f64" if args.fp64 else "f32"
     stream = torch.cuda.current_stream()
-    opts = di.opts_default(fluid_fp64=1 if args.fp64 else 0, stream=stream.cuda_stream)
+    opts = di.opts_default(fluid_fp64=1 if args.fp64 else 0, stream=stream.cuda_stream,
+                           timing=1 if args.host_loop else 0, l2_window=0 if args.no_l2_window else 1)
+    if args.alpha is not None:
+        opts.alpha = args.alpha
+    if args.recompute_every is not None:
+        opts.recompute_every = args.recompute_every
+    if args.propagation is not None:
+        opts.propagation = args.propagation
+    if args.push_ratio is not None:
+        opts.push_ratio = args.push_ratio
 
     g = di.Graph.create(rp, col, stream=stream)
     B = torch.from_numpy(b).cuda()
@@ -241,9 +261,12 @@ def run_native(args, world, rank, local):
     if rank == 0 and not args.no_extras:
         # roofline of the dominant kernel (the push), from CUDA events around
         # every push launch of instrumented solves (host-driven levels)
-        topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1)
+        topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
+                               alpha=opts.alpha, recompute_every=opts.recompute_every,
+                               l2_window=opts.l2_window, propagation=opts.propagation,
+                               push_ratio=opts.push_ratio)
         te = tn = 0
-        tpush = tscan = trec = 0.0
+        tpush = trec = 0.0
         npush = 0
         reps = min(3, max(args.steps, 1))
         for _ in range(reps):
@@ -251,11 +274,10 @@ def run_native(args, world, rank, local):
             _, ts = di.di_solve(g, B, D, tol, H, None, topt)
             te += ts.edge_diffusions
             tn += ts.node_diffusions
-            tpush += ts.push_seconds
-            tscan += ts.scan_seconds
+            tpush += ts.level_seconds
             trec += ts.recompute_seconds
-            npush += ts.push_launches
-        alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn
+            npush += ts.level_launches
+        alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
         achieved = alg_bytes / tpush / 1e9
         peak, peak_src = measured_hbm_peak()
         traffic = None
@@ -268,13 +290,14 @@ def run_native(args, world, rank, local):
                     traffic = pt.get("dram_bytes_per_launch")
             except (OSError, ValueError):
                 traffic = None
-        extras["roofline"] = {"bound": "hbm", "kernel": f"k_push<{'double' if args.fp64 else 'float'}>",
+        extras["roofline"] = {"bound": "hbm", "kernel": f"k_level<{'double' if args.fp64 else 'float'}> (scan + push)",
                               "achieved": achieved, "peak": peak, "unit": "GB/s",
                               "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
                               "traffic": traffic,
                               "alg_bytes_per_launch": alg_bytes / max(npush, 1),
                               "avg_launch_us": 1e6 * tpush / max(npush, 1),
-                              "time_share": {"push": tpush, "scan": tscan, "recompute_and_control": trec}}
+                              "seconds": {"level": tpush, "recompute_and_empty_launches": trec},
+                              "measured_by": "CUDA events around every level kernel of host-driven solves"}
         # end to end through the host-buffer entry point: H2D of B, D2H of H
         Bh = torch.from_numpy(b).pin_memory()
         Hh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -311,6 +334,11 @@ def run_native(args, world, rank, local):
                            "n_hot_targets": info["n_hot"], "d": D, "tol": tol, "tol_rel_b_l1": 1e-8,
                            "fluid": prec, "history": "f64", "recompute_every": opts.recompute_every,
                            "alpha": opts.alpha, "l2": "flushed (256 MiB write) before each timed step",
+                           "l2_window": bool(opts.l2_window),
+                           "propagation": ["auto: binned gather / push", "auto: flat gather / push",
+                                           "push only", "asynchronous push"][opts.propagation],
+                           "push_ratio": opts.push_ratio,
+                           "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "time_to_tol_ms": 1e3 * secs_max / args.steps,
                 "edge_diffusions_per_step": edges / args.steps,

@@ -65,6 +65,15 @@ typedef struct {
     int l2_window;         /* 1: keep the fluid vector L2-resident (access-policy window) */
     int timing;            /* 1: run the levels host-driven with a CUDA event around every
                               kernel and fill the per-kernel times of di_stats (slower) */
+    int propagation;       /* how a level diffuses its frontier.  Levels of modes 0-2 drain
+                              the whole frontier first, then send its fluid: 0 gather over
+                              in-edges (binned rows) on dense levels, scatter on sparse
+                              ones; 1 the same with a flat edge-parallel gather; 2 always
+                              scatter.  3 (default): asynchronous push - each frontier node
+                              is drained with an atomic exchange when its row is pushed, so
+                              fluid arriving earlier in the level goes with it */
+    int push_ratio;        /* auto: a level is dense (gather) when its active edges times
+                              push_ratio reach the edge count; default 8 */
     long long spin_limit;  /* iteration limit of every bounded device wait */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
 } di_opts;
@@ -83,9 +92,13 @@ typedef struct {
     int32_t warm_used;         /* 1 if the warm start was kept, 0 if plain/fallback */
     int32_t status;            /* the di_status the call returned */
     int64_t gpu_launches;      /* kernels this call launched */
-    /* per-kernel CUDA-event times, filled only when opts.timing = 1 */
-    double scan_seconds, push_seconds, recompute_seconds;
-    int32_t scan_launches, push_launches, recompute_launches, body_iterations;
+    /* CUDA-event times, filled only when opts.timing = 1 */
+    double level_seconds;      /* level kernels (frontier selection fused with the push) */
+    double recompute_seconds;  /* exact-residual kernels (timing mode launches them each level) */
+    int32_t level_launches;    /* level kernels that did work */
+    int32_t recompute_launches;/* exact residual recomputations */
+    int32_t body_iterations;   /* iterations of the device-side level loop */
+    int32_t reserved;
 } di_stats;
 
 /* Library version string. */
@@ -96,7 +109,7 @@ DI_API const char *di_last_error(void);
 
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 8, max_levels 100000,
  * cold start (fallback on when warm), L2 window on, timing off,
- * spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+ * propagation 3, push_ratio 8, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "DI_OK", 1: "DI_EINVAL", 2: "DI_ENOMEM", 3: "DI_ECUDA", 4: "D
 class di_opts(ctypes.Structure):
     _fields_ = [("alpha", c_dbl), ("fluid_fp64", c_int), ("recompute_every", c_int),
                 ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
-                ("l2_window", c_int), ("timing", c_int), ("spin_limit", ctypes.c_longlong),
+                ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int),
+                ("spin_limit", ctypes.c_longlong),
                 ("stream", c_vp)]
 
 
@@ -32,9 +33,9 @@ class di_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("recomputes", c_i32), ("node_diffusions", c_i64),
                 ("edge_diffusions", c_i64), ("resid_l1", c_dbl), ("err_bound", c_dbl),
                 ("b_l1", c_dbl), ("f0_l1", c_dbl), ("seconds", c_dbl), ("warm_used", c_i32),
-                ("status", c_i32), ("gpu_launches", c_i64), ("scan_seconds", c_dbl),
-                ("push_seconds", c_dbl), ("recompute_seconds", c_dbl), ("scan_launches", c_i32),
-                ("push_launches", c_i32), ("recompute_launches", c_i32), ("body_iterations", c_i32)]
+                ("status", c_i32), ("gpu_launches", c_i64), ("level_seconds", c_dbl),
+                ("recompute_seconds", c_dbl), ("level_launches", c_i32), ("recompute_launches", c_i32),
+                ("body_iterations", c_i32), ("reserved", c_i32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

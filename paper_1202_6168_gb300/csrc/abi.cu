@@ -35,6 +35,9 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->warm_start = 0;
     o->warm_fallback = 1;
     o->l2_window = 1;
+    o->timing = 0;
+    o->propagation = 3;
+    o->push_ratio = 8;
     o->spin_limit = 1LL << 26;
     o->stream = nullptr;
     return DI_OK;

@@ -40,7 +40,8 @@ constexpr int kPushThreads = 256;                            // = frontier tile 
 constexpr int kThreadMaxDeg = 16;   // out-degree <= this: one thread pushes the row
 constexpr int kWarpMaxDeg = 512;    // <= this: one warp; above: the whole CTA
 constexpr int kResThreads = 256;
-constexpr int kResSeg = 8192;       // in-rows longer than this are split in segments
+constexpr int kResSeg = 8192;       // in-rows longer than this are split in segments (allocation-free path)
+constexpr int kResFine = 256;       // segment length of the exact residual's long in-rows
 constexpr int kMaxHot = 2048;       // privatised hot targets (shared-memory slots)
 constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
 
@@ -59,6 +60,8 @@ struct SolveDesc {
     int recompute_every;  // FP32 fluid: exact recompute period (levels)
     int fluid_fp64;
     int max_body_iters;   // absolute cap on loop iterations (safety net)
+    int propagation;      // 0/1 auto (binned/flat gather for dense levels), 2 push only, 3 async push
+    int push_ratio;       // dense when active edges * push_ratio >= edges
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -81,6 +84,14 @@ struct SolveState {
     int force_push;       // a stop request was refuted: push at least once
     int done;             // 0 running, 1 converged, 2 level cap, 3 non-finite
     int body_iters;
+    int nsel;             // nodes selected in this level (all chunks)
+    double est_scale;     // calibration of the scan's residual estimate (0 = 1)
+    double r_confirm;     // estimate that triggered the pending confirmation
+    unsigned int chunk_ctr;     // (unused)
+    unsigned int rctr[64];      // chunk counters of the sparse push, one per node range
+    unsigned long long lvl_nodes, lvl_edges;   // drained this level
+    int p2mode;                 // propagation of this level: 0 none, 1 pull, 2 push
+    unsigned int push_blocks;   // last-block counter of the sparse push
     unsigned int tile_ctr;      // dynamic tile scheduling of the push
     unsigned int scan_blocks;   // last-block counters
     unsigned int res_blocks;
@@ -98,14 +109,18 @@ enum ResMode : int {
 struct SolverGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle h_while = 0, h_if = 0;
+    cudaGraphConditionalHandle h_while = 0, h_if = 0, h_p2 = 0;
     bool built = false;
+    int l2 = 0;           // built with the L2 window
+    int prop = 0;         // built with this propagation option
 };
 
 struct Workspace {
     bool ready = false;
     float *F32 = nullptr;
     double *F64 = nullptr;
+    float *w32 = nullptr;          // drained fluid scaled by d/outdeg, per level
+    double *w64 = nullptr;
     int32_t *front = nullptr;      // frontier list [n]
     double *g = nullptr;           // s_j H_j for the exact residual [n]
     double *seg_part = nullptr;    // per-segment partial sums
@@ -139,14 +154,31 @@ struct di_graph {
     int32_t *long_seg0 = nullptr; // [n_long_rows + 1] first segment of each
     int32_t *seg_row = nullptr;   // [n_seg] in-row of each segment (index in long_rows)
     int64_t *seg_beg = nullptr;   // [n_seg] first in-edge of each segment
+    // the same table with kResFine-edge segments (exact residual of the solver)
+    int n_fseg = 0, n_frows = 0;
+    int32_t *frows = nullptr, *fseg0 = nullptr, *fseg_row = nullptr;
+    int64_t *fseg_beg = nullptr;
+    // binned pull plan over the in-edges (pull.cuh): device arrays and offsets
+    int32_t *pl_rows = nullptr, *pl_seg_row = nullptr, *pl_seg_beg = nullptr;
+    int32_t *pl_b12_off = nullptr, *pl_b12_col = nullptr;   // bins 1-2 edges in bin order
+    int32_t *outdeg = nullptr;                            // [n] out-degrees
+    int32_t *erow = nullptr;                              // [nnz] destination row of each in-edge
+    int32_t *pl_lrows = nullptr, *pl_lseg0 = nullptr;   // rows of bin 5 and their first segment
+    int pl_nlrows = 0;
+    int64_t pl_bin_off[5] = {0, 0, 0, 0, 0};
+    int64_t pl_task_off[6] = {0, 0, 0, 0, 0, 0};
     // d / outdeg, cached for the last damping factor used
     double scale_d = -1.0;
     float *s32 = nullptr;
     double *s64 = nullptr;
     // grid sizes (persistent kernels)
-    int grid_scan = 0, grid_push = 0, grid_res = 0;
+    int grid_scan = 0, grid_push = 0, grid_res = 0, grid_level = 0;
+    int grid_select = 0, grid_pull = 0, grid_pushw = 0, grid_flat = 0;
+    int level_items = 8;          // nodes per thread per chunk of the fused level kernel
     di::Workspace ws;
     di::SolverGraph sg[2];        // [fluid_fp64]
+    cudaAccessPolicyWindow win[4] = {};   // L2 windows: [2 * (0: F, 1: w) + fluid_fp64]
+    int win_ready[4] = {0, 0, 0, 0}, win_ok[4] = {0, 0, 0, 0};
 };
 
 namespace di {
@@ -225,6 +257,7 @@ di_status ensure_workspace(di_graph *g);
 void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s);
 int residual_grid(int sms);
 int residual_kernels(const di_graph *g);
+int residual_partials(const di_graph *g);
 // batched / warm-start modules register nothing here yet
 
 inline cudaStream_t as_stream(void *p) { return reinterpret_cast<cudaStream_t>(p); }

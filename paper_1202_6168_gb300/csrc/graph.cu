@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "di_internal.cuh"
+#include "pull.cuh"
 
 namespace di {
 namespace {
@@ -172,6 +173,29 @@ __global__ void k_encode_hot(int32_t *__restrict__ pcol, int64_t nnz, const int3
     }
 }
 
+// Contiguous copy of the in-edges of the rows of bins 1-2, in bin order.
+__global__ void k_copy_rows(const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ in_rp,
+                            const int32_t *__restrict__ in_col, const int32_t *__restrict__ off,
+                            int32_t *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += stride) {
+        const int32_t r = rows[i], b = in_rp[r], e = in_rp[r + 1], o = off[i];
+        for (int32_t q = b; q < e; ++q) out[o + (q - b)] = in_col[q];
+    }
+}
+
+// Destination row of every in-edge (the flat gather's run keys).
+__global__ void k_erow(const int32_t *__restrict__ in_rp, int64_t n, int32_t *__restrict__ erow) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        for (int32_t q = in_rp[k]; q < in_rp[k + 1]; ++q) erow[q] = (int32_t)k;
+}
+
+__global__ void k_outdeg(const int32_t *__restrict__ rp, int64_t n, int32_t *__restrict__ deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) deg[i] = rp[i + 1] - rp[i];
+}
+
 // d / outdeg (0 for a dangling node) in FP64 and its FP32 rounding.
 __global__ void k_scale(const int32_t *__restrict__ rp, int64_t n, double d, double *__restrict__ s64,
                         float *__restrict__ s32) {
@@ -213,7 +237,9 @@ void free_graph(di_graph *g) {
         if (sg.graph) cudaGraphDestroy(sg.graph);
     }
     void *dev[] = {g->rp, g->pcol, g->hot_node, g->in_rp, g->in_col, g->long_rows, g->long_seg0,
-                   g->seg_row, g->seg_beg, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.front, g->ws.g,
+                   g->seg_row, g->seg_beg, g->frows, g->fseg0, g->fseg_row, g->fseg_beg,
+                   g->pl_rows, g->pl_seg_row, g->pl_seg_beg, g->pl_lrows, g->pl_lseg0, g->pl_b12_off,
+                   g->pl_b12_col, g->outdeg, g->erow, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.w32, g->ws.w64, g->ws.front, g->ws.g,
                    g->ws.seg_part, g->ws.part_sum, g->ws.part_max, g->ws.desc, g->ws.st,
                    g->ws.hostB, g->ws.hostH, g->ws.hostF};
     for (void *q : dev)
@@ -228,7 +254,116 @@ void free_graph(di_graph *g) {
     delete g;
 }
 
+// Rows of in-degree > seg_len, cut in segments of seg_len in-edges:
+// rows[r] = row id, seg0[r] = first segment of row r (seg0[n_rows] = n_seg),
+// seg_row[s] = r, seg_beg[s] = first in-edge of segment s.
+di_status build_segments(const std::vector<int32_t> &hin, int seg_len, int *n_rows, int *n_seg, int32_t **d_rows,
+                         int32_t **d_seg0, int32_t **d_seg_row, int64_t **d_seg_beg) {
+    const int64_t n = (int64_t)hin.size() - 1;
+    std::vector<int32_t> rows, seg0, segrow;
+    std::vector<int64_t> segbeg;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t len = (int64_t)hin[k + 1] - hin[k];
+        if (len > seg_len) {
+            seg0.push_back(static_cast<int32_t>(segrow.size()));
+            for (int64_t b = hin[k]; b < hin[k + 1]; b += seg_len) {
+                segrow.push_back(static_cast<int32_t>(rows.size()));
+                segbeg.push_back(b);
+            }
+            rows.push_back(static_cast<int32_t>(k));
+        }
+    }
+    seg0.push_back(static_cast<int32_t>(segrow.size()));
+    *n_rows = static_cast<int>(rows.size());
+    *n_seg = static_cast<int>(segrow.size());
+    DI_CUDA_TRY(cudaMalloc(d_rows, std::max<size_t>(rows.size(), 1) * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(d_seg0, seg0.size() * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(d_seg_row, std::max<size_t>(segrow.size(), 1) * sizeof(int32_t)));
+    DI_CUDA_TRY(cudaMalloc(d_seg_beg, std::max<size_t>(segbeg.size(), 1) * sizeof(int64_t)));
+    if (!rows.empty()) {
+        DI_CUDA_TRY(cudaMemcpy(*d_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        DI_CUDA_TRY(cudaMemcpy(*d_seg_row, segrow.data(), segrow.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        DI_CUDA_TRY(cudaMemcpy(*d_seg_beg, segbeg.data(), segbeg.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+    DI_CUDA_TRY(cudaMemcpy(*d_seg0, seg0.data(), seg0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return DI_OK;
+}
+
+// Binned pull plan (pull.cuh) from the host copy of the in-CSR offsets.
+di_status build_pull_plan(di_graph *g, const std::vector<int32_t> &hin) {
+    const int64_t n = (int64_t)hin.size() - 1;
+    std::vector<int32_t> bins[4], segrow, segbeg, lrows, lseg0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t len = (int64_t)hin[k + 1] - hin[k];
+        if (len <= kBin1Max) bins[0].push_back((int32_t)k);
+        else if (len <= kBin2Max) bins[1].push_back((int32_t)k);
+        else if (len <= kBin3Max) bins[2].push_back((int32_t)k);
+        else if (len <= kBin4Max) bins[3].push_back((int32_t)k);
+        else {
+            lseg0.push_back((int32_t)segrow.size());
+            lrows.push_back((int32_t)k);
+            for (int64_t b = hin[k]; b < hin[k + 1]; b += kPullSeg) {
+                segrow.push_back((int32_t)k);
+                segbeg.push_back((int32_t)b);
+            }
+        }
+    }
+    lseg0.push_back((int32_t)segrow.size());
+    std::vector<int32_t> rows;
+    rows.reserve(n);
+    g->pl_bin_off[0] = 0;
+    for (int b = 0; b < 4; ++b) {
+        rows.insert(rows.end(), bins[b].begin(), bins[b].end());
+        g->pl_bin_off[b + 1] = (int64_t)rows.size();
+    }
+    const int64_t per_task[4] = {kPullThreads, kPullThreads / 4, kPullThreads / 32, 1};
+    g->pl_task_off[0] = 0;
+    for (int b = 0; b < 4; ++b)
+        g->pl_task_off[b + 1] = g->pl_task_off[b] + ((int64_t)bins[b].size() + per_task[b] - 1) / per_task[b];
+    g->pl_task_off[5] = g->pl_task_off[4] + (int64_t)segrow.size();
+    g->pl_nlrows = (int)lrows.size();
+    // bins 1-2: offsets of their edges once copied contiguously in bin order
+    const int64_t n12 = g->pl_bin_off[2];
+    std::vector<int32_t> off12(n12 + 1);
+    int64_t run = 0;
+    for (int64_t i = 0; i < n12; ++i) {
+        off12[i] = (int32_t)run;
+        run += (int64_t)hin[rows[i] + 1] - hin[rows[i]];
+    }
+    off12[n12] = (int32_t)run;
+    auto up = [](int32_t **d, const std::vector<int32_t> &h) -> di_status {
+        DI_CUDA_TRY(cudaMalloc(d, std::max<size_t>(h.size(), 1) * sizeof(int32_t)));
+        if (!h.empty()) DI_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return DI_OK;
+    };
+    DI_TRY(up(&g->pl_rows, rows));
+    DI_TRY(up(&g->pl_seg_row, segrow));
+    DI_TRY(up(&g->pl_seg_beg, segbeg));
+    DI_TRY(up(&g->pl_lrows, lrows));
+    DI_TRY(up(&g->pl_lseg0, lseg0));
+    DI_TRY(up(&g->pl_b12_off, off12));
+    DI_CUDA_TRY(cudaMalloc(&g->pl_b12_col, std::max<int64_t>(run, 1) * sizeof(int32_t)));
+    if (n12 > 0)
+        k_copy_rows<<<(int)std::min<int64_t>((n12 + 255) / 256, 4096), 256>>>(g->pl_rows, n12, g->in_rp, g->in_col,
+                                                                              g->pl_b12_off, g->pl_b12_col);
+    DI_CUDA_TRY(cudaGetLastError());
+    DI_CUDA_TRY(cudaDeviceSynchronize());   // graph creation is synchronous
+    return DI_OK;
+}
+
 }  // namespace
+
+PullPlan pull_plan_of(const di_graph *g) {
+    PullPlan p;
+    p.rows = g->pl_rows;
+    p.b12_off = g->pl_b12_off;
+    p.b12_col = g->pl_b12_col;
+    for (int b = 0; b < 5; ++b) p.bin_off[b] = g->pl_bin_off[b];
+    for (int b = 0; b < 6; ++b) p.task_off[b] = g->pl_task_off[b];
+    p.seg_row = g->pl_seg_row;
+    p.seg_beg = g->pl_seg_beg;
+    return p;
+}
 
 di_status ensure_scale(di_graph *g, double d, cudaStream_t s) {
     if (g->s64 && g->scale_d == d) return DI_OK;
@@ -301,6 +436,8 @@ extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_
     }
     // 2. int32 offsets and out-degree statistics
     k_offsets32<<<grid_for(n + 1, kThreads, cap), kThreads, 0, s>>>(rp64, g->rp, n, cnt64 + 1, ints);
+    DI_CUDA_TRY(cudaMalloc(&g->outdeg, n * sizeof(int32_t)));
+    k_outdeg<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, n, g->outdeg);
     // 3. in-degrees
     DI_CUDA_TRY(tmp.alloc(&cnt, n));
     DI_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int32_t), s));
@@ -328,6 +465,8 @@ extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_
     DI_CUDA_TRY(cudaMemcpyAsync(cursor, g->in_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     k_fill_in<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, g->pcol, n, cursor, g->in_col);
 
+    DI_CUDA_TRY(cudaMalloc(&g->erow, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    k_erow<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->in_rp, n, g->erow);
     // 6. hot targets: the smallest threshold t >= kHotMinIndeg with at most
     //    kMaxHot nodes of in-degree >= t (binary search on t)
     int lo = kHotMinIndeg, hi = INT32_MAX;
@@ -367,37 +506,13 @@ extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_
     DI_CUDA_TRY(cudaStreamSynchronize(s));
     g->n_hot = nh;
 
-    // 7. segments of the long in-rows (exact residual load balance)
+    // 7. segments of the long in-rows (exact residual load balance), two granularities
     {
         std::vector<int32_t> hin(n + 1);
-        // only the long rows matter; copying the offsets once is cheap next to the graph upload
         DI_CUDA_TRY(cudaMemcpy(hin.data(), g->in_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        std::vector<int32_t> rows, seg0, segrow;
-        std::vector<int64_t> segbeg;
-        for (int64_t k = 0; k < n; ++k) {
-            int64_t len = (int64_t)hin[k + 1] - hin[k];
-            if (len > kResSeg) {
-                seg0.push_back(static_cast<int32_t>(segrow.size()));
-                for (int64_t b = hin[k]; b < hin[k + 1]; b += kResSeg) {
-                    segrow.push_back(static_cast<int32_t>(rows.size()));
-                    segbeg.push_back(b);
-                }
-                rows.push_back(static_cast<int32_t>(k));
-            }
-        }
-        seg0.push_back(static_cast<int32_t>(segrow.size()));
-        g->n_long_rows = static_cast<int>(rows.size());
-        g->n_seg = static_cast<int>(segrow.size());
-        DI_CUDA_TRY(cudaMalloc(&g->long_rows, std::max<size_t>(rows.size(), 1) * sizeof(int32_t)));
-        DI_CUDA_TRY(cudaMalloc(&g->long_seg0, seg0.size() * sizeof(int32_t)));
-        DI_CUDA_TRY(cudaMalloc(&g->seg_row, std::max<size_t>(segrow.size(), 1) * sizeof(int32_t)));
-        DI_CUDA_TRY(cudaMalloc(&g->seg_beg, std::max<size_t>(segbeg.size(), 1) * sizeof(int64_t)));
-        if (!rows.empty()) {
-            DI_CUDA_TRY(cudaMemcpy(g->long_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-            DI_CUDA_TRY(cudaMemcpy(g->seg_row, segrow.data(), segrow.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-            DI_CUDA_TRY(cudaMemcpy(g->seg_beg, segbeg.data(), segbeg.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-        }
-        DI_CUDA_TRY(cudaMemcpy(g->long_seg0, seg0.data(), seg0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        DI_TRY(build_segments(hin, kResSeg, &g->n_long_rows, &g->n_seg, &g->long_rows, &g->long_seg0, &g->seg_row,
+                              &g->seg_beg));
+        DI_TRY(build_pull_plan(g, hin));
     }
     DI_CUDA_TRY(cudaGetLastError());
     DI_CUDA_TRY(cudaStreamSynchronize(s));

@@ -6,11 +6,14 @@
 // rounding that FP32 pushes accumulate, gives the exact stopping residual
 // |F|_1, and forms the warm-start fluid F_0.
 //
-// (P H)_k = sum over in-edges j -> k of (d / outdeg_j) H_j is a gather over
-// the transpose: no atomics, and a fixed summation order per graph object.
-// In-rows longer than kResSeg edges are cut in segments whose partial sums
-// are combined in segment order.
+// (P H)_k = sum over in-edges j -> k of g_j, g_j = (d / outdeg_j) H_j, is a
+// gather over the transpose with the binned pull plan of pull.cuh: no
+// atomics and a fixed summation order per graph object (rows longer than
+// 4096 in-edges are summed in segments whose partials are added in order).
+#include <algorithm>
+
 #include "di_internal.cuh"
+#include "pull.cuh"
 
 namespace di {
 namespace {
@@ -25,46 +28,25 @@ __global__ void __launch_bounds__(kResThreads) k_res_prep(const SolveDesc *__res
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) g[i] = s64[i] * H[i];
 }
 
-__global__ void __launch_bounds__(kResThreads) k_res_seg(const SolveState *__restrict__ st, int mode,
-                                                         const int32_t *__restrict__ in_rp,
-                                                         const int32_t *__restrict__ in_col,
-                                                         const int32_t *__restrict__ long_rows,
-                                                         const int32_t *__restrict__ seg_row,
-                                                         const int64_t *__restrict__ seg_beg, int n_seg,
-                                                         const double *__restrict__ g,
-                                                         double *__restrict__ seg_part) {
-    if (mode == RES_LEVEL && !st->do_recompute) return;
-    for (int s = blockIdx.x; s < n_seg; s += gridDim.x) {
-        const int32_t row = long_rows[seg_row[s]];
-        const int64_t b = seg_beg[s];
-        const int64_t e = b + kResSeg < (int64_t)in_rp[row + 1] ? b + kResSeg : (int64_t)in_rp[row + 1];
-        double acc = 0.0;
-        for (int64_t q = b + threadIdx.x; q < e; q += kResThreads) acc += g[in_col[q]];
-        double mx = 0.0;
-        block_sum_max<kResThreads>(acc, mx);
-        if (threadIdx.x == 0) seg_part[s] = acc;
-    }
-}
-
+// Rows of bins 1-5 of the pull plan: F = B + P H - H written by the row's
+// owner; segments of the longest rows leave their partial sums in seg_part
+// for k_res_long.
 template <typename FT>
-__global__ void __launch_bounds__(kResThreads) k_res_rows(
-    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ in_rp,
-    const int32_t *__restrict__ in_col, const int32_t *__restrict__ long_rows,
-    const int32_t *__restrict__ long_seg0, int n_long, const double *__restrict__ seg_part,
-    const double *__restrict__ g, int64_t n, double *__restrict__ part_sum, double *__restrict__ part_max,
-    int mode) {
+__global__ void __launch_bounds__(kPullThreads, 4) k_res_pull(const PullPlan pl, const SolveDesc *__restrict__ desc,
+                                                           const SolveState *__restrict__ st,
+                                                           const int32_t *__restrict__ in_rp,
+                                                           const int32_t *__restrict__ in_col,
+                                                           const double *__restrict__ g,
+                                                           double *__restrict__ seg_part,
+                                                           double *__restrict__ part_sum,
+                                                           double *__restrict__ part_max, int mode) {
     if (mode == RES_LEVEL && !st->do_recompute) return;   // host-driven levels launch it every time
     const double *__restrict__ B = desc->B;
     const double *__restrict__ H = desc->H;
     FT *__restrict__ Ffl = (mode == RES_LEVEL || mode == RES_WARM_INIT) ? static_cast<FT *>(desc->F) : nullptr;
     double *__restrict__ F64 = mode == RES_WARM_INIT ? nullptr : desc->F_out;
-
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double lsum = 0.0, lmax = 0.0;
-
-    auto emit = [&](int64_t k, double acc) {
+    auto emit = [&](int32_t k, double acc) {
         const double f = B[k] + acc - H[k];
         if (Ffl) Ffl[k] = static_cast<FT>(f);
         if (F64) F64[k] = f;
@@ -72,46 +54,56 @@ __global__ void __launch_bounds__(kResThreads) k_res_rows(
         lsum += a;
         lmax = fmax(lmax, a);
     };
-
-    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-        const int64_t k = base + lane;
-        int32_t b = 0, e = 0;
-        if (k < n) { b = in_rp[k]; e = in_rp[k + 1]; }
-        const int len = e - b;
-        double acc = 0.0;
-        if (len <= 32) {
-            for (int32_t q = b; q < e; ++q) acc += g[in_col[q]];
-        }
-        unsigned med = __ballot_sync(0xffffffffu, len > 32 && len <= kResSeg);
-        while (med) {
-            const int src = __ffs(med) - 1;
-            med &= med - 1;
-            const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
-            double part = 0.0;
-            for (int32_t q = mb + lane; q < me; q += 32) part += g[in_col[q]];
-            part = warp_sum(part);
-            if (lane == src) acc = part;
-        }
-        if (k < n && len <= kResSeg) emit(k, acc);
-    }
-    // rows split in segments: one warp per row, segment partials in order
-    for (int64_t r = warp; r < n_long; r += nwarps) {
-        const int32_t s0 = long_seg0[r], s1 = long_seg0[r + 1];
-        double part = 0.0;
-        for (int32_t s = s0 + lane; s < s1; s += 32) part += seg_part[s];
-        part = warp_sum(part);
-        if (lane == 0) emit(long_rows[r], part);
-    }
-
-    block_sum_max<kResThreads>(lsum, lmax);
+    auto seg = [&](int64_t s, int32_t, double acc) { seg_part[s] = acc; };
+    pull_plan<double>(pl, in_rp, in_col, g, emit, seg);
+    block_sum_max<kPullThreads>(lsum, lmax);
     if (threadIdx.x == 0) {
         part_sum[blockIdx.x] = lsum;
         part_max[blockIdx.x] = lmax;
     }
+}
+
+// Rows longer than kPullSeg: one warp adds a row's segment partials in
+// segment order, then the last CTA combines every CTA partial of both
+// kernels (in a fixed order) and runs the control step of the mode.
+template <typename FT>
+__global__ void __launch_bounds__(kResThreads) k_res_long(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ lrows,
+    const int32_t *__restrict__ lseg0, int n_long, const double *__restrict__ seg_part,
+    double *__restrict__ part_sum, double *__restrict__ part_max, int pull_blocks, int mode) {
+    if (mode == RES_LEVEL && !st->do_recompute) return;
+    const double *__restrict__ B = desc->B;
+    const double *__restrict__ H = desc->H;
+    FT *__restrict__ Ffl = (mode == RES_LEVEL || mode == RES_WARM_INIT) ? static_cast<FT *>(desc->F) : nullptr;
+    double *__restrict__ F64 = mode == RES_WARM_INIT ? nullptr : desc->F_out;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double lsum = 0.0, lmax = 0.0;
+    for (int64_t r = warp; r < n_long; r += nwarps) {
+        const int32_t s0 = lseg0[r], s1 = lseg0[r + 1];
+        double part = 0.0;
+        for (int32_t s = s0 + lane; s < s1; s += 32) part += seg_part[s];
+        part = warp_sum(part);
+        if (lane == 0) {
+            const int32_t k = lrows[r];
+            const double f = B[k] + part - H[k];
+            if (Ffl) Ffl[k] = static_cast<FT>(f);
+            if (F64) F64[k] = f;
+            lsum += fabs(f);
+            lmax = fmax(lmax, fabs(f));
+        }
+    }
+    block_sum_max<kResThreads>(lsum, lmax);
+    if (threadIdx.x == 0) {
+        part_sum[pull_blocks + blockIdx.x] = lsum;
+        part_max[pull_blocks + blockIdx.x] = lmax;
+    }
     if (!last_block(&st->res_blocks)) return;
-    // last block: deterministic combination of the block partials
+    // last block: deterministic combination of the partials of both kernels
+    const int total = pull_blocks + gridDim.x;
     double s = 0.0, m = 0.0;
-    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
         s += part_sum[i];
         m = fmax(m, part_max[i]);
     }
@@ -127,42 +119,53 @@ __global__ void __launch_bounds__(kResThreads) k_res_rows(
             st->done = 3;
         } else if (s <= desc->tol) {
             st->done = 1;
-        } else if (st->confirming) {
-            st->force_push = 1;   // the scan's estimate was too optimistic
+        } else if (st->confirming && st->r_confirm > 0.0) {
+            // the level's estimate was too optimistic: calibrate later estimates
+            st->est_scale = fmax(st->est_scale, 1.0) * fmax(s / st->r_confirm, 1.0);
         }
         st->confirming = 0;
     } else if (mode == RES_WARM_INIT) {
         st->T = m;
         st->f0_l1 = s;
+        if (!isfinite(s)) st->done = 3;
+        else if (s <= desc->tol) st->done = 1;   // H_0 already meets the tolerance
     }
 }
 
 }  // namespace
 
+constexpr int kResLongBlocks = 64;
+
 int residual_grid(int sms) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_res_rows<double>, kResThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_res_pull<double>, kPullThreads, 0) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
     return per_sm * sms;
 }
 
-int residual_kernels(const di_graph *g) { return g->n_seg > 0 ? 3 : 2; }
+int residual_kernels(const di_graph *) { return 3; }
+
+int residual_partials(const di_graph *g) { return g->grid_res + kResLongBlocks; }
 
 void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s) {
     Workspace &ws = g->ws;
+    const PullPlan pl = pull_plan_of(g);
+    const int pull_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(g->grid_res, pl.task_off[5]));
     k_res_prep<<<g->grid_res, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, g->s64, ws.g, g->n);
-    if (g->n_seg > 0)
-        k_res_seg<<<std::min(g->n_seg, g->grid_res), kResThreads, 0, s>>>(
-            ws.st, (int)mode, g->in_rp, g->in_col, g->long_rows, g->seg_row, g->seg_beg, g->n_seg, ws.g, ws.seg_part);
-    if (fluid_fp64)
-        k_res_rows<double><<<g->grid_res, kResThreads, 0, s>>>(ws.desc, ws.st, g->in_rp, g->in_col, g->long_rows,
-                                                               g->long_seg0, g->n_long_rows, ws.seg_part, ws.g,
-                                                               g->n, ws.part_sum, ws.part_max, (int)mode);
-    else
-        k_res_rows<float><<<g->grid_res, kResThreads, 0, s>>>(ws.desc, ws.st, g->in_rp, g->in_col, g->long_rows,
-                                                              g->long_seg0, g->n_long_rows, ws.seg_part, ws.g,
-                                                              g->n, ws.part_sum, ws.part_max, (int)mode);
+    if (fluid_fp64) {
+        k_res_pull<double><<<pull_blocks, kPullThreads, 0, s>>>(pl, ws.desc, ws.st, g->in_rp, g->in_col, ws.g,
+                                                                ws.seg_part, ws.part_sum, ws.part_max, (int)mode);
+        k_res_long<double><<<kResLongBlocks, kResThreads, 0, s>>>(ws.desc, ws.st, g->pl_lrows, g->pl_lseg0,
+                                                                  g->pl_nlrows, ws.seg_part, ws.part_sum,
+                                                                  ws.part_max, pull_blocks, (int)mode);
+    } else {
+        k_res_pull<float><<<pull_blocks, kPullThreads, 0, s>>>(pl, ws.desc, ws.st, g->in_rp, g->in_col, ws.g,
+                                                               ws.seg_part, ws.part_sum, ws.part_max, (int)mode);
+        k_res_long<float><<<kResLongBlocks, kResThreads, 0, s>>>(ws.desc, ws.st, g->pl_lrows, g->pl_lseg0,
+                                                                 g->pl_nlrows, ws.seg_part, ws.part_sum,
+                                                                 ws.part_max, pull_blocks, (int)mode);
+    }
 }
 
 }  // namespace di

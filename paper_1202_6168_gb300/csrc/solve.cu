@@ -1,25 +1,27 @@
 // solve.cu - the D-iteration level loop on one GPU.
 //
-// One threshold level (Sec. 2.4) is two kernels:
-//   k_scan  - reads the fluid once: fused L1 residual sum |F_i| and max |F_i|,
-//             and compaction of the frontier S = { i : |F_i| >= T } by warp
-//             ballots and a block prefix (one atomic per 2048 nodes);
-//   k_push  - for every i in S: f = atomicExch(F_i, 0), H_i += f (FP64),
-//             and F_k += (d / outdeg_i) f for every out-edge i -> k
-//             (Eqs. defF/defH), with red.global.add.  A row is pushed by one
-//             thread (outdeg <= 16), one warp (<= 512) or the whole CTA.
-//             Targets of very high in-degree are accumulated in shared
-//             memory per CTA and flushed once, so the hottest addresses of
-//             a power-law graph do not serialise the L2 atomics.
-// The last block of k_scan decides the next step on the device: push, lower
-// T to the largest fluid when the frontier is empty, confirm a stop request
-// with an exact FP64 residual (residual.cu), or finish.  The levels run in a
-// CUDA graph whose WHILE conditional node repeats [scan, push, IF(recompute)]
-// until the scan reports completion: no host round trip per level.
+// One threshold level (Sec. 2.4) diffuses, at once, every node whose fluid
+// satisfies |F_i| >= T (Eqs. defF/defH):
+//   k_select     - drains the selected nodes (H_i += F_i, F_i = 0) into
+//                  w_i = (d / outdeg_i) F_i, with the L1 norm and max of the
+//                  fluid from the same read, and decides the next steps;
+//   k_pull_level - dense levels: F_k += sum of w_j over the in-edges (binned
+//                  gather over the transpose, no atomics);
+//   k_pushw      - sparse levels: F_k += w_j for the out-edges of the active
+//                  nodes (edge-parallel red.global.add; targets of very high
+//                  in-degree accumulated in shared memory per CTA).
+// Both propagations send the fluid the selected nodes held at the start of
+// the level, so F + H - P H is unchanged by a level (the invariant that gives
+// H -> X and |X - H|_1 <= |F|_1 / (1 - d)).  The levels run in a CUDA graph:
+// a WHILE conditional node repeats [k_select, IF/ELSE(pull | push),
+// IF(exact FP64 residual)], every decision taken by k_select's last CTA on
+// the device, with no host round trip per level.
+// k_scan is the frontier selection alone (di_frontier).
 #include <algorithm>
 #include <cmath>
 
 #include "di_internal.cuh"
+#include "pull.cuh"
 
 namespace di {
 namespace {
@@ -62,8 +64,10 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
     if (threadIdx.x == 0) {
         st->b_l1 = ts;
         st->f0_l1 = ts;
-        st->r_exact = ts;
-        st->T = tm;   // T_0 = max |F_0|
+        st->r_exact = ts;   // F_0 = B exactly: this is the exact residual of H_0 = 0
+        st->T = tm;         // T_0 = max |F_0|
+        if (!isfinite(ts)) st->done = 3;
+        else if (ts <= desc->tol) st->done = 1;
     }
 }
 
@@ -86,20 +90,13 @@ __global__ void __launch_bounds__(kScanThreads) k_bnorm(const SolveDesc *__restr
 
 // ------------------------------------------------------------------ scan
 
+// Frontier selection alone: S = { i : |F_i| >= T } compacted in node order
+// within blocks of 2048 nodes (warp ballots, one prefix, one atomic per
+// block), with the L1 norm and max |F_i| fused into the same read.
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                        int32_t *__restrict__ front, int64_t n,
-                                                       double *__restrict__ part_sum, double *__restrict__ part_max,
-                                                       cudaGraphConditionalHandle h_while,
-                                                       cudaGraphConditionalHandle h_if, int ctl) {
-    // ctl: 0 standalone frontier, 1 level loop in a CUDA graph, 2 host-driven level loop
-    if (ctl && st->done) {
-        if (ctl == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
-            cudaGraphSetConditional(h_if, 0);
-            cudaGraphSetConditional(h_while, 0);
-        }
-        return;
-    }
+                                                       double *__restrict__ part_sum, double *__restrict__ part_max) {
     using AT = typename Acc<FT>::T;
     const FT *__restrict__ F = static_cast<const FT *>(desc->F);
     const FT Tc = thr_cast(st->T, FT(0));
@@ -158,46 +155,146 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const SolveDesc *__restri
     if (threadIdx.x != 0) return;
     st->r_scan = ts;
     st->max_scan = tm;
-    if (!ctl) return;   // standalone frontier: the host reads nfront
+}
 
+// ------------------------------------------------------------------ asynchronous push level
+
+// Scan of one level of the asynchronous design: frontier compaction in node
+// order within 2048-node blocks (warp ballots, one prefix, one atomic per
+// block) with the L1 norm and max of the fluid fused into the same read.
+// Its last CTA decides the level: push the frontier (T <- T / alpha), lower T
+// to the largest fluid after an empty scan, or request an exact residual to
+// confirm a stop (no push).  ctl: 1 in a CUDA graph, 2 host-driven.
+template <typename FT>
+__global__ void __launch_bounds__(kScanThreads) k_scan_level(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front, int64_t n,
+    double *__restrict__ part_sum, double *__restrict__ part_max, cudaGraphConditionalHandle h_while,
+    cudaGraphConditionalHandle h_rec, int ctl) {
+    {
+        const int done0 = st->done;
+        const int stop = done0 ? done0 : (st->level >= desc->max_levels ? 2 : 0);
+        if (stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->done = stop;
+                st->push_count = 0;
+                if (ctl == 1) {
+                    cudaGraphSetConditional(h_rec, 0);
+                    cudaGraphSetConditional(h_while, 0);
+                }
+            }
+            return;
+        }
+    }
+    using AT = typename Acc<FT>::T;
+    const FT *__restrict__ F = static_cast<const FT *>(desc->F);
+    const FT Tc = thr_cast(st->T, FT(0));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    __shared__ int s_cnt[kScanItems * (kScanThreads / 32)];
+    __shared__ int s_base;
+    AT acc = 0;
+    FT mx = 0;
+    for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
+        unsigned masks[kScanItems];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t idx = c0 + k * kScanThreads + threadIdx.x;
+            FT v = 0;
+            if (idx < n) v = fabs(F[idx]);
+            const bool sel = idx < n && v >= Tc && v > FT(0);
+            masks[k] = __ballot_sync(0xffffffffu, sel);
+            acc += static_cast<AT>(v);
+            mx = max(mx, v);
+            if (lane == 0) s_cnt[k * (kScanThreads / 32) + warp] = __popc(masks[k]);
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan of the 64 counts in node order
+            const int a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
+            int incl = a + b;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = incl - a - b;
+            s_cnt[2 * lane] = excl;
+            s_cnt[2 * lane + 1] = excl + a;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) s_base = total ? atomicAdd(&st->nfront, total) : 0;
+        }
+        __syncthreads();
+        const int base = s_base;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if ((masks[k] >> lane) & 1u)
+                front[base + s_cnt[k * (kScanThreads / 32) + warp] + __popc(masks[k] & lt_mask)] =
+                    static_cast<int32_t>(c0 + k * kScanThreads + threadIdx.x);
+        }
+        __syncthreads();
+    }
+    double s = static_cast<double>(acc);
+    double m = static_cast<double>(mx);
+    block_sum_max<kScanThreads>(s, m);
+    if (threadIdx.x == 0) { part_sum[blockIdx.x] = s; part_max[blockIdx.x] = m; }
+    if (!last_block(&st->scan_blocks)) return;
+    double ts = 0.0, tm = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) { ts += part_sum[i]; tm = fmax(tm, part_max[i]); }
+    block_sum_max<kScanThreads>(ts, tm);
+    if (threadIdx.x != 0) return;
+
+    // control (all loads first: one round trip)
     const int nf = st->nfront;
-    st->nfront = 0;
-    st->tile_ctr = 0;
-    int push = 0, rec = 0;
+    double T = st->T;
+    int level = st->level, since = st->since_recompute, iters = st->body_iters;
+    const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
+    const double tol = desc->tol, alpha = desc->alpha;
+    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    int done = 0, rec = 0, push = 0;
     if (!isfinite(ts)) {
-        st->done = 3;
-    } else if (ts <= desc->tol && !st->force_push) {
-        rec = 1;                  // stop request: confirm on the exact residual
+        done = 3;
+    } else if (ts * est <= tol) {
+        rec = 1;                            // stop request: confirm on the exact residual, no push
         st->confirming = 1;
-    } else if (st->level >= desc->max_levels) {
-        st->done = 2;
+        st->r_confirm = ts * est;
     } else if (nf == 0) {
-        double T = st->T;         // empty level: skip straight to the first T <= max |F|
-        while (T > tm && T > 0.0) T /= desc->alpha;
-        st->T = T;
+        if (tm > 0.0)                       // empty level: next T is the first T / alpha^k <= max |F|
+            for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
     } else {
         push = nf;
-        st->level += 1;
-        st->force_push = 0;
-        st->since_recompute += 1;
-        st->T = st->T / desc->alpha;
-        if (!desc->fluid_fp64 && desc->recompute_every > 0 && st->since_recompute >= desc->recompute_every) rec = 1;
+        level += 1;
+        since += 1;
+        T = T / alpha;
+        if (!fp64 && R > 0 && since >= R) rec = 1;
     }
-    st->body_iters += 1;
-    if (!st->done && st->body_iters >= desc->max_body_iters) st->done = 2;
-    if (st->done) { push = 0; rec = 0; }
+    iters += 1;
+    if (!done && iters >= max_iters) done = 2;
+    if (done) { rec = 0; push = 0; }
+    st->r_scan = ts;
+    st->max_scan = tm;
+    st->nfront = 0;
+    st->tile_ctr = 0;
     st->push_count = push;
+    st->T = T;
+    st->level = level;
+    st->since_recompute = since;
+    st->body_iters = iters;
     st->do_recompute = rec;
+    if (done) st->done = done;
     if (ctl == 1) {
-        cudaGraphSetConditional(h_if, rec ? 1u : 0u);
-        if (st->done) cudaGraphSetConditional(h_while, 0);
+        cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
+        if (done) cudaGraphSetConditional(h_while, 0);
     }
 }
 
-// ------------------------------------------------------------------ push
-
+// Push of the asynchronous design, for every frontier node i: f =
+// atomicExch(F_i, 0) (fluid that arrives after the exchange waits for a
+// later level), H_i += f in FP64, and F_k += (d / outdeg_i) f for every
+// out-edge i -> k with red.global.add.  Dynamic tiles of 256 frontier
+// nodes; a row is pushed by its thread (outdeg <= 16), by a warp (<= 512)
+// or by the whole CTA.  Targets of very high in-degree are accumulated in
+// shared memory per CTA and flushed once.
 template <typename FT>
-__global__ void __launch_bounds__(kPushThreads) k_push(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+__global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                        const int32_t *__restrict__ front,
                                                        const int32_t *__restrict__ rp,
                                                        const int32_t *__restrict__ pcol,
@@ -284,52 +381,522 @@ __global__ void __launch_bounds__(kPushThreads) k_push(const SolveDesc *__restri
     }
 }
 
+
+// ------------------------------------------------------------------ one threshold level
+
+constexpr int kLevelThreads = 256;
+constexpr int kChunkNodes = 32;    // nodes per warp chunk of the sparse push
+constexpr int kRanges = 64;        // chunk counters (contiguous node ranges)
+
+enum : int { P2_NONE = 0, P2_PULL = 1, P2_PUSH = 2 };
+
+// Selection and drain (Sec. 2.4 selection, Eqs. defF/defH drain): for every
+// node with |F_i| >= T: H_i += F_i, F_i = 0, w_i = (d / outdeg_i) F_i; every
+// other node has w_i = 0.  The same read gives the L1 norm and max of the
+// fluid at the start of the level.  The last CTA then decides the next
+// steps on the device: how to propagate w (gather over the in-edges when the
+// active edges are a large share of all edges, scatter from the active nodes
+// otherwise), the next threshold, and whether an exact FP64 residual must
+// follow (FP32 fluid refresh, or confirmation of a stop).
+template <typename FT>
+struct Vec4;   // 4 consecutive fluid values per load
+template <>
+struct Vec4<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float *p) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ void store(float *p) const {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ __forceinline__ void load_cs(const float *p) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double *p) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ void store(double *p) const {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+    __device__ __forceinline__ void load_cs(const double *p) {
+        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p)),
+                      b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+// Selection and drain (Sec. 2.4 selection, Eqs. defF/defH drain): for every
+// node with |F_i| >= T: H_i += F_i, F_i = 0, w_i = (d / outdeg_i) F_i; every
+// other node has w_i = 0.  The same read gives the L1 norm and max of the
+// fluid at the start of the level.  Four nodes per thread with vector loads;
+// the history updates of the selected ones are independent loads/stores.
+// The last CTA then decides the next steps on the device: how to propagate w
+// (gather over the in-edges when the active edges are a large share of all
+// edges, scatter from the active nodes otherwise), the next threshold, and
+// whether an exact FP64 residual must follow (FP32 fluid refresh, or
+// confirmation of a stop).
+template <typename FT>
+__global__ void __launch_bounds__(kLevelThreads) k_select(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ outdeg,
+    const FT *__restrict__ scale, FT *__restrict__ w, int64_t n, int64_t nnz, double *__restrict__ part_sum,
+    double *__restrict__ part_max, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_p2,
+    cudaGraphConditionalHandle h_rec, int ctl) {
+    using AT = typename Acc<FT>::T;
+    {
+        const int done0 = st->done;
+        const int stop = done0 ? done0 : (st->level >= desc->max_levels ? 2 : 0);
+        if (stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->done = stop;
+                st->p2mode = P2_NONE;
+                if (ctl == 1) {
+                    cudaGraphSetConditional(h_p2, 0);
+                    cudaGraphSetConditional(h_rec, 0);
+                    cudaGraphSetConditional(h_while, 0);
+                }
+            }
+            return;
+        }
+    }
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    double *__restrict__ H = desc->H;
+    const FT Tc = thr_cast(st->T, FT(0));
+    AT acc = 0;
+    FT mx = 0;
+    unsigned long long my_edges = 0, my_nodes = 0;
+    const int64_t n4 = n / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const int64_t i0 = 4 * q;
+        Vec4<FT> f, sc, wv;
+        f.load(F + i0);
+        sc.load_cs(scale + i0);
+        const int4 dg = __ldcs(reinterpret_cast<const int4 *>(outdeg) + q);
+        const int degs[4] = {dg.x, dg.y, dg.z, dg.w};
+        unsigned selm = 0;
+        double h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const FT a = fabs(f.v[k]);
+            acc += static_cast<AT>(a);
+            mx = max(mx, a);
+            if (a >= Tc && a > FT(0)) selm |= 1u << k;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // independent loads of the selected histories
+            const bool sel = (selm >> k) & 1u;
+            h[k] = sel ? __ldcs(H + i0 + k) : 0.0;
+            wv.v[k] = sel ? f.v[k] * sc.v[k] : FT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((selm >> k) & 1u) {
+                __stcs(H + i0 + k, h[k] + static_cast<double>(f.v[k]));
+                my_nodes += 1;
+                my_edges += static_cast<unsigned long long>(degs[k]);
+                f.v[k] = FT(0);
+            }
+        }
+        if (selm) f.store(F + i0);
+        wv.store(w + i0);
+    }
+    // tail (n not a multiple of 4)
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const FT v = F[i];
+        const FT a = fabs(v);
+        acc += static_cast<AT>(a);
+        mx = max(mx, a);
+        FT wvi = FT(0);
+        if (a >= Tc && a > FT(0)) {
+            __stcs(H + i, __ldcs(H + i) + static_cast<double>(v));
+            F[i] = FT(0);
+            wvi = v * scale[i];
+            my_nodes += 1;
+            my_edges += static_cast<unsigned long long>(outdeg[i]);
+        }
+        w[i] = wvi;
+    }
+    my_edges = warp_sum(my_edges);
+    my_nodes = warp_sum(my_nodes);
+    if ((threadIdx.x & 31) == 0 && my_nodes) {
+        atomicAdd(&st->node_diff, my_nodes);
+        atomicAdd(&st->edge_diff, my_edges);
+        atomicAdd(&st->lvl_nodes, my_nodes);
+        atomicAdd(&st->lvl_edges, my_edges);
+    }
+    double s = static_cast<double>(acc);
+    double m = static_cast<double>(mx);
+    block_sum_max<kLevelThreads>(s, m);
+    if (threadIdx.x == 0) { part_sum[blockIdx.x] = s; part_max[blockIdx.x] = m; }
+    if (!last_block(&st->scan_blocks)) return;
+    double ts = 0.0, tm = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) { ts += part_sum[i]; tm = fmax(tm, part_max[i]); }
+    block_sum_max<kLevelThreads>(ts, tm);
+    if (threadIdx.x != 0) return;
+
+    // control of the next steps (all loads first: one round trip)
+    const unsigned long long lnodes = st->lvl_nodes, ledges = st->lvl_edges;
+    double T = st->T;
+    int level = st->level, since = st->since_recompute, iters = st->body_iters;
+    const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
+    const double tol = desc->tol, alpha = desc->alpha;
+    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    int done = 0, rec = 0, p2 = P2_NONE;
+    if (!isfinite(ts)) {
+        done = 3;
+    } else {
+        if (lnodes > 0) {
+            level += 1;
+            since += 1;
+            T = T / alpha;
+            p2 = desc->propagation != 2 &&
+                         ledges * (unsigned long long)desc->push_ratio >= (unsigned long long)nnz
+                     ? P2_PULL
+                     : P2_PUSH;
+            if (ledges == 0) p2 = P2_NONE;      // only dangling nodes drained
+        } else if (tm > 0.0) {
+            // empty level: next T is the first T / alpha^k <= max |F| (tm > 0, so
+            // at most ~3600 steps from any double down to the smallest denormal)
+            for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+        }
+        if (ts * est <= tol) {
+            rec = 1;                      // stop request: confirm on the exact residual
+            st->confirming = 1;
+            st->r_confirm = ts * est;
+        } else if (!fp64 && R > 0 && since >= R) {
+            rec = 1;
+        }
+    }
+    iters += 1;
+    if (!done && iters >= max_iters) done = 2;
+    if (done) rec = 0;
+    // with done set here nothing was drained (non-finite) or the cap is hit
+    // after this level's drain: the propagation below still runs
+    st->r_scan = ts;
+    st->max_scan = tm;
+    st->T = T;
+    st->level = level;
+    st->since_recompute = since;
+    st->body_iters = iters;
+    st->lvl_nodes = 0;
+    st->lvl_edges = 0;
+    st->p2mode = p2;
+    st->do_recompute = rec;
+    if (done) st->done = done;
+    if (ctl == 1) {
+        cudaGraphSetConditional(h_p2, p2 == P2_PULL ? 1u : 0u);
+        cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
+        if (done) cudaGraphSetConditional(h_while, 0);
+    }
+}
+
+// Dense propagation: F_k += sum of w_j over the in-edges j -> k (binned
+// gather, pull.cuh).  Each row has one owner, except the longest rows whose
+// segments add their partial sums with red.global.add.
+template <typename FT>
+__global__ void __launch_bounds__(kPullThreads, 4) k_pull_level(const PullPlan pl, const SolveDesc *__restrict__ desc,
+                                                             const SolveState *__restrict__ st,
+                                                             const int32_t *__restrict__ in_rp,
+                                                             const int32_t *__restrict__ in_col,
+                                                             const FT *__restrict__ w) {
+    if (st->p2mode != P2_PULL) return;
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    auto emit = [&](int32_t k, FT acc) {
+        if (acc != FT(0)) F[k] += acc;
+    };
+    auto seg = [&](int64_t, int32_t k, FT acc) {
+        if (acc != FT(0)) red_add(F + k, acc);
+    };
+    pull_plan<FT>(pl, in_rp, in_col, w, emit, seg);
+}
+
+// Dense propagation, flat form: each thread takes 16 consecutive in-edges
+// (vector loads of their sources and destination rows), gathers the 16
+// values of w independently, sums runs of equal destination and adds each
+// run with one red.global.add.  Perfectly balanced whatever the in-degrees;
+// the reds of a warp land on neighbouring rows.
+constexpr int kFlatEdges = 16;
+
+template <typename FT>
+__global__ void __launch_bounds__(kLevelThreads) k_pull_flat(const SolveDesc *__restrict__ desc,
+                                                             const SolveState *__restrict__ st,
+                                                             const int32_t *__restrict__ in_col,
+                                                             const int32_t *__restrict__ erow,
+                                                             const FT *__restrict__ w, int64_t nnz) {
+    if (st->p2mode != P2_PULL) return;
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    const int64_t nchunks = (nnz + kFlatEdges - 1) / kFlatEdges;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += stride) {
+        const int64_t e0 = c * kFlatEdges;
+        int32_t col[kFlatEdges], row[kFlatEdges];
+        if (e0 + kFlatEdges <= nnz) {
+#pragma unroll
+            for (int v = 0; v < kFlatEdges / 4; ++v) {
+                const int4 a = __ldcs(reinterpret_cast<const int4 *>(in_col + e0) + v);
+                const int4 b = __ldcs(reinterpret_cast<const int4 *>(erow + e0) + v);
+                col[4 * v] = a.x; col[4 * v + 1] = a.y; col[4 * v + 2] = a.z; col[4 * v + 3] = a.w;
+                row[4 * v] = b.x; row[4 * v + 1] = b.y; row[4 * v + 2] = b.z; row[4 * v + 3] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kFlatEdges; ++k) {
+                const bool ok = e0 + k < nnz;
+                col[k] = ok ? in_col[e0 + k] : 0;
+                row[k] = ok ? erow[e0 + k] : -1;
+            }
+        }
+        FT val[kFlatEdges];
+#pragma unroll
+        for (int k = 0; k < kFlatEdges; ++k) val[k] = row[k] >= 0 ? w[col[k]] : FT(0);
+        int32_t cur = row[0];
+        FT acc = val[0];
+#pragma unroll
+        for (int k = 1; k < kFlatEdges; ++k) {
+            if (row[k] != cur) {
+                if (cur >= 0 && acc != FT(0)) red_add(F + cur, acc);
+                cur = row[k];
+                acc = val[k];
+            } else {
+                acc += val[k];
+            }
+        }
+        if (cur >= 0 && acc != FT(0)) red_add(F + cur, acc);
+    }
+}
+
+// Edge-parallel push of the out-edges of up to 32 nodes held one per lane
+// (b, deg, w; deg = 0 for an idle lane).  The warp walks the concatenation
+// of the 32 rows 32 edges at a time: edge e belongs to the first lane whose
+// inclusive degree prefix exceeds e (5-step search over the lanes'
+// prefixes), so column loads are coalesced and each lane issues an
+// independent red whatever the mix of degrees.
+template <typename FT>
+__device__ __forceinline__ void push_rows(FT *__restrict__ F, FT *s_hot, const int32_t *__restrict__ pcol,
+                                          int32_t b, int deg, FT w, int lane) {
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - deg;
+    const int32_t off = b - excl;   // column position of edge e of this lane's row: off + e
+    auto src_of = [&](int e) {      // number of lanes whose inclusive prefix is <= e
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, src + step - 1);
+            if (v <= e) src += step;
+        }
+        return src < 31 ? src : 31;
+    };
+    auto push1 = [&](int32_t c, FT wv) {
+        if (c >= 0) red_add(F + c, wv);
+        else atomicAdd(&s_hot[-1 - c], wv);
+    };
+    for (int base = 0; base < total; base += 64) {
+        const int e0 = base + lane, e1 = base + 32 + lane;
+        const int s0 = src_of(e0), s1 = src_of(e1);
+        const int32_t o0 = __shfl_sync(0xffffffffu, off, s0), o1 = __shfl_sync(0xffffffffu, off, s1);
+        const FT w0 = __shfl_sync(0xffffffffu, w, s0), w1 = __shfl_sync(0xffffffffu, w, s1);
+        const bool ok0 = e0 < total, ok1 = e1 < total;
+        const int32_t c0 = ok0 ? __ldcs(pcol + o0 + e0) : 0;
+        const int32_t c1 = ok1 ? __ldcs(pcol + o1 + e1) : 0;
+        if (ok0) push1(c0, w0);
+        if (ok1) push1(c1, w1);
+    }
+}
+
+// Sparse propagation: F_k += w_j for every out-edge j -> k of the nodes with
+// w_j != 0.  Warps claim 32-node chunks from kRanges range counters, find
+// the active nodes with a ballot and push their rows edge-parallel.  Targets
+// of very high in-degree are accumulated in shared memory per CTA and
+// flushed once at the end.
+template <typename FT>
+__global__ void __launch_bounds__(kLevelThreads, 4) k_pushw(const SolveDesc *__restrict__ desc,
+                                                            SolveState *__restrict__ st,
+                                                            const int32_t *__restrict__ rp,
+                                                            const int32_t *__restrict__ pcol,
+                                                            const int32_t *__restrict__ hot_node, int n_hot,
+                                                            const FT *__restrict__ w, int64_t n) {
+    if (st->p2mode != P2_PUSH) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FT *s_hot = reinterpret_cast<FT *>(smem_raw);
+    for (int sl = threadIdx.x; sl < n_hot; sl += kLevelThreads) s_hot[sl] = FT(0);
+    __syncthreads();
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * kLevelThreads + threadIdx.x) >> 5);
+    const int64_t nchunks = (n + kChunkNodes - 1) / kChunkNodes;
+    const int nranges = (int)(nchunks < kRanges ? nchunks : kRanges);
+    const int64_t per_range = (nchunks + nranges - 1) / nranges;
+    for (int t = 0; t < nranges; ++t) {
+        const int r = (gwarp + t) % nranges;
+        const int64_t r_hi = (int64_t)(r + 1) * per_range;
+        const int64_t r_end = r_hi < nchunks ? r_hi : nchunks;
+        for (;;) {
+            unsigned k = 0;
+            if (lane == 0) k = atomicAdd(&st->rctr[r], 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            const int64_t chunk = (int64_t)r * per_range + k;
+            if (chunk >= r_end) break;
+            const int64_t i = chunk * kChunkNodes + lane;
+            FT wv = FT(0);
+            if (i < n) wv = w[i];
+            if (!__ballot_sync(0xffffffffu, wv != FT(0))) continue;
+            int32_t b = 0;
+            int deg = 0;
+            if (wv != FT(0)) {
+                b = __ldcs(rp + i);
+                deg = __ldcs(rp + i + 1) - b;
+            }
+            push_rows<FT>(F, s_hot, pcol, b, deg, wv, lane);
+        }
+    }
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < n_hot; sl += kLevelThreads) {
+        const FT v = s_hot[sl];
+        if (v != FT(0)) red_add(F + hot_node[sl], v);
+    }
+    if (!last_block(&st->push_blocks)) return;
+    for (int r = threadIdx.x; r < kRanges; r += kLevelThreads) st->rctr[r] = 0;
+}
+
 // ------------------------------------------------------------------ host side
 
-template <typename FT>
-void launch_scan(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hi, int ctl) {
-    Workspace &ws = g->ws;
-    k_scan<FT><<<g->grid_scan, kScanThreads, 0, s>>>(ws.desc, ws.st, ws.front, g->n, ws.part_sum, ws.part_max, hw,
-                                                     hi, ctl);
+// L2 access-policy windows: the sparse push scatters into the fluid F and
+// the dense pull gathers from the drained vector w, so each keeps its own
+// target resident while the column indices stream past it.  Attached to
+// each launch, so they are captured into graph nodes and also apply to
+// host-driven launches.  which: 0 = F, 1 = w.
+const cudaAccessPolicyWindow *l2_window(di_graph *g, int which, int fp64, int enabled) {
+    if (!enabled) return nullptr;
+    const int slot = 2 * which + fp64;
+    if (!g->win_ready[slot]) {
+        g->win_ready[slot] = 1;
+        g->win_ok[slot] = 0;
+        int max_persist = 0, max_window = 0;
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, g->device);
+        const size_t bytes = (size_t)g->n * (fp64 ? sizeof(double) : sizeof(float));
+        void *base = which == 0 ? (fp64 ? (void *)g->ws.F64 : (void *)g->ws.F32)
+                                : (fp64 ? (void *)g->ws.w64 : (void *)g->ws.w32);
+        if (max_persist > 0 && max_window > 0 && base) {
+            const size_t limit = std::min<size_t>((size_t)max_persist, bytes);
+            size_t cur = 0;
+            cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+            if (cur < limit) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+            cudaAccessPolicyWindow &w = g->win[slot];
+            w.base_ptr = base;
+            w.num_bytes = std::min<size_t>(bytes, (size_t)max_window);
+            w.hitRatio = (float)std::min(1.0, (double)limit / (double)w.num_bytes);
+            w.hitProp = cudaAccessPropertyPersisting;
+            w.missProp = cudaAccessPropertyStreaming;
+            g->win_ok[slot] = 1;
+        }
+        cudaGetLastError();   // the window is an optimisation; a refusal is not an error
+    }
+    return g->win_ok[slot] ? &g->win[slot] : nullptr;
+}
+
+template <typename Kern, typename... Args>
+void launch_ex(Kern kernel, int grid, int block, size_t smem, cudaStream_t s, const cudaAccessPolicyWindow *win,
+               Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (win) {
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow = *win;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <typename FT>
-void launch_push(di_graph *g, cudaStream_t s) {
+void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
+                  int l2) {
+    Workspace &ws = g->ws;
+    const cudaAccessPolicyWindow *win = l2_window(g, 0, sizeof(FT) == 8, l2);
+    launch_ex(k_scan_level<FT>, g->grid_scan, kScanThreads, 0, s, nullptr, (const SolveDesc *)ws.desc, ws.st,
+              ws.front, (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
+    const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
+    launch_ex(k_push_async<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
+              (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
+              (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
+}
+
+template <typename FT>
+void launch_select(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hp,
+                   cudaGraphConditionalHandle hr, int ctl, int) {
+    const cudaAccessPolicyWindow *win = nullptr;   // elementwise streaming pass
     Workspace &ws = g->ws;
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
-    k_push<FT><<<g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s>>>(ws.desc, ws.st, ws.front, g->rp, g->pcol,
-                                                                         g->hot_node, g->n_hot, scale);
+    FT *w = sizeof(FT) == 4 ? reinterpret_cast<FT *>(ws.w32) : reinterpret_cast<FT *>(ws.w64);
+    launch_ex(k_select<FT>, g->grid_select, kLevelThreads, 0, s, win, (const SolveDesc *)ws.desc, ws.st,
+              (const int32_t *)g->outdeg, scale, w, (int64_t)g->n, (int64_t)g->nnz, ws.part_sum, ws.part_max, hw, hp,
+              hr, ctl);
 }
 
-di_status build_level_graph(di_graph *g, int fp64, int l2_window) {
+template <typename FT>
+void launch_pull(di_graph *g, cudaStream_t s, int l2, int propagation) {
+    const cudaAccessPolicyWindow *win = l2_window(g, 1, sizeof(FT) == 8, l2);
+    if (propagation == 1) {
+        Workspace &ws = g->ws;
+        const FT *w = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(ws.w32) : reinterpret_cast<const FT *>(ws.w64);
+        launch_ex(k_pull_flat<FT>, g->grid_flat, kLevelThreads, 0, s, win, (const SolveDesc *)ws.desc,
+                  (const SolveState *)ws.st, (const int32_t *)g->in_col, (const int32_t *)g->erow, w,
+                  (int64_t)g->nnz);
+        return;
+    }
+    Workspace &ws = g->ws;
+    const FT *w = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(ws.w32) : reinterpret_cast<const FT *>(ws.w64);
+    launch_ex(k_pull_level<FT>, g->grid_pull, kPullThreads, 0, s, win, pull_plan_of(g), (const SolveDesc *)ws.desc,
+              (const SolveState *)ws.st, (const int32_t *)g->in_rp, (const int32_t *)g->in_col, w);
+}
+
+template <typename FT>
+void launch_pushw(di_graph *g, cudaStream_t s, int l2) {
+    const cudaAccessPolicyWindow *win = l2_window(g, 0, sizeof(FT) == 8, l2);
+    Workspace &ws = g->ws;
+    const FT *w = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(ws.w32) : reinterpret_cast<const FT *>(ws.w64);
+    launch_ex(k_pushw<FT>, g->grid_pushw, kLevelThreads, g->n_hot * sizeof(FT), s, win, (const SolveDesc *)ws.desc,
+              ws.st, (const int32_t *)g->rp, (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, w,
+              (int64_t)g->n);
+}
+
+di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     SolverGraph &sg = g->sg[fp64];
-    if (sg.built) return DI_OK;
+    if (sg.built && sg.l2 == l2 && sg.prop == prop) return DI_OK;
+    if (sg.built) {   // rebuilt with the other window setting
+        cudaGraphExecDestroy(sg.exec);
+        cudaGraphDestroy(sg.graph);
+        sg = SolverGraph();
+    }
     cudaStream_t cs = nullptr;
     DI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     struct StreamGuard {
         cudaStream_t s;
         ~StreamGuard() { cudaStreamDestroy(s); }
     } sgd{cs};
-    if (l2_window) {
-        // keep the fluid vector resident in L2 while the column indices stream past it
-        int max_persist = 0, max_window = 0;
-        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
-        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, g->device);
-        const size_t bytes = (size_t)g->n * (fp64 ? sizeof(double) : sizeof(float));
-        if (max_persist > 0 && max_window > 0) {
-            size_t limit = std::min<size_t>((size_t)max_persist, bytes);
-            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
-            cudaStreamAttrValue v = {};
-            v.accessPolicyWindow.base_ptr = fp64 ? (void *)g->ws.F64 : (void *)g->ws.F32;
-            v.accessPolicyWindow.num_bytes = std::min<size_t>(bytes, (size_t)max_window);
-            v.accessPolicyWindow.hitRatio =
-                (float)std::min(1.0, (double)limit / (double)v.accessPolicyWindow.num_bytes);
-            v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-            v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-            cudaStreamSetAttribute(cs, cudaStreamAttributeAccessPolicyWindow, &v);
-            cudaGetLastError();   // the window is an optimisation; ignore refusal
-        }
-    }
+    const int win = l2;
+    // resolve the windows now: their set-up calls are not allowed during capture
+    l2_window(g, 0, fp64, win);
+    l2_window(g, 1, fp64, win);
     DI_CUDA_TRY(cudaGraphCreate(&sg.graph, 0));
     DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_while, sg.graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams wp = {};
@@ -340,22 +907,35 @@ di_status build_level_graph(di_graph *g, int fp64, int l2_window) {
     cudaGraphNode_t wnode;
     DI_CUDA_TRY(cudaGraphAddNode(&wnode, sg.graph, nullptr, nullptr, 0, &wp));
     cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (prop != 3) DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_p2, body, 0, 0));
     DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_if, body, 0, 0));
 
-    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (fp64) {
-        launch_scan<double>(g, cs, sg.h_while, sg.h_if, 1);
-        launch_push<double>(g, cs);
-    } else {
-        launch_scan<float>(g, cs, sg.h_while, sg.h_if, 1);
-        launch_push<float>(g, cs);
-    }
+    cudaGraphNodeParams pp = {};
+    cudaGraphNodeParams ip = {};
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaGraph_t capg = nullptr;
+    cudaGraph_t ended = nullptr;
+    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (prop == 3) {
+        // body: k_scan_level -> k_push_async -> IF(exact residual)
+        if (fp64) launch_async<double>(g, cs, sg.h_while, sg.h_if, 1, win);
+        else launch_async<float>(g, cs, sg.h_while, sg.h_if, 1, win);
+    } else {
+        // body: k_select -> IF/ELSE(pull | push) -> IF(exact residual)
+        if (fp64) launch_select<double>(g, cs, sg.h_while, sg.h_p2, sg.h_if, 1, win);
+        else launch_select<float>(g, cs, sg.h_while, sg.h_p2, sg.h_if, 1, win);
+        DI_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
+        pp.type = cudaGraphNodeTypeConditional;
+        pp.conditional.handle = sg.h_p2;
+        pp.conditional.type = cudaGraphCondTypeIf;
+        pp.conditional.size = 2;                  // [0]: condition != 0 (pull), [1]: else (push)
+        cudaGraphNode_t pnode;
+        DI_CUDA_TRY(cudaGraphAddNode(&pnode, capg, deps, nullptr, ndeps, &pp));
+        DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &pnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
     DI_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
-    cudaGraphNodeParams ip = {};
     ip.type = cudaGraphNodeTypeConditional;
     ip.conditional.handle = sg.h_if;
     ip.conditional.type = cudaGraphCondTypeIf;
@@ -363,16 +943,28 @@ di_status build_level_graph(di_graph *g, int fp64, int l2_window) {
     cudaGraphNode_t inode;
     DI_CUDA_TRY(cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip));
     DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaGraph_t ended = nullptr;
     DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
 
-    cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
-    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (prop != 3) {
+        DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, pp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+        if (fp64) launch_pull<double>(g, cs, win, prop); else launch_pull<float>(g, cs, win, prop);
+        DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
+        DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, pp.conditional.phGraph_out[1], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+        if (fp64) launch_pushw<double>(g, cs, win); else launch_pushw<float>(g, cs, win);
+        DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
+    }
+    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
     launch_residual(g, fp64, RES_LEVEL, cs);
     DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
 
+    DI_CUDA_TRY(cudaGetLastError());
     DI_CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
     sg.built = true;
+    sg.l2 = l2;
+    sg.prop = prop;
     return DI_OK;
 }
 
@@ -405,12 +997,31 @@ di_status ensure_workspace(di_graph *g) {
     const int64_t n = g->n;
     g->grid_scan = std::max(1, std::min<int>(occupancy_grid((const void *)k_scan<float>, kScanThreads, 0, g->num_sms),
                                              (int)((n + kScanChunk - 1) / kScanChunk)));
-    g->grid_push = occupancy_grid((const void *)k_push<double>, kPushThreads, kMaxHot * sizeof(double), g->num_sms);
+    {
+        const int sel = occupancy_grid((const void *)k_select<double>, kLevelThreads, 0, g->num_sms);
+        g->grid_select =
+            (int)std::max<int64_t>(1, std::min<int64_t>(sel, (n / 4 + kLevelThreads - 1) / kLevelThreads));
+        const PullPlan pl = pull_plan_of(g);
+        const int pull = occupancy_grid((const void *)k_pull_level<double>, kPullThreads, 0, g->num_sms);
+        g->grid_pull = (int)std::max<int64_t>(1, std::min<int64_t>(pull, pl.task_off[5]));
+        const int push = occupancy_grid((const void *)k_pushw<double>, kLevelThreads, kMaxHot * sizeof(double),
+                                        g->num_sms);
+        const int64_t chunks = (n + kChunkNodes - 1) / kChunkNodes;
+        g->grid_pushw = (int)std::max<int64_t>(1, std::min<int64_t>(push, (chunks + 7) / 8));
+        g->grid_push = occupancy_grid((const void *)k_push_async<double>, kPushThreads, kMaxHot * sizeof(double),
+                                      g->num_sms);
+        const int flat = occupancy_grid((const void *)k_pull_flat<double>, kLevelThreads, 0, g->num_sms);
+        const int64_t fchunks = (g->nnz + kFlatEdges - 1) / kFlatEdges;
+        g->grid_flat =
+            (int)std::max<int64_t>(1, std::min<int64_t>(flat, (fchunks + kLevelThreads - 1) / kLevelThreads));
+    }
     g->grid_res = residual_grid(g->num_sms);
-    const int parts = std::max({g->grid_scan, g->grid_push, g->grid_res});
+    const int parts = std::max({g->grid_scan, g->grid_select, residual_partials(g)});
+    const PullPlan pl = pull_plan_of(g);
+    const int64_t nseg5 = pl.task_off[5] - pl.task_off[4];
     DI_CUDA_TRY(dmalloc(&ws.front, n));
     DI_CUDA_TRY(dmalloc(&ws.g, n));
-    DI_CUDA_TRY(dmalloc(&ws.seg_part, std::max(g->n_seg, 1)));
+    DI_CUDA_TRY(dmalloc(&ws.seg_part, std::max<int64_t>({(int64_t)g->n_seg, nseg5, 1})));
     DI_CUDA_TRY(dmalloc(&ws.part_sum, parts));
     DI_CUDA_TRY(dmalloc(&ws.part_max, parts));
     DI_CUDA_TRY(dmalloc(&ws.desc, 1));
@@ -443,9 +1054,11 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     Workspace &ws = g->ws;
     const int fp64 = o.fluid_fp64 ? 1 : 0;
     if (fp64 && !ws.F64) DI_CUDA_TRY(dmalloc(&ws.F64, g->n));
+    if (fp64 && !ws.w64) DI_CUDA_TRY(dmalloc(&ws.w64, g->n));
     if (!fp64 && !ws.F32) DI_CUDA_TRY(dmalloc(&ws.F32, g->n));
+    if (!fp64 && !ws.w32) DI_CUDA_TRY(dmalloc(&ws.w32, g->n));
     DI_TRY(ensure_scale(g, d, s));
-    if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window));
+    if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
 
     // descriptor (the previous call has completed: every solve synchronises)
     SolveDesc &dh = *ws.desc_h;
@@ -461,6 +1074,8 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.recompute_every = o.recompute_every;
     dh.fluid_fp64 = fp64;
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
+    dh.propagation = o.propagation;
+    dh.push_ratio = o.push_ratio > 0 ? o.push_ratio : 8;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
@@ -494,8 +1109,9 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     }
     DI_CUDA_TRY(cudaGetLastError());
 
-    double t_scan = 0.0, t_push = 0.0, t_rec = 0.0;
+    double t_level = 0.0, t_rec = 0.0;
     int live_iters = 0;
+    long long host_launches = 0;   // timing mode: kernels launched by the host loop
     if (!o.timing) {
         DI_CUDA_TRY(cudaGraphLaunch(g->sg[fp64].exec, s));
         DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -503,31 +1119,40 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     } else {
         // host-driven levels, a CUDA event between every two kernels
         constexpr int kBatch = 16;
+        const int win = o.l2_window;
         for (cudaEvent_t &e : ws.tev)
             if (!e) DI_CUDA_TRY(cudaEventCreate(&e));
         for (;;) {
             for (int l = 0; l < kBatch; ++l) {
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
-                if (fp64) launch_scan<double>(g, s, 0, 0, 2); else launch_scan<float>(g, s, 0, 0, 2);
+                if (o.propagation == 3) {
+                    if (fp64) launch_async<double>(g, s, 0, 0, 2, win);
+                    else launch_async<float>(g, s, 0, 0, 2, win);
+                } else if (fp64) {
+                    launch_select<double>(g, s, 0, 0, 0, 2, win);
+                    launch_pull<double>(g, s, win, o.propagation);
+                    launch_pushw<double>(g, s, win);
+                } else {
+                    launch_select<float>(g, s, 0, 0, 0, 2, win);
+                    launch_pull<float>(g, s, win, o.propagation);
+                    launch_pushw<float>(g, s, win);
+                }
                 DI_CUDA_TRY(cudaEventRecord(e[1], s));
-                if (fp64) launch_push<double>(g, s); else launch_push<float>(g, s);
-                DI_CUDA_TRY(cudaEventRecord(e[2], s));
                 launch_residual(g, fp64, RES_LEVEL, s);
-                DI_CUDA_TRY(cudaEventRecord(e[3], s));
+                DI_CUDA_TRY(cudaEventRecord(e[2], s));
+                host_launches += (o.propagation == 3 ? 2 : 3) + residual_kernels(g);
             }
             DI_CUDA_TRY(cudaGetLastError());
             DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
             DI_CUDA_TRY(cudaStreamSynchronize(s));
             const int live = std::min(kBatch, ws.st_h->body_iters - live_iters);
             for (int l = 0; l < live; ++l) {
-                float a = 0.f, b = 0.f, c = 0.f;
+                float a = 0.f, c = 0.f;
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventElapsedTime(&a, e[0], e[1]));
-                DI_CUDA_TRY(cudaEventElapsedTime(&b, e[1], e[2]));
-                DI_CUDA_TRY(cudaEventElapsedTime(&c, e[2], e[3]));
-                t_scan += a * 1e-3;
-                t_push += b * 1e-3;
+                DI_CUDA_TRY(cudaEventElapsedTime(&c, e[1], e[2]));
+                t_level += a * 1e-3;
                 t_rec += c * 1e-3;
             }
             live_iters = ws.st_h->body_iters;
@@ -535,8 +1160,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         }
     }
     SolveState st = *ws.st_h;
-    if (st.done != 1) {
-        // level cap or non-finite residual: refresh F_out and the exact residual
+    const bool refresh = st.done != 1 || (F != nullptr && st.recomputes == 0);
+    if (refresh) {
+        // level cap, non-finite residual, or converged before any exact
+        // recomputation wrote F: refresh F_out and the exact residual
         launch_residual(g, fp64, RES_FINAL, s);
         DI_CUDA_TRY(cudaGetLastError());
         DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -569,18 +1196,19 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         stats->warm_used = warm_used;
         stats->status = rc;
         const int rk = residual_kernels(g);
-        long long launches = o.warm_start ? 1 + rk + (warm_used ? 0 : 1) : 1;
-        launches += 2LL * st.body_iters + (long long)rk * st.recomputes;
-        if (!o.timing && st.done == 1) launches += 1;   // the iteration that exits the loop
-        if (st.done != 1) launches += rk;               // final residual refresh
-        if (o.timing) launches = (o.warm_start ? 1 + rk + (warm_used ? 0 : 1) : 1) +
-                                 (long long)(2 + rk) * st.body_iters + (st.done != 1 ? rk : 0);
+        long long launches = o.warm_start ? 1 + rk + (warm_used ? 0 : 1) : 1;   // start
+        if (o.timing) {
+            launches += host_launches;
+        } else {
+            // per live level: select + one propagation kernel; the level that
+            // finds the loop finished; the exact residuals
+            launches += 2LL * st.body_iters + 1 + (long long)rk * st.recomputes;
+        }
+        if (refresh) launches += rk;        // final residual refresh
         stats->gpu_launches = launches;
-        stats->scan_seconds = t_scan;
-        stats->push_seconds = t_push;
+        stats->level_seconds = t_level;
         stats->recompute_seconds = t_rec;
-        stats->scan_launches = o.timing ? live_iters : 0;
-        stats->push_launches = o.timing ? live_iters : 0;
+        stats->level_launches = o.timing ? live_iters : 0;
         stats->recompute_launches = st.recomputes;
         stats->body_iterations = st.body_iters;
     }
@@ -633,9 +1261,9 @@ extern "C" DI_API di_status di_frontier(di_graph *g, const void *F, int fluid_fp
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.st, ws.st_h, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     if (fluid_fp64)
-        k_scan<double><<<g->grid_scan, kScanThreads, 0, s>>>(ws.desc, ws.st, list, g->n, ws.part_sum, ws.part_max, 0, 0, 0);
+        k_scan<double><<<g->grid_scan, kScanThreads, 0, s>>>(ws.desc, ws.st, list, g->n, ws.part_sum, ws.part_max);
     else
-        k_scan<float><<<g->grid_scan, kScanThreads, 0, s>>>(ws.desc, ws.st, list, g->n, ws.part_sum, ws.part_max, 0, 0, 0);
+        k_scan<float><<<g->grid_scan, kScanThreads, 0, s>>>(ws.desc, ws.st, list, g->n, ws.part_sum, ws.part_max);
     DI_CUDA_TRY(cudaGetLastError());
     DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     DI_CUDA_TRY(cudaStreamSynchronize(s));
