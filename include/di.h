@@ -203,6 +203,46 @@ DI_API di_status di_frontier(di_graph *g, const void *F, int fluid_fp64, double 
 DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double d, const double *H,
                                      double *F, double *r_l1, void *stream);
 
+/*
+ * Batched solves (many right-hand sides of many graphs in one level loop).
+ * Work item t is right-hand side r of graph g, numbered graph-major: the
+ * items of graphs[0] first (r = 0 .. nrhs[0]-1), then those of graphs[1] ...
+ * Every item is an independent D-iteration (Eqs. defF/defH) with its own
+ * threshold schedule (Sec. 2.4) and its own stop rule.  di_batch_create lays
+ * the items side by side in one device-resident union graph (one copy of
+ * graph g per right-hand side, each starting on a multiple of 2048 nodes), so
+ * all items advance together in the same kernel launches.  The graphs must
+ * live on the current device; they are copied (the batch does not reference
+ * them afterwards).  The union must stay below 2^31 nodes and 2^31 edges.
+ * stream: cudaStream_t or NULL.  Synchronous.
+ */
+typedef struct di_batch di_batch;
+
+DI_API di_status di_batch_create(const di_graph *const *graphs, int ng, const int *nrhs, void *stream,
+                                 di_batch **out);
+
+/* Frees a batch and all its device memory (NULL is a no-op). */
+DI_API void di_batch_destroy(di_batch *b);
+
+/* Items, union nodes (chunk-aligned) and union edges; outputs may be NULL. */
+DI_API di_status di_batch_info(const di_batch *b, int *n_items, int64_t *n_union, int64_t *nnz_union);
+
+/*
+ * Solves every item of the batch: B[t], H[t] are device pointers of n_g
+ * doubles (host array of n_items pointers); tol[t] > 0 is item t's absolute
+ * L1 tolerance on |B + P H - H|_1 (host array).  d in (0, 1).  opts as for
+ * di_solve (warm_start must be 0; timing = 1 runs the levels host-driven).
+ * item_stats (host array of n_items, may be NULL) receives each item's
+ * statistics; total (may be NULL) the sums (levels = max over items,
+ * gpu_launches and seconds of the whole call).  Returns DI_OK when every
+ * item converged, DI_ENOCONV when at least one reached the level cap (its H
+ * and statistics are still valid), DI_ENONFINITE, DI_EINVAL, DI_ENOMEM or
+ * DI_ECUDA.  Synchronous on opts->stream.
+ */
+DI_API di_status di_solve_batched(di_batch *b, const double *const *B, double d, const double *tol,
+                                  double *const *H, const di_opts *opts, di_stats *item_stats,
+                                  di_stats *total);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ CU_SOURCES = [
     "solve.cu",
     "residual.cu",
     "noalloc.cu",
+    "batch.cu",
 ]
 
 

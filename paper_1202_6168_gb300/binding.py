@@ -66,6 +66,11 @@ SIGNATURES = {
     "di_frontier": (c_int, [c_vp, c_vp, c_int, c_dbl, c_vp, ctypes.POINTER(c_i64),
                             ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
     "di_residual_noalloc": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
+    "di_batch_create": (c_int, [c_vp, c_int, c_vp, c_vp, ctypes.POINTER(c_vp)]),
+    "di_batch_destroy": (None, [c_vp]),
+    "di_batch_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "di_solve_batched": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts),
+                                 ctypes.POINTER(di_stats), ctypes.POINTER(di_stats)]),
 }
 
 
@@ -196,6 +201,59 @@ def di_residual_noalloc(graph: Graph, B, d: float, H, F, stream=None) -> float:
     check(lib().di_residual_noalloc(graph.handle, _ptr(B), d, _ptr(H), _ptr(F), ctypes.byref(r),
                                     _stream(stream)))
     return r.value
+
+
+class Batch:
+    """Owner of a ``di_batch`` handle: work item t is right-hand side r of
+    graph g, numbered graph-major (all items of graphs[0] first)."""
+
+    def __init__(self, graphs, nrhs, stream=None):
+        self.graphs = list(graphs)
+        self.nrhs = [int(r) for r in nrhs]
+        if len(self.graphs) != len(self.nrhs):
+            raise ValueError("one nrhs per graph")
+        handles = (c_vp * len(self.graphs))(*[g.handle for g in self.graphs])
+        counts = (c_int * len(self.nrhs))(*self.nrhs)
+        h = c_vp()
+        check(lib().di_batch_create(handles, len(self.graphs), counts, _stream(stream), ctypes.byref(h)))
+        self.handle = h.value
+        self.sizes = [g.n for g, r in zip(self.graphs, self.nrhs) for _ in range(r)]
+
+    def info(self) -> dict:
+        ni, nu, eu = c_int(), c_i64(), c_i64()
+        check(lib().di_batch_info(self.handle, ctypes.byref(ni), ctypes.byref(nu), ctypes.byref(eu)))
+        return {"n_items": ni.value, "n_union": nu.value, "nnz_union": eu.value}
+
+    def close(self) -> None:
+        if self.handle:
+            lib().di_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def di_solve_batched(batch: Batch, B: list, d: float, tol, H: list, opts: di_opts | None = None,
+                     allow=(DI_OK,)) -> tuple[int, list, di_stats]:
+    """Solves every item; B and H are lists of device buffers (one per item),
+    tol a scalar or one tolerance per item.  Returns (status, per-item
+    stats, total stats)."""
+    ni = len(batch.sizes)
+    if len(B) != ni or len(H) != ni:
+        raise ValueError(f"need {ni} B and H buffers")
+    tols = [float(tol)] * ni if isinstance(tol, (int, float)) else [float(t) for t in tol]
+    bp = (c_vp * ni)(*[_ptr(x) for x in B])
+    hp = (c_vp * ni)(*[_ptr(x) for x in H])
+    tp = (c_dbl * ni)(*tols)
+    items = (di_stats * ni)()
+    tot = di_stats()
+    rc = lib().di_solve_batched(batch.handle, bp, d, tp, hp,
+                                ctypes.byref(opts) if opts is not None else None, items, ctypes.byref(tot))
+    check(rc, allow)
+    return rc, list(items), tot
 
 
 def di_frontier(graph: Graph, F, fluid_fp64: bool, T: float, out_list, stream=None) -> tuple[int, float, float]:
