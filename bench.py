@@ -5,7 +5,7 @@ One step = one complete solve of X = P X + B (PageRank form, d = 0.85) by the
 threshold-frontier D-iteration, from F = B to the exact FP64 stop
 |B + P H - H|_1 <= 1e-8 |B|_1, on a seeded synthetic web-like graph.
 Metric: edge diffusions per second (the paper's elementary cost unit,
-Sec. 2.5) and time to tolerance.
+Sec. 2.4) and time to tolerance.
 
 Default workload: N = 1,000,000 nodes, mean out-degree 10 (non-dangling),
 10% dangling, +-64 locality window, FP32 fluid with FP64 history, exact
@@ -42,6 +42,8 @@ WORKLOADS = {
     "web-1m": (gg.WEB_1M, "web-like N=1e6, m=10, +-64 window, seed 0"),
     "stress-16m": (gg.STRESS_16M, "web-like N=2^24, m=16, +-256 window, seed 0"),
     "web-10k": (gg.SMALL_10K, "web-like N=1e4, m=8, +-64 window, seed 0"),
+    "warmstart": (None, "learned warm start: trained on seeded web-like graphs (N log-uniform in [1e5, 1e6], "
+                        "m=10, seeds 1000..), evaluated on held-out N=3e6, m=10 graphs (seeds 2000..)"),
     "batch-64x4": (None, "64 web-like graphs, N log-uniform in [1e4, 2e6], m ~ U[6, 14], seeds 0..63; "
                          "4 personalised right-hand sides each (B = 0.15 e_s), 256 solves per step"),
 }
@@ -61,12 +63,19 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="web-1m")
     p.add_argument("--fp64", action="store_true", help="FP64 fluid instead of FP32")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, roofline and CPU baseline legs")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the oracle check only")
     p.add_argument("--alpha", type=float, default=None, help="threshold decay (library default if unset)")
     p.add_argument("--recompute-every", type=int, default=None, help="exact FP64 residual period (levels)")
     p.add_argument("--no-l2-window", action="store_true", help="no L2 access-policy windows")
     p.add_argument("--propagation", type=int, default=None,
-                   help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push")
+                   help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push, "
+                        "4 asynchronous push with warp-level tiles")
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
+    p.add_argument("--exact-residual", type=int, default=None,
+                   help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
+    p.add_argument("--ws-train", type=int, default=200, help="warm start: training graphs")
+    p.add_argument("--ws-eval", type=int, default=32, help="warm start: held-out evaluation graphs")
+    p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
     p.add_argument("--host-loop", action="store_true",
                    help="host-driven levels with per-kernel events (profilers cannot see kernels in "
                         "graphs with conditional nodes)")
@@ -162,6 +171,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     spec, desc = WORKLOADS[args.workload]
+    if spec is None:
+        run_reference_multi(args, desc)
+        return
     rp, col = gg.generate(spec)
     b = gg.uniform_b(spec.n, D)
     tol = 1e-8 * b.sum()
@@ -186,6 +198,40 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_reference_multi(args, desc):
+    """Reference arm of the batched and warm-start workloads: the oracle's cold
+    solves of a bounded sample of their items, on one host core."""
+    from oracle import diter as od
+    if args.workload == "batch-64x4":
+        specs, csrs, rhs = batch_inputs()
+        order = sorted(range(len(specs)), key=lambda g: specs[g].n)
+        items = [(csrs[gi], gg.personalised_b(specs[gi].n, src, D)) for gi in order for (g2, src) in rhs if g2 == gi]
+        sample = "items of the smallest graphs"
+    else:
+        sp = gg.warmstart_specs("eval", 1)[0]
+        items = [(gg.generate(sp), gg.uniform_b(sp.n, D))]
+        sample = "the cold solve of one held-out N=3e6 graph"
+    edges, secs, done = 0, 0.0, 0
+    for step in range(args.warmup + args.steps):
+        for (rp, col), b in items[:max(1, len(items) // 8)]:
+            t0 = time.perf_counter()
+            r = od.d_iteration(rp, col, b, D, tol=1e-8 * b.sum())
+            if step >= args.warmup:
+                secs += time.perf_counter() - t0
+                edges += r.edge_diffusions
+                done += 1
+    value = edges / secs
+    print(json.dumps({"impl": "reference", "metric": "edge_diffusions_per_s", "value": value,
+                      "unit": "edge_diffusions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "oracle": "sequential cyclic-threshold D-iteration, FP64, 1 core"},
+                      "cpu_baseline": {"value": value, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"{done} solves: {sample}"},
+                      "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_native(args, world, rank, local):
@@ -213,6 +259,8 @@ def run_native(args, world, rank, local):
         opts.propagation = args.propagation
     if args.push_ratio is not None:
         opts.push_ratio = args.push_ratio
+    if args.exact_residual is not None:
+        opts.exact_residual = args.exact_residual
 
     g = di.Graph.create(rp, col, stream=stream)
     B = torch.from_numpy(b).cuda()
@@ -266,7 +314,7 @@ def run_native(args, world, rank, local):
         topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
                                alpha=opts.alpha, recompute_every=opts.recompute_every,
                                l2_window=opts.l2_window, propagation=opts.propagation,
-                               push_ratio=opts.push_ratio)
+                               push_ratio=opts.push_ratio, exact_residual=opts.exact_residual)
         te = tn = 0
         tpush = trec = 0.0
         npush = 0
@@ -318,13 +366,15 @@ def run_native(args, world, rank, local):
                          "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                          "ms_per_step": 1e3 * e_secs / args.steps,
                          "api": "di_solve_host (pinned host B in, H out; graph resident)"}
-        # error of the result against the exact residual bound, and the CPU oracle
-        h = H.cpu().numpy()
-        from oracle import diter as od
-        _, r_cpu = od.residual(rp, col, b, D, h)
-        extras["check"] = {"resid_l1_oracle_fp64": r_cpu, "tol": tol, "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
-                           "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
-        extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol)
+        if not args.no_cpu:
+            # error of the result against the exact residual bound, and the CPU oracle
+            h = H.cpu().numpy()
+            from oracle import diter as od
+            _, r_cpu = od.residual(rp, col, b, D, h)
+            extras["check"] = {"resid_l1_oracle_fp64": r_cpu, "tol": tol,
+                               "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
+                               "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
+            extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol)
 
     if rank == 0:
         info = g.info()
@@ -338,8 +388,10 @@ def run_native(args, world, rank, local):
                            "alpha": opts.alpha, "l2": "flushed (256 MiB write) before each timed step",
                            "l2_window": bool(opts.l2_window),
                            "propagation": ["auto: binned gather / push", "auto: flat gather / push",
-                                           "push only", "asynchronous push"][opts.propagation],
+                                           "push only", "asynchronous push",
+                                           "asynchronous push, warp-level tiles"][opts.propagation],
                            "push_ratio": opts.push_ratio,
+                           "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
                            "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "time_to_tol_ms": 1e3 * secs_max / args.steps,
@@ -477,10 +529,100 @@ def run_batch(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_warmstart(args, world, rank, local):
+    """Time to |F|_1 <= 1e-8 |B|_1 with the learned warm start (features, network,
+    F0 and the solve, all timed) against the zero start, on held-out graphs."""
+    import torch
+    from paper_1202_6168_gb300 import binding as di
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    graphs, Bs, Xs = [], [], []
+    train_nodes = 0
+    for sp in gg.warmstart_specs("train", args.ws_train):
+        rp, col = gg.generate(sp)
+        g = di.Graph.create(rp, col, stream=stream)
+        b = torch.full((sp.n,), (1.0 - D) / sp.n, dtype=torch.float64, device="cuda")
+        h = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+        di.di_solve(g, b, D, 1e-8 * (1.0 - D), h, None, di.opts_default(stream=stream.cuda_stream))
+        graphs.append(g)
+        Bs.append(b)
+        Xs.append(h)
+        train_nodes += sp.n
+    t_gen = time.perf_counter() - t_gen
+    model = di.Model.create(7)
+    t0 = time.perf_counter()
+    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=args.ws_epochs, batch=65536, lr=1e-3,
+                                                             stream=stream.cuda_stream))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for g in graphs:
+        g.close()
+    del Bs, Xs
+    rows = []
+    opts_c = di.opts_default(stream=stream.cuda_stream)
+    opts_w = di.opts_default(stream=stream.cuda_stream, warm_start=1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for sp in gg.warmstart_specs("eval", args.ws_eval):
+        rp, col = gg.generate(sp)
+        g = di.Graph.create(rp, col, stream=stream)
+        n = sp.n
+        b = torch.full((n,), (1.0 - D) / n, dtype=torch.float64, device="cuda")
+        tol = 1e-8 * (1.0 - D)
+        H = torch.zeros(n, dtype=torch.float64, device="cuda")
+        res = {}
+        for label in ("cold", "warm"):
+            times = []
+            for rep in range(max(args.warmup, 1) + max(args.steps, 1)):
+                flush.zero_()
+                if label == "cold":
+                    ev[0].record(stream)
+                    _, st = di.di_solve(g, b, D, tol, H, None, opts_c)
+                    ev[1].record(stream)
+                else:
+                    ev[0].record(stream)
+                    model.infer(g, b, H, stream)
+                    _, st = di.di_solve(g, b, D, tol, H, None, opts_w)
+                    ev[1].record(stream)
+                torch.cuda.synchronize()
+                if rep >= max(args.warmup, 1):
+                    times.append(ev[0].elapsed_time(ev[1]))
+            res[label] = {"ms": statistics.median(times), "edges": st.edge_diffusions, "levels": st.levels,
+                          "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1, "resid": st.resid_l1}
+        rows.append(res)
+        g.close()
+    cold = [r["cold"]["ms"] for r in rows]
+    warm = [r["warm"]["ms"] for r in rows]
+    line = {"metric": "time_to_tol_ms", "value": statistics.mean(warm), "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(warm),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["warmstart"][1], "train_graphs": args.ws_train,
+                       "train_nodes": train_nodes, "eval_graphs": args.ws_eval, "epochs": args.ws_epochs,
+                       "tol": "1e-8 |B|_1", "timed": "warm: features + network + F0 + solve; cold: solve",
+                       "l2": "flushed (256 MiB write) before each timed solve"},
+            "cold_ms": statistics.mean(cold), "warm_ms": statistics.mean(warm),
+            "speedup": statistics.mean(cold) / statistics.mean(warm),
+            "warm_used": sum(r["warm"]["warm_used"] for r in rows),
+            "f0_over_b_mean": statistics.mean(r["warm"]["f0_over_b"] for r in rows),
+            "edges_cold": statistics.mean(r["cold"]["edges"] for r in rows),
+            "edges_warm": statistics.mean(r["warm"]["edges"] for r in rows),
+            "levels_cold": statistics.mean(r["cold"]["levels"] for r in rows),
+            "levels_warm": statistics.mean(r["warm"]["levels"] for r in rows),
+            "train": {"loss_last_epoch": loss, "seconds": t_train, "generate_and_solve_s": t_gen},
+            "per_graph": rows}
+    print(json.dumps(line), flush=True)
+    model.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
-    if args.workload == "batch-64x4" and args.impl != "reference":
+    if args.workload == "warmstart" and args.impl != "reference":
+        if rank == 0:
+            run_warmstart(args, world, rank, local)
+    elif args.workload == "batch-64x4" and args.impl != "reference":
         run_batch(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

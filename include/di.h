@@ -60,7 +60,8 @@ typedef struct {
     int recompute_every;   /* FP32 fluid: exact FP64 residual F = B + P H - H every this
                               many levels; 0 = only to confirm the stop.  default 8 */
     int max_levels;        /* level cap -> DI_ENOCONV; default 100000 */
-    int warm_start;        /* 1: H holds H0 on entry and F0 = B + P H0 - H0 */
+    int warm_start;        /* 1: H holds H0 on entry and F0 = B + P H0 - H0; the first
+                              threshold is then |F0|_1 / N (a cold start uses max |F0|) */
     int warm_fallback;     /* with warm_start: fall back to H0 = 0 when |F0|_1 > |B|_1 */
     int l2_window;         /* 1: keep the fluid vector L2-resident (access-policy window) */
     int timing;            /* 1: run the levels host-driven with a CUDA event around every
@@ -71,9 +72,16 @@ typedef struct {
                               ones; 1 the same with a flat edge-parallel gather; 2 always
                               scatter.  3 (default): asynchronous push - each frontier node
                               is drained with an atomic exchange when its row is pushed, so
-                              fluid arriving earlier in the level goes with it */
+                              fluid arriving earlier in the level goes with it; 4: the same
+                              asynchronous push with warp-level tiles (each warp drains 32
+                              frontier nodes at a time; no block-wide barrier) */
     int push_ratio;        /* auto: a level is dense (gather) when its active edges times
                               push_ratio reach the edge count; default 8 */
+    int exact_residual;    /* form of the exact FP64 residual B + P H - H: 1 gather over the
+                              in-rows binned by length (no atomics, fixed summation order);
+                              2 in-edges in source-blocked order (blocks of 2^22 sources,
+                              so the gathered H stays in L2), runs added with FP64 reds;
+                              0 (default) = 2 */
     long long spin_limit;  /* iteration limit of every bounded device wait */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
 } di_opts;
@@ -83,7 +91,7 @@ typedef struct {
     int32_t levels;            /* threshold levels with a non-empty frontier */
     int32_t recomputes;        /* exact FP64 residual recomputations */
     int64_t node_diffusions;   /* nodes diffused (F_i moved into H_i) */
-    int64_t edge_diffusions;   /* elementary node-to-node diffusions (Sec. 2.5 cost) */
+    int64_t edge_diffusions;   /* elementary node-to-node diffusions (Sec. 2.4 cost) */
     double resid_l1;           /* final |B + P H - H|_1, recomputed exactly in FP64 */
     double err_bound;          /* resid_l1 / (1 - d): bound on |X - H|_1 */
     double b_l1;               /* |B|_1 */
@@ -109,7 +117,7 @@ DI_API const char *di_last_error(void);
 
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 8, max_levels 100000,
  * cold start (fallback on when warm), L2 window on, timing off,
- * propagation 3, push_ratio 8, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+ * propagation 3, push_ratio 8, exact_residual 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*
@@ -242,6 +250,91 @@ DI_API di_status di_batch_info(const di_batch *b, int *n_items, int64_t *n_union
 DI_API di_status di_solve_batched(di_batch *b, const double *const *B, double d, const double *tol,
                                   double *const *H, const di_opts *opts, di_stats *item_stats,
                                   di_stats *total);
+
+/*
+ * Learned warm start.  The paper starts from H_0 = 0 (F_0 = B); any H_0 is
+ * as valid (F_0 = B + P H_0 - H_0 keeps the invariant of Eqs. defF/defH and
+ * the bound |X - H|_1 <= |F|_1 / (1 - d)), so a good guess of X can shorten
+ * the solve.  A small network predicts y_i = log(N x_i) from per-node
+ * features and H0_i = exp(y_i) / N is handed to di_solve with
+ * opts.warm_start = 1 (and warm_fallback = 1: H0 is dropped when
+ * |F0|_1 > |B|_1).
+ *
+ * Features (DI_MODEL_NFEAT per node, float, row-major [n][9]): for node i
+ * with in-degree m_i, out-degree o_i (edges with multiplicity), ld = log(1+m)
+ * and s = 1/o (0 if dangling):
+ *   x0 = ld_i, x1 = log(1 + o_i), x2/x3 = mean/max of ld_j over the in-edges
+ *   j -> i, x4/x5 = mean of x2_j / max of x3_j over the in-edges,
+ *   x6 = log(1 + sum s_j), x7 = log(1 + sum s_j a1_j) (a1_j = sum over j's
+ *   in-edges of s), x8 = N B_i; empty means, maxima and sums are 0.
+ * Network: standardise (x - mu) / sd, then 9 -> 64 -> 64 -> 1 with ReLU
+ * (BF16 tensor-core operands, FP32 accumulation), y = w3 . h2 + b3.
+ * Parameters (DI_MODEL_NPARAM floats): W1 [64][16] (input columns 9..15 are
+ * zero padding), b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1].  The model
+ * "state" is mu [9], sd [9], then the parameters (DI_MODEL_STATE floats).
+ */
+#define DI_MODEL_NFEAT 9
+#define DI_MODEL_NPARAM 5313
+#define DI_MODEL_STATE (2 * DI_MODEL_NFEAT + DI_MODEL_NPARAM)
+
+typedef struct di_model di_model;
+
+typedef struct {
+    int epochs;        /* passes over the training nodes (default 4) */
+    int batch;         /* nodes per Adam step, drawn with replacement (default 65536) */
+    double lr, beta1, beta2, eps;   /* Adam (defaults 1e-3, 0.9, 0.999, 1e-8) */
+    uint64_t seed;     /* minibatch sampling (default 1) */
+    void *stream;      /* cudaStream_t or NULL */
+} di_train_opts;
+
+DI_API di_status di_train_opts_default(di_train_opts *o);
+
+/* New model on the current device: uniform He initialisation from seed
+ * (SplitMix64), zero biases, identity standardisation (mu 0, sd 1). */
+DI_API di_status di_model_create(uint64_t seed, di_model **out);
+
+/* Frees a model (NULL is a no-op). */
+DI_API void di_model_destroy(di_model *m);
+
+/* Copies the model state (host array of DI_MODEL_STATE floats) out / in.
+ * di_model_set rejects sd <= 0 or a non-finite mu with DI_EINVAL. */
+DI_API di_status di_model_get(const di_model *m, float *state);
+DI_API di_status di_model_set(di_model *m, const float *state);
+
+/* Features of every node of g (device B of n doubles) into the device array
+ * feat ([n][9] floats).  Asynchronous on stream. */
+DI_API di_status di_features(di_model *m, di_graph *g, const double *B, float *feat, void *stream);
+
+/* Network prediction y (device, n floats) for n feature rows (device
+ * [n][9]).  Asynchronous on stream. */
+DI_API di_status di_mlp_forward(const di_model *m, const float *feat, int64_t n, float *y, void *stream);
+
+/* Mean squared error (1/n) sum (y_i - target_i)^2 over the n rows (device
+ * feat [n][9], device target [n]) and its gradient with respect to the
+ * parameters (host, DI_MODEL_NPARAM floats).  Synchronous. */
+DI_API di_status di_mlp_grad(di_model *m, const float *feat, const float *target, int64_t n, float *grad,
+                             double *loss, void *stream);
+
+/* One Adam step with the gradient grad (host, DI_MODEL_NPARAM floats),
+ * bias-corrected with the model's step count.  Synchronous. */
+DI_API di_status di_model_adam(di_model *m, const float *grad, const di_train_opts *opts);
+
+/* Trains m on ng graphs with right-hand sides B[g] and converged solutions
+ * X[g] (device pointers of n_g doubles, e.g. H from di_solve): features,
+ * target log(N x_i), standardisation statistics of the training features
+ * (set into the model), then epochs of Adam steps on minibatches drawn over
+ * all training nodes.  *final_loss (may be NULL) receives the mean squared
+ * error over the last epoch.  Synchronous. */
+DI_API di_status di_warmstart_train(di_model *m, di_graph *const *graphs, int ng, const double *const *B,
+                                    const double *const *X, const di_train_opts *opts, double *final_loss);
+
+/* H0 = exp(y) / N for every node of g (device H0, n doubles) from the
+ * features of g and B (device).  Asynchronous on stream. */
+DI_API di_status di_warmstart_infer(di_model *m, di_graph *g, const double *B, double *H0, void *stream);
+
+/* Model file: header, step, state, Adam moments (little-endian floats). */
+DI_API di_status di_warmstart_save(const di_model *m, const char *path);
+DI_API di_status di_warmstart_load(const char *path, di_model **out);
 
 #ifdef __cplusplus
 }

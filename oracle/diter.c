@@ -37,7 +37,7 @@
 typedef struct {
     int64_t levels;           /* non-empty sweeps performed */
     int64_t node_diffusions;  /* nodes diffused */
-    int64_t edge_diffusions;  /* elementary node-to-node diffusions (Sec. 2.5) */
+    int64_t edge_diffusions;  /* elementary node-to-node diffusions (Sec. 2.4) */
     double resid_l1;          /* sum |F_i| at return */
     double threshold;         /* T at return */
 } oracle_stats;

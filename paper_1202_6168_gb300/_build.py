@@ -36,6 +36,7 @@ CU_SOURCES = [
     "residual.cu",
     "noalloc.cu",
     "batch.cu",
+    "warmstart.cu",
 ]
 
 

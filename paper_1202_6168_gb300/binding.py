@@ -24,9 +24,14 @@ STATUS_NAMES = {0: "DI_OK", 1: "DI_EINVAL", 2: "DI_ENOMEM", 3: "DI_ECUDA", 4: "D
 class di_opts(ctypes.Structure):
     _fields_ = [("alpha", c_dbl), ("fluid_fp64", c_int), ("recompute_every", c_int),
                 ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
-                ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int),
+                ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int), ("exact_residual", c_int),
                 ("spin_limit", ctypes.c_longlong),
                 ("stream", c_vp)]
+
+
+class di_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", c_int), ("batch", c_int), ("lr", c_dbl), ("beta1", c_dbl), ("beta2", c_dbl),
+                ("eps", c_dbl), ("seed", ctypes.c_uint64), ("stream", c_vp)]
 
 
 class di_stats(ctypes.Structure):
@@ -66,6 +71,20 @@ SIGNATURES = {
     "di_frontier": (c_int, [c_vp, c_vp, c_int, c_dbl, c_vp, ctypes.POINTER(c_i64),
                             ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
     "di_residual_noalloc": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
+    "di_train_opts_default": (c_int, [ctypes.POINTER(di_train_opts)]),
+    "di_model_create": (c_int, [ctypes.c_uint64, ctypes.POINTER(c_vp)]),
+    "di_model_destroy": (None, [c_vp]),
+    "di_model_get": (c_int, [c_vp, c_vp]),
+    "di_model_set": (c_int, [c_vp, c_vp]),
+    "di_features": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "di_mlp_forward": (c_int, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "di_mlp_grad": (c_int, [c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_dbl), c_vp]),
+    "di_model_adam": (c_int, [c_vp, c_vp, ctypes.POINTER(di_train_opts)]),
+    "di_warmstart_train": (c_int, [c_vp, c_vp, c_int, c_vp, c_vp, ctypes.POINTER(di_train_opts),
+                                   ctypes.POINTER(c_dbl)]),
+    "di_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "di_warmstart_save": (c_int, [c_vp, ctypes.c_char_p]),
+    "di_warmstart_load": (c_int, [ctypes.c_char_p, ctypes.POINTER(c_vp)]),
     "di_batch_create": (c_int, [c_vp, c_int, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "di_batch_destroy": (None, [c_vp]),
     "di_batch_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
@@ -254,6 +273,97 @@ def di_solve_batched(batch: Batch, B: list, d: float, tol, H: list, opts: di_opt
                                 ctypes.byref(opts) if opts is not None else None, items, ctypes.byref(tot))
     check(rc, allow)
     return rc, list(items), tot
+
+
+MODEL_NFEAT = 9
+MODEL_NPARAM = 5313
+MODEL_STATE = 2 * MODEL_NFEAT + MODEL_NPARAM
+
+
+def train_opts_default(**overrides) -> di_train_opts:
+    o = di_train_opts()
+    check(lib().di_train_opts_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Model:
+    """Owner of a ``di_model`` handle (the learned warm start)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @classmethod
+    def create(cls, seed: int = 1) -> "Model":
+        h = c_vp()
+        check(lib().di_model_create(seed, ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def load(cls, path: str) -> "Model":
+        h = c_vp()
+        check(lib().di_warmstart_load(path.encode(), ctypes.byref(h)))
+        return cls(h.value)
+
+    def save(self, path: str) -> None:
+        check(lib().di_warmstart_save(self.handle, path.encode()))
+
+    def get_state(self):
+        import numpy as np
+        st = np.zeros(MODEL_STATE, dtype=np.float32)
+        check(lib().di_model_get(self.handle, st.ctypes.data))
+        return st
+
+    def set_state(self, state) -> None:
+        import numpy as np
+        st = np.ascontiguousarray(state, dtype=np.float32)
+        if st.shape != (MODEL_STATE,):
+            raise ValueError(f"state must have {MODEL_STATE} floats")
+        check(lib().di_model_set(self.handle, st.ctypes.data))
+
+    def features(self, graph: "Graph", B, feat, stream=None) -> None:
+        check(lib().di_features(self.handle, graph.handle, _ptr(B), _ptr(feat), _stream(stream)))
+
+    def forward(self, feat, n: int, y, stream=None) -> None:
+        check(lib().di_mlp_forward(self.handle, _ptr(feat), n, _ptr(y), _stream(stream)))
+
+    def grad(self, feat, target, n: int, stream=None):
+        import numpy as np
+        g = np.zeros(MODEL_NPARAM, dtype=np.float32)
+        loss = c_dbl()
+        check(lib().di_mlp_grad(self.handle, _ptr(feat), _ptr(target), n, g.ctypes.data, ctypes.byref(loss),
+                                _stream(stream)))
+        return loss.value, g
+
+    def adam(self, grad, opts: di_train_opts | None = None) -> None:
+        import numpy as np
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        check(lib().di_model_adam(self.handle, g.ctypes.data, ctypes.byref(opts) if opts is not None else None))
+
+    def train(self, graphs: list, B: list, X: list, opts: di_train_opts | None = None) -> float:
+        ng = len(graphs)
+        gp = (c_vp * ng)(*[g.handle for g in graphs])
+        bp = (c_vp * ng)(*[_ptr(b) for b in B])
+        xp = (c_vp * ng)(*[_ptr(x) for x in X])
+        loss = c_dbl()
+        check(lib().di_warmstart_train(self.handle, gp, ng, bp, xp,
+                                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(loss)))
+        return loss.value
+
+    def infer(self, graph: "Graph", B, H0, stream=None) -> None:
+        check(lib().di_warmstart_infer(self.handle, graph.handle, _ptr(B), _ptr(H0), _stream(stream)))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().di_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def di_frontier(graph: Graph, F, fluid_fp64: bool, T: float, out_list, stream=None) -> tuple[int, float, float]:

@@ -38,6 +38,7 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->timing = 0;
     o->propagation = 3;
     o->push_ratio = 8;
+    o->exact_residual = 0;
     o->spin_limit = 1LL << 26;
     o->stream = nullptr;
     return DI_OK;

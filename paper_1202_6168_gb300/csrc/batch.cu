@@ -324,8 +324,9 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
     double *__restrict__ H = desc->H;
     const int lane = threadIdx.x & 31;
     for (int sl = threadIdx.x; sl < n_hot; sl += kBThreads) s_hot[sl] = FT(0);
+    const uint64_t keep = l2_keep_policy();
     auto push1 = [&](int32_t c, FT w) {
-        if (c >= 0) red_add(F + c, w);
+        if (c >= 0) red_add_keep(F + c, w, keep);
         else atomicAdd(&s_hot[-1 - c], w);
     };
     for (;;) {
@@ -340,18 +341,18 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
         int32_t b = 0, e = 0;
         FT w = FT(0);
         if (idx < count) {
-            const int32_t i = front[idx];
+            const int32_t i = __ldcs(front + idx);
             if (items[item_of_chunk[i >> kBChunkShift]].push) {
-                b = rp[i];
-                e = rp[i + 1];
-                const FT f = atomic_exch_fluid(F + i, FT(0));
-                H[i] += static_cast<double>(f);
-                w = f * scale[i];
+                b = __ldcs(rp + i);
+                e = __ldcs(rp + i + 1);
+                const FT f = atomic_exch_keep(F + i, FT(0), keep);
+                __stcs(H + i, __ldcs(H + i) + static_cast<double>(f));
+                w = f * __ldcs(scale + i);
             }
         }
         const int deg = e - b;
         if (deg <= kThreadMaxDeg) {
-            for (int32_t q = b; q < e; ++q) push1(pcol[q], w);
+            for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
         }
         unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg && deg <= kWarpMaxDeg);
         while (wm) {
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
             wm &= wm - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const FT mw = __shfl_sync(0xffffffffu, w, src);
-            for (int32_t q = mb + lane; q < me; q += 32) push1(pcol[q], mw);
+            for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
         }
         if (deg > kWarpMaxDeg) {
             const int slot = atomicAdd(&s_qn, 1);
@@ -372,14 +373,14 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
         for (int h = 0; h < qn; ++h) {
             const int32_t hb = s_qb[h], he = s_qe[h];
             const FT hw = s_qw[h];
-            for (int32_t q = hb + threadIdx.x; q < he; q += kBThreads) push1(pcol[q], hw);
+            for (int32_t q = hb + threadIdx.x; q < he; q += kBThreads) push1(__ldcs(pcol + q), hw);
         }
         __syncthreads();
     }
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kBThreads) {
         const FT v = s_hot[sl];
-        if (v != FT(0)) red_add(F + hot_node[sl], v);
+        if (v != FT(0)) red_add_keep(F + hot_node[sl], v, keep);
     }
 }
 

@@ -44,6 +44,7 @@ constexpr int kResSeg = 8192;       // in-rows longer than this are split in seg
 constexpr int kResFine = 256;       // segment length of the exact residual's long in-rows
 constexpr int kMaxHot = 2048;       // privatised hot targets (shared-memory slots)
 constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
+constexpr int kSrcBlockShift = 22;  // exact residual: sources in blocks of 2^22 nodes (32 MB of FP64 gathers)
 
 // ------------------------------------------------------------------ solver state
 
@@ -62,6 +63,7 @@ struct SolveDesc {
     int max_body_iters;   // absolute cap on loop iterations (safety net)
     int propagation;      // 0/1 auto (binned/flat gather for dense levels), 2 push only, 3 async push
     int push_ratio;       // dense when active edges * push_ratio >= edges
+    int64_t n_nodes;
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -113,6 +115,7 @@ struct SolverGraph {
     bool built = false;
     int l2 = 0;           // built with the L2 window
     int prop = 0;         // built with this propagation option
+    int res_form = 0;     // built with this exact-residual form
 };
 
 struct Workspace {
@@ -123,6 +126,7 @@ struct Workspace {
     double *w64 = nullptr;
     int32_t *front = nullptr;      // frontier list [n]
     double *g = nullptr;           // s_j H_j for the exact residual [n]
+    double *acc = nullptr;         // exact residual accumulator of the source-blocked form [n]
     double *seg_part = nullptr;    // per-segment partial sums
     double *part_sum = nullptr;    // per-block partial sums
     double *part_max = nullptr;
@@ -163,6 +167,12 @@ struct di_graph {
     int32_t *pl_b12_off = nullptr, *pl_b12_col = nullptr;   // bins 1-2 edges in bin order
     int32_t *outdeg = nullptr;                            // [n] out-degrees
     int32_t *erow = nullptr;                              // [nnz] destination row of each in-edge
+    // in-edges in source-blocked order (source block of kSrcBlock nodes, then
+    // destination row): bcol = source, brow = destination.  With one block
+    // they alias in_col / erow.
+    int32_t *bcol = nullptr, *brow = nullptr;
+    int n_src_blocks = 1;
+    int res_form = 0;             // exact residual: 0 auto, 1 binned gather, 2 source-blocked flat gather
     int32_t *pl_lrows = nullptr, *pl_lseg0 = nullptr;   // rows of bin 5 and their first segment
     int pl_nlrows = 0;
     int64_t pl_bin_off[5] = {0, 0, 0, 0, 0};
@@ -190,6 +200,33 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 }
 __device__ __forceinline__ void red_add(double *addr, double v) {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(v) : "memory");
+}
+
+// L2 policy "evict last" for the fluid vector: the scatter target stays in
+// L2 while the column indices, offsets and histories stream past it.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void red_add_keep(float *addr, float v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(addr), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_keep(double *addr, double v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(addr), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float atomic_exch_keep(float *p, float v, uint64_t pol) {
+    uint32_t old;
+    asm volatile("atom.global.exch.L2::cache_hint.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "l"(p), "r"(__float_as_uint(v)), "l"(pol) : "memory");
+    return __uint_as_float(old);
+}
+__device__ __forceinline__ double atomic_exch_keep(double *p, double v, uint64_t pol) {
+    unsigned long long old;
+    asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
+                 : "=l"(old) : "l"(p), "l"(static_cast<unsigned long long>(__double_as_longlong(v))), "l"(pol)
+                 : "memory");
+    return __longlong_as_double(static_cast<long long>(old));
 }
 
 __device__ __forceinline__ float atomic_exch_fluid(float *p, float v) { return atomicExch(p, v); }

@@ -191,6 +191,41 @@ __global__ void k_erow(const int32_t *__restrict__ in_rp, int64_t n, int32_t *__
         for (int32_t q = in_rp[k]; q < in_rp[k + 1]; ++q) erow[q] = (int32_t)k;
 }
 
+// Source-blocked order of the in-edges: virtual row v = (j >> shift) * n + k
+// for the edge j -> k.  Count, then fill (order inside a virtual row is
+// arbitrary).
+__global__ void k_vcount(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, int shift,
+                         int32_t *__restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const int64_t vb = (j >> shift) * n;
+        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) atomicAdd(&cnt[vb + col[e]], 1);
+    }
+}
+
+__global__ void k_vfill(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, int shift,
+                        int32_t *__restrict__ cursor, int32_t *__restrict__ bcol, int32_t *__restrict__ brow) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const int64_t vb = (j >> shift) * n;
+        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) {
+            const int32_t k = col[e];
+            const int32_t pos = atomicAdd(&cursor[vb + k], 1);
+            bcol[pos] = static_cast<int32_t>(j);
+            brow[pos] = k;
+        }
+    }
+}
+
+// Hot-slot codes (-1 - slot) back to node ids.
+__global__ void k_decode_hot(int32_t *__restrict__ col, int64_t nnz, const int32_t *__restrict__ hot_node) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const int32_t c = col[e];
+        if (c < 0) col[e] = hot_node[-1 - c];
+    }
+}
+
 __global__ void k_outdeg(const int32_t *__restrict__ rp, int64_t n, int32_t *__restrict__ deg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) deg[i] = rp[i + 1] - rp[i];
@@ -239,11 +274,15 @@ void free_graph(di_graph *g) {
     void *dev[] = {g->rp, g->pcol, g->hot_node, g->in_rp, g->in_col, g->long_rows, g->long_seg0,
                    g->seg_row, g->seg_beg, g->frows, g->fseg0, g->fseg_row, g->fseg_beg,
                    g->pl_rows, g->pl_seg_row, g->pl_seg_beg, g->pl_lrows, g->pl_lseg0, g->pl_b12_off,
-                   g->pl_b12_col, g->outdeg, g->erow, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.w32, g->ws.w64, g->ws.front, g->ws.g,
+                   g->pl_b12_col, g->outdeg, g->erow, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.w32, g->ws.w64, g->ws.front, g->ws.g, g->ws.acc,
                    g->ws.seg_part, g->ws.part_sum, g->ws.part_max, g->ws.desc, g->ws.st,
                    g->ws.hostB, g->ws.hostH, g->ws.hostF};
     for (void *q : dev)
         if (q) cudaFree(q);
+    if (g->n_src_blocks > 1) {
+        if (g->bcol) cudaFree(g->bcol);
+        if (g->brow) cudaFree(g->brow);
+    }
     if (g->ws.desc_h) cudaFreeHost(g->ws.desc_h);
     if (g->ws.st_h) cudaFreeHost(g->ws.st_h);
     if (g->ws.ev0) cudaEventDestroy(g->ws.ev0);
@@ -506,7 +545,48 @@ extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_
     DI_CUDA_TRY(cudaStreamSynchronize(s));
     g->n_hot = nh;
 
-    // 7. segments of the long in-rows (exact residual load balance), two granularities
+    // 7. in-edges in source-blocked order for the exact residual (alias of the
+    //    in-CSR order when every source fits in one block)
+    g->n_src_blocks = (int)((n + (1LL << kSrcBlockShift) - 1) >> kSrcBlockShift);
+    if (g->n_src_blocks <= 1) {
+        g->bcol = g->in_col;
+        g->brow = g->erow;
+    } else if (nnz > 0) {
+        const int64_t nv = (int64_t)g->n_src_blocks * n;
+        if (nv + 1 > INT32_MAX) { set_error("di_graph_create: too many nodes for the blocked order"); return DI_EINVAL; }
+        int32_t *vcnt = nullptr, *voff = nullptr;
+        DI_CUDA_TRY(tmp.alloc(&vcnt, nv));
+        DI_CUDA_TRY(tmp.alloc(&voff, nv + 1));
+        DI_CUDA_TRY(cudaMemsetAsync(vcnt, 0, nv * sizeof(int32_t), s));
+        int32_t *dec = nullptr;   // targets with the hot-slot codes of pcol decoded
+        DI_CUDA_TRY(tmp.alloc(&dec, nnz));
+        DI_CUDA_TRY(cudaMemcpyAsync(dec, g->pcol, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        k_decode_hot<<<grid_for(nnz, kThreads, cap), kThreads, 0, s>>>(dec, nnz, g->hot_node);
+        k_vcount<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, dec, n, kSrcBlockShift, vcnt);
+        const int vchunks = static_cast<int>((nv + kScanChunkElems - 1) / kScanChunkElems);
+        int64_t *vchunk = nullptr;
+        DI_CUDA_TRY(tmp.alloc(&vchunk, vchunks));
+        k_chunk_sums<<<vchunks, kThreads, 0, s>>>(vcnt, nv, vchunk);
+        std::vector<int64_t> hv(vchunks);
+        DI_CUDA_TRY(cudaMemcpyAsync(hv.data(), vchunk, vchunks * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t vrun = 0;
+        for (int c = 0; c < vchunks; ++c) {
+            const int64_t v = hv[c];
+            hv[c] = vrun;
+            vrun += v;
+        }
+        if (vrun != nnz) { set_error("di_graph_create: blocked order counted %lld edges != nnz", (long long)vrun); return DI_ECUDA; }
+        DI_CUDA_TRY(cudaMemcpyAsync(vchunk, hv.data(), vchunks * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_chunk_scan<<<vchunks, kThreads, 0, s>>>(vcnt, nv, vchunk, voff);
+        DI_CUDA_TRY(cudaMalloc(&g->bcol, nnz * sizeof(int32_t)));
+        DI_CUDA_TRY(cudaMalloc(&g->brow, nnz * sizeof(int32_t)));
+        k_vfill<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, dec, n, kSrcBlockShift, voff, g->bcol,
+                                                                g->brow);
+        DI_CUDA_TRY(cudaGetLastError());
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // 8. segments of the long in-rows (exact residual load balance), two granularities
     {
         std::vector<int32_t> hin(n + 1);
         DI_CUDA_TRY(cudaMemcpy(hin.data(), g->in_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));

@@ -18,6 +18,9 @@
 namespace di {
 namespace {
 
+__device__ void res_control(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int mode, double s,
+                            double m);
+
 __global__ void __launch_bounds__(kResThreads) k_res_prep(const SolveDesc *__restrict__ desc,
                                                           const SolveState *__restrict__ st, int mode,
                                                           const double *__restrict__ s64,
@@ -109,6 +112,118 @@ __global__ void __launch_bounds__(kResThreads) k_res_long(
     }
     block_sum_max<kResThreads>(s, m);
     if (threadIdx.x != 0) return;
+    res_control(desc, st, mode, s, m);
+}
+
+// ------------------------------------------------------------------ source-blocked form
+
+// acc = B - H and g = (d / outdeg) H.
+__global__ void __launch_bounds__(kResThreads) k_resb_init(const SolveDesc *__restrict__ desc,
+                                                           const SolveState *__restrict__ st, int mode,
+                                                           const double *__restrict__ s64, double *__restrict__ g,
+                                                           double *__restrict__ acc, int64_t n) {
+    if (mode == RES_LEVEL && !st->do_recompute) return;
+    const double *__restrict__ B = desc->B;
+    const double *__restrict__ H = desc->H;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double h = H[i];
+        g[i] = s64[i] * h;
+        acc[i] = B[i] - h;
+    }
+}
+
+// acc_k += g_j over the in-edges j -> k, taken in source-blocked order: at any
+// time the grid works inside one block of 2^22 sources, whose 32 MB of g stay
+// in L2 while the edge arrays stream.  16 consecutive edges per thread; runs
+// of equal destination are summed and added with one red.global.add.f64.
+__global__ void __launch_bounds__(kResThreads) k_resb_flat(const SolveState *__restrict__ st, int mode,
+                                                           const int32_t *__restrict__ bcol,
+                                                           const int32_t *__restrict__ brow,
+                                                           const double *__restrict__ g, double *__restrict__ acc,
+                                                           int64_t nnz) {
+    if (mode == RES_LEVEL && !st->do_recompute) return;
+    constexpr int kE = 16;
+    const int64_t nch = (nnz + kE - 1) / kE;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += stride) {
+        const int64_t e0 = c * kE;
+        int32_t col[kE], row[kE];
+        if (e0 + kE <= nnz) {
+#pragma unroll
+            for (int v = 0; v < kE / 4; ++v) {
+                const int4 a = __ldcs(reinterpret_cast<const int4 *>(bcol + e0) + v);
+                const int4 b = __ldcs(reinterpret_cast<const int4 *>(brow + e0) + v);
+                col[4 * v] = a.x; col[4 * v + 1] = a.y; col[4 * v + 2] = a.z; col[4 * v + 3] = a.w;
+                row[4 * v] = b.x; row[4 * v + 1] = b.y; row[4 * v + 2] = b.z; row[4 * v + 3] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const bool ok = e0 + k < nnz;
+                col[k] = ok ? bcol[e0 + k] : 0;
+                row[k] = ok ? brow[e0 + k] : -1;
+            }
+        }
+        double val[kE];
+#pragma unroll
+        for (int k = 0; k < kE; ++k) val[k] = row[k] >= 0 ? g[col[k]] : 0.0;
+        int32_t cur = row[0];
+        double sum = val[0];
+#pragma unroll
+        for (int k = 1; k < kE; ++k) {
+            if (row[k] != cur) {
+                if (cur >= 0) red_add(acc + cur, sum);
+                cur = row[k];
+                sum = val[k];
+            } else {
+                sum += val[k];
+            }
+        }
+        if (cur >= 0) red_add(acc + cur, sum);
+    }
+}
+
+// F = acc into the outputs of the mode, L1 norm and max; the last CTA runs
+// the control step.
+template <typename FT>
+__global__ void __launch_bounds__(kResThreads) k_resb_fin(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                          int mode, const double *__restrict__ acc, int64_t n,
+                                                          double *__restrict__ part_sum, double *__restrict__ part_max) {
+    if (mode == RES_LEVEL && !st->do_recompute) return;
+    FT *__restrict__ Ffl = (mode == RES_LEVEL || mode == RES_WARM_INIT) ? static_cast<FT *>(desc->F) : nullptr;
+    double *__restrict__ F64 = mode == RES_WARM_INIT ? nullptr : desc->F_out;
+    double lsum = 0.0, lmax = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double f = acc[i];
+        if (Ffl) Ffl[i] = static_cast<FT>(f);
+        if (F64) F64[i] = f;
+        lsum += fabs(f);
+        lmax = fmax(lmax, fabs(f));
+    }
+    block_sum_max<kResThreads>(lsum, lmax);
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = lsum;
+        part_max[blockIdx.x] = lmax;
+    }
+    if (!last_block(&st->res_blocks)) return;
+    double s = 0.0, m = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        s += part_sum[i];
+        m = fmax(m, part_max[i]);
+    }
+    block_sum_max<kResThreads>(s, m);
+    if (threadIdx.x != 0) return;
+    res_control(desc, st, mode, s, m);
+}
+
+// ------------------------------------------------------------------ control
+
+// After an exact residual with L1 norm s and max m: stop, calibrate the
+// scan's estimate, or (warm start) set T_0 and |F_0|_1.
+__device__ void res_control(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int mode, double s,
+                            double m) {
     st->r_exact = s;
     st->max_exact = m;
     if (mode == RES_LEVEL) {
@@ -125,7 +240,10 @@ __global__ void __launch_bounds__(kResThreads) k_res_long(
         }
         st->confirming = 0;
     } else if (mode == RES_WARM_INIT) {
-        st->T = m;
+        // T_0 = mean |F0_i| (<= max |F0|): equal to max |F0| for a cold start
+        // with uniform B; for a warm start it avoids a run of sparse levels
+        // over the few largest residuals
+        st->T = desc->n_nodes > 0 ? s / (double)desc->n_nodes : m;
         st->f0_l1 = s;
         if (!isfinite(s)) st->done = 3;
         else if (s <= desc->tol) st->done = 1;   // H_0 already meets the tolerance
@@ -148,8 +266,23 @@ int residual_kernels(const di_graph *) { return 3; }
 
 int residual_partials(const di_graph *g) { return g->grid_res + kResLongBlocks; }
 
+bool residual_blocked(const di_graph *g) { return g->res_form != 1; }
+
 void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s) {
     Workspace &ws = g->ws;
+    if (residual_blocked(g)) {
+        const int grid = g->grid_res;
+        const int flat = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)grid, (g->nnz / 16 + kResThreads) / kResThreads));
+        k_resb_init<<<grid, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, g->s64, ws.g, ws.acc, g->n);
+        k_resb_flat<<<flat, kResThreads, 0, s>>>(ws.st, (int)mode, g->bcol, g->brow, ws.g, ws.acc, g->nnz);
+        if (fluid_fp64)
+            k_resb_fin<double><<<grid, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, ws.acc, g->n, ws.part_sum,
+                                                            ws.part_max);
+        else
+            k_resb_fin<float><<<grid, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, ws.acc, g->n, ws.part_sum,
+                                                           ws.part_max);
+        return;
+    }
     const PullPlan pl = pull_plan_of(g);
     const int pull_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(g->grid_res, pl.task_off[5]));
     k_res_prep<<<g->grid_res, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, g->s64, ws.g, g->n);
@@ -180,6 +313,7 @@ extern "C" DI_API di_status di_residual(di_graph *g, const double *B, double d, 
     cudaStream_t s = as_stream(stream);
     DI_TRY(ensure_workspace(g));
     DI_TRY(ensure_scale(g, d, s));
+    g->res_form = 0;
     Workspace &ws = g->ws;
     // the workspace descriptor is shared with di_solve: stage it through the pinned mirror
     DI_CUDA_TRY(cudaStreamSynchronize(s));

@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
     double *__restrict__ H = desc->H;
     const int lane = threadIdx.x & 31;
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
+    const uint64_t keep = l2_keep_policy();
 
     auto push1 = [&](int32_t c, FT w) {
-        if (c >= 0) red_add(F + c, w);
+        if (c >= 0) red_add_keep(F + c, w, keep);
         else atomicAdd(&s_hot[-1 - c], w);
     };
 
@@ -332,18 +333,18 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
         int32_t b = 0, e = 0;
         FT w = FT(0);
         if (idx < count) {
-            const int32_t i = front[idx];
-            b = rp[i];
-            e = rp[i + 1];
-            const FT f = atomic_exch_fluid(F + i, FT(0));
-            H[i] += static_cast<double>(f);   // i appears once per frontier
-            w = f * scale[i];
+            const int32_t i = __ldcs(front + idx);
+            b = __ldcs(rp + i);
+            e = __ldcs(rp + i + 1);
+            const FT f = atomic_exch_keep(F + i, FT(0), keep);
+            __stcs(H + i, __ldcs(H + i) + static_cast<double>(f));   // i appears once per frontier
+            w = f * __ldcs(scale + i);
             my_nodes += 1;
             my_edges += static_cast<unsigned long long>(e - b);
         }
         const int deg = e - b;
         if (deg <= kThreadMaxDeg) {
-            for (int32_t q = b; q < e; ++q) push1(pcol[q], w);
+            for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
         }
         unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg && deg <= kWarpMaxDeg);
         while (wm) {
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
             wm &= wm - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const FT mw = __shfl_sync(0xffffffffu, w, src);
-            for (int32_t q = mb + lane; q < me; q += 32) push1(pcol[q], mw);
+            for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
         }
         if (deg > kWarpMaxDeg) {
             const int slot = atomicAdd(&s_qn, 1);
@@ -364,14 +365,14 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
         for (int h = 0; h < qn; ++h) {
             const int32_t hb = s_qb[h], he = s_qe[h];
             const FT hw = s_qw[h];
-            for (int32_t q = hb + threadIdx.x; q < he; q += kPushThreads) push1(pcol[q], hw);
+            for (int32_t q = hb + threadIdx.x; q < he; q += kPushThreads) push1(__ldcs(pcol + q), hw);
         }
         __syncthreads();
     }
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
         const FT v = s_hot[sl];
-        if (v != FT(0)) red_add(F + hot_node[sl], v);
+        if (v != FT(0)) red_add_keep(F + hot_node[sl], v, keep);
     }
     my_edges = warp_sum(my_edges);
     my_nodes = warp_sum(my_nodes);
@@ -381,6 +382,87 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
     }
 }
 
+// Push of the asynchronous design, warp-level form: every warp claims
+// kWarpGrab frontier entries with one atomic and takes them 32 at a time
+// (drain: f = atomicExch(F_i, 0), H_i += f), so drains and pushes interleave
+// finely and fluid that arrives before a node's turn goes with it.  A row of
+// at most kThreadMaxDeg edges is pushed by its own lane; a longer one by the
+// whole warp (coalesced column loads).  No block-wide barrier inside the
+// loop; hot targets accumulate in shared memory and are flushed at the end.
+constexpr int kWarpGrab = 128;
+
+template <typename FT>
+__global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                      const int32_t *__restrict__ front,
+                                                      const int32_t *__restrict__ rp,
+                                                      const int32_t *__restrict__ pcol,
+                                                      const int32_t *__restrict__ hot_node, int n_hot,
+                                                      const FT *__restrict__ scale) {
+    const int count = st->push_count;
+    if (count == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FT *s_hot = reinterpret_cast<FT *>(smem_raw);
+    for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
+    __syncthreads();
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    double *__restrict__ H = desc->H;
+    const int lane = threadIdx.x & 31;
+    const uint64_t keep = l2_keep_policy();
+    auto push1 = [&](int32_t c, FT w) {
+        if (c >= 0) red_add_keep(F + c, w, keep);
+        else atomicAdd(&s_hot[-1 - c], w);
+    };
+    // claim size: 128 entries on large frontiers, down to 32 when the frontier
+    // would leave warps idle
+    const int nwarps = (int)(gridDim.x * (kPushThreads / 32));
+    int grab = count / (nwarps * 4);
+    grab = grab < 32 ? 32 : (grab > kWarpGrab ? kWarpGrab : grab & ~31);
+    unsigned long long my_edges = 0, my_nodes = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&st->tile_ctr, (unsigned)grab);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base >= count) break;
+#pragma unroll 1
+        for (int sub = 0; sub < grab; sub += 32) {
+            const int64_t idx = (int64_t)base + sub + lane;
+            int32_t b = 0, e = 0;
+            FT w = FT(0);
+            if (idx < count) {
+                const int32_t i = __ldcs(front + idx);
+                b = __ldcs(rp + i);
+                e = __ldcs(rp + i + 1);
+                const FT f = atomic_exch_keep(F + i, FT(0), keep);
+                __stcs(H + i, __ldcs(H + i) + static_cast<double>(f));   // i appears once per frontier
+                w = f * __ldcs(scale + i);
+                my_nodes += 1;
+                my_edges += static_cast<unsigned long long>(e - b);
+            }
+            const int deg = e - b;
+            if (deg <= kThreadMaxDeg)
+                for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
+            unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg);
+            while (wm) {
+                const int src = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
+                const FT mw = __shfl_sync(0xffffffffu, w, src);
+                for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
+            }
+        }
+    }
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
+        const FT v = s_hot[sl];
+        if (v != FT(0)) red_add_keep(F + hot_node[sl], v, keep);
+    }
+    my_edges = warp_sum(my_edges);
+    my_nodes = warp_sum(my_nodes);
+    if (lane == 0 && my_nodes) {
+        atomicAdd(&st->node_diff, my_nodes);
+        atomicAdd(&st->edge_diff, my_edges);
+    }
+}
 
 // ------------------------------------------------------------------ one threshold level
 
@@ -829,15 +911,20 @@ void launch_ex(Kern kernel, int grid, int block, size_t smem, cudaStream_t s, co
 
 template <typename FT>
 void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
-                  int l2) {
+                  int l2, int prop) {
     Workspace &ws = g->ws;
     const cudaAccessPolicyWindow *win = l2_window(g, 0, sizeof(FT) == 8, l2);
     launch_ex(k_scan_level<FT>, g->grid_scan, kScanThreads, 0, s, nullptr, (const SolveDesc *)ws.desc, ws.st,
               ws.front, (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
-    launch_ex(k_push_async<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
-              (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
-              (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
+    if (prop == 4)
+        launch_ex(k_push_warp<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
+                  (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
+                  (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
+    else
+        launch_ex(k_push_async<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
+                  (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
+                  (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
 }
 
 template <typename FT>
@@ -881,7 +968,7 @@ void launch_pushw(di_graph *g, cudaStream_t s, int l2) {
 
 di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     SolverGraph &sg = g->sg[fp64];
-    if (sg.built && sg.l2 == l2 && sg.prop == prop) return DI_OK;
+    if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form) return DI_OK;
     if (sg.built) {   // rebuilt with the other window setting
         cudaGraphExecDestroy(sg.exec);
         cudaGraphDestroy(sg.graph);
@@ -907,7 +994,7 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraphNode_t wnode;
     DI_CUDA_TRY(cudaGraphAddNode(&wnode, sg.graph, nullptr, nullptr, 0, &wp));
     cudaGraph_t body = wp.conditional.phGraph_out[0];
-    if (prop != 3) DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_p2, body, 0, 0));
+    if (prop < 3) DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_p2, body, 0, 0));
     DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_if, body, 0, 0));
 
     cudaGraphNodeParams pp = {};
@@ -918,10 +1005,10 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraph_t capg = nullptr;
     cudaGraph_t ended = nullptr;
     DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (prop == 3) {
-        // body: k_scan_level -> k_push_async -> IF(exact residual)
-        if (fp64) launch_async<double>(g, cs, sg.h_while, sg.h_if, 1, win);
-        else launch_async<float>(g, cs, sg.h_while, sg.h_if, 1, win);
+    if (prop >= 3) {
+        // body: k_scan_level -> k_push_async (or k_push_warp) -> IF(exact residual)
+        if (fp64) launch_async<double>(g, cs, sg.h_while, sg.h_if, 1, win, prop);
+        else launch_async<float>(g, cs, sg.h_while, sg.h_if, 1, win, prop);
     } else {
         // body: k_select -> IF/ELSE(pull | push) -> IF(exact residual)
         if (fp64) launch_select<double>(g, cs, sg.h_while, sg.h_p2, sg.h_if, 1, win);
@@ -945,7 +1032,7 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
     DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
 
-    if (prop != 3) {
+    if (prop < 3) {
         DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, pp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
         if (fp64) launch_pull<double>(g, cs, win, prop); else launch_pull<float>(g, cs, win, prop);
@@ -965,6 +1052,7 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     sg.built = true;
     sg.l2 = l2;
     sg.prop = prop;
+    sg.res_form = g->res_form;
     return DI_OK;
 }
 
@@ -986,6 +1074,8 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("di_solve: tol = %g must be finite and > 0", tol); return DI_EINVAL; }
     if (!(o->alpha > 1.0) || !std::isfinite(o->alpha)) { set_error("di_solve: alpha = %g must be > 1", o->alpha); return DI_EINVAL; }
     if (o->max_levels < 0 || o->recompute_every < 0) { set_error("di_solve: negative max_levels or recompute_every"); return DI_EINVAL; }
+    if (o->propagation < 0 || o->propagation > 4) { set_error("di_solve: propagation = %d outside [0, 4]", o->propagation); return DI_EINVAL; }
+    if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     return DI_OK;
 }
 
@@ -1021,6 +1111,7 @@ di_status ensure_workspace(di_graph *g) {
     const int64_t nseg5 = pl.task_off[5] - pl.task_off[4];
     DI_CUDA_TRY(dmalloc(&ws.front, n));
     DI_CUDA_TRY(dmalloc(&ws.g, n));
+    DI_CUDA_TRY(dmalloc(&ws.acc, n));
     DI_CUDA_TRY(dmalloc(&ws.seg_part, std::max<int64_t>({(int64_t)g->n_seg, nseg5, 1})));
     DI_CUDA_TRY(dmalloc(&ws.part_sum, parts));
     DI_CUDA_TRY(dmalloc(&ws.part_max, parts));
@@ -1058,6 +1149,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     if (!fp64 && !ws.F32) DI_CUDA_TRY(dmalloc(&ws.F32, g->n));
     if (!fp64 && !ws.w32) DI_CUDA_TRY(dmalloc(&ws.w32, g->n));
     DI_TRY(ensure_scale(g, d, s));
+    g->res_form = o.exact_residual;
     if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
 
     // descriptor (the previous call has completed: every solve synchronises)
@@ -1076,6 +1168,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
     dh.propagation = o.propagation;
     dh.push_ratio = o.push_ratio > 0 ? o.push_ratio : 8;
+    dh.n_nodes = g->n;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
@@ -1126,9 +1219,9 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             for (int l = 0; l < kBatch; ++l) {
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
-                if (o.propagation == 3) {
-                    if (fp64) launch_async<double>(g, s, 0, 0, 2, win);
-                    else launch_async<float>(g, s, 0, 0, 2, win);
+                if (o.propagation >= 3) {
+                    if (fp64) launch_async<double>(g, s, 0, 0, 2, win, o.propagation);
+                    else launch_async<float>(g, s, 0, 0, 2, win, o.propagation);
                 } else if (fp64) {
                     launch_select<double>(g, s, 0, 0, 0, 2, win);
                     launch_pull<double>(g, s, win, o.propagation);
@@ -1141,7 +1234,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                 DI_CUDA_TRY(cudaEventRecord(e[1], s));
                 launch_residual(g, fp64, RES_LEVEL, s);
                 DI_CUDA_TRY(cudaEventRecord(e[2], s));
-                host_launches += (o.propagation == 3 ? 2 : 3) + residual_kernels(g);
+                host_launches += (o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
             }
             DI_CUDA_TRY(cudaGetLastError());
             DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
