@@ -42,6 +42,7 @@ WORKLOADS = {
     "web-1m": (gg.WEB_1M, "web-like N=1e6, m=10, +-64 window, seed 0"),
     "stress-16m": (gg.STRESS_16M, "web-like N=2^24, m=16, +-256 window, seed 0"),
     "web-10k": (gg.SMALL_10K, "web-like N=1e4, m=8, +-64 window, seed 0"),
+    "web-4m": (gg.MID_4M, "web-like N=2^22, m=16, +-256 window, seed 0"),
     "warmstart": (None, "learned warm start: trained on seeded web-like graphs (N log-uniform in [1e5, 1e6], "
                         "m=10, seeds 1000..), evaluated on held-out N=3e6, m=10 graphs (seeds 2000..)"),
     "batch-64x4": (None, "64 web-like graphs, N log-uniform in [1e4, 2e6], m ~ U[6, 14], seeds 0..63; "
@@ -80,6 +81,21 @@ def parse():
                    help="host-driven levels with per-kernel events (profilers cannot see kernels in "
                         "graphs with conditional nodes)")
     return p.parse_args()
+
+
+def aggregate_over_ranks(secs: float, units: float, world: int, device: str) -> tuple[float, float]:
+    """Whole-job figures of replicas: the slowest rank's time (max) and the
+    units all ranks processed (sum).  No data-path collective: this is the
+    only exchange, after the timed region."""
+    if world <= 1:
+        return float(secs), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def dist_env():
@@ -234,6 +250,53 @@ def run_reference_multi(args, desc):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def warm_start_leg(args, g, B, tol, stream, flush, n_train=24, epochs=8):
+    """Time to tolerance of this workload's graph from the learned warm start
+    (features, network, F0 and solve, all timed) against the zero start.  The
+    network is trained first on n_train other seeded graphs (N log-uniform in
+    [1e5, 1e6], m = 10) with targets from the plain solver."""
+    import torch
+    from paper_1202_6168_gb300 import binding as di
+    graphs, Bs, Xs = [], [], []
+    for sp in gg.warmstart_specs("train", n_train):
+        rp, col = gg.generate(sp)
+        gt = di.Graph.create(rp, col, stream=stream)
+        b = torch.full((sp.n,), (1.0 - D) / sp.n, dtype=torch.float64, device="cuda")
+        h = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+        di.di_solve(gt, b, D, 1e-8 * (1.0 - D), h, None, di.opts_default(stream=stream.cuda_stream))
+        graphs.append(gt)
+        Bs.append(b)
+        Xs.append(h)
+    model = di.Model.create(7)
+    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=epochs, batch=65536, lr=1e-3,
+                                                             stream=stream.cuda_stream))
+    for gt in graphs:
+        gt.close()
+    H = torch.zeros_like(B)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    res = {}
+    for label in ("cold", "warm"):
+        o = di.opts_default(stream=stream.cuda_stream, warm_start=1 if label == "warm" else 0)
+        times = []
+        for rep in range(3 + max(args.steps, 1)):
+            flush.zero_()
+            ev[0].record(stream)
+            if label == "warm":
+                model.infer(g, B, H, stream)
+            _, st = di.di_solve(g, B, D, tol, H, None, o)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if rep >= 3:
+                times.append(ev[0].elapsed_time(ev[1]))
+        res[label] = {"ms": statistics.median(times), "edge_diffusions": st.edge_diffusions, "levels": st.levels,
+                      "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1}
+    model.close()
+    res["speedup"] = res["cold"]["ms"] / res["warm"]["ms"]
+    res["train"] = {"graphs": n_train, "epochs": epochs, "loss_last_epoch": loss}
+    res["timed"] = "warm: features + network + F0 + solve; cold: solve; L2 flushed before each"
+    return res
+
+
 def run_native(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -297,14 +360,7 @@ def run_native(args, world, rank, local):
     secs = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) * 1e-3
     last = st
 
-    if world > 1:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([edges], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        secs_max, edges_all = float(t.item()), float(e.item())
-    else:
-        secs_max, edges_all = secs, float(edges)
+    secs_max, edges_all = aggregate_over_ranks(secs, edges, world, "cuda")
     value = edges_all / secs_max
 
     extras = {}
@@ -362,6 +418,8 @@ def run_native(args, world, rank, local):
             _, es = di.di_solve_host(g, Bh.data_ptr(), D, tol, Hh.data_ptr(), None, opts)
             e_secs += time.perf_counter() - t0
             e_edges += es.edge_diffusions
+        if args.workload == "web-1m" and not args.no_cpu:
+            extras["warm_start"] = warm_start_leg(args, g, B, tol, stream, flush)
         extras["e2e"] = {"value": e_edges / e_secs, "unit": "edge_diffusions/s",
                          "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                          "ms_per_step": 1e3 * e_secs / args.steps,
@@ -459,14 +517,7 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     secs = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) * 1e-3
-    if world > 1:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([float(edges)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        secs, edges_all = float(t.item()), float(e.item())
-    else:
-        edges_all = float(edges)
+    secs, edges_all = aggregate_over_ranks(secs, edges, world, "cuda")
     extras = {}
     if rank == 0 and not args.no_extras:
         # the same 256 solves one di_solve call at a time

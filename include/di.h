@@ -53,6 +53,19 @@ typedef enum {
 
 typedef struct di_graph di_graph;
 
+/* Shape of the push kernels (see di_autotune): a frontier node whose out-row
+ * has at most thread_max_deg edges is pushed by one thread, one of at most
+ * warp_max_deg edges by a warp, a longer one by the whole CTA (the
+ * warp-tile push, propagation 4, sends every row above thread_max_deg to a
+ * warp); the push runs push_ctas_per_sm CTAs per SM (0 = the occupancy
+ * maximum).  Defaults: 16, 512, 0. */
+typedef struct {
+    int32_t thread_max_deg;    /* 1 .. 1024 */
+    int32_t warp_max_deg;      /* thread_max_deg .. 2^30 */
+    int32_t push_ctas_per_sm;  /* 0 .. 64 */
+    int32_t reserved;
+} di_tune;
+
 /* Solver options.  Fill with di_opts_default() and change what you need. */
 typedef struct {
     double alpha;          /* threshold decay T <- T/alpha, > 1; default 1.5 (Sec. 2.4) */
@@ -267,6 +280,8 @@ DI_API di_status di_solve_batched(di_batch *b, const double *const *B, double d,
  *   j -> i, x4/x5 = mean of x2_j / max of x3_j over the in-edges,
  *   x6 = log(1 + sum s_j), x7 = log(1 + sum s_j a1_j) (a1_j = sum over j's
  *   in-edges of s), x8 = N B_i; empty means, maxima and sums are 0.
+ *   Logarithms and 1/o are evaluated in FP32; sums over in-edges are
+ *   accumulated in FP64 and rounded once to FP32.
  * Network: standardise (x - mu) / sd, then 9 -> 64 -> 64 -> 1 with ReLU
  * (BF16 tensor-core operands, FP32 accumulation), y = w3 . h2 + b3.
  * Parameters (DI_MODEL_NPARAM floats): W1 [64][16] (input columns 9..15 are
@@ -335,6 +350,33 @@ DI_API di_status di_warmstart_infer(di_model *m, di_graph *g, const double *B, d
 /* Model file: header, step, state, Adam moments (little-endian floats). */
 DI_API di_status di_warmstart_save(const di_model *m, const char *path);
 DI_API di_status di_warmstart_load(const char *path, di_model **out);
+
+/*
+ * Autotuning of the push shape.  The paper's cost model counts elementary
+ * diffusions only (Sec. 2.4); on a GPU the time per diffusion also depends
+ * on how frontier rows are spread over threads, warps and CTAs, which
+ * depends on the graph's degree mix.  di_autotune / di_batch_autotune time
+ * complete solves of the caller's problem (plain D-iteration, the same
+ * options) for candidate shapes - thread_max_deg in {4, 8, 16, 32}, with the
+ * occupancy-maximum push grid and with half of it - keep the fastest, store
+ * it in the graph or batch (used by every later solve) and return it.
+ * cache_path (may be NULL) names a text file of JSON lines keyed by the
+ * problem's size bucket (log2 of nodes and edges, items, fluid precision,
+ * propagation): a hit is used without timing, a miss appends the result.
+ * *best_seconds (may be NULL) receives the winner's time (0 on a cache hit).
+ * The solves write the caller's H buffers (graph: a scratch buffer of the
+ * library).  Synchronous.
+ */
+DI_API di_status di_tune_default(di_tune *t);
+DI_API di_status di_graph_set_tune(di_graph *g, const di_tune *t);
+DI_API di_status di_graph_get_tune(const di_graph *g, di_tune *t);
+DI_API di_status di_batch_set_tune(di_batch *b, const di_tune *t);
+DI_API di_status di_batch_get_tune(const di_batch *b, di_tune *t);
+DI_API di_status di_autotune(di_graph *g, const double *B, double d, double tol, const di_opts *opts,
+                             const char *cache_path, di_tune *best, double *best_seconds);
+DI_API di_status di_batch_autotune(di_batch *b, const double *const *B, double d, const double *tol,
+                                   double *const *H, const di_opts *opts, const char *cache_path,
+                                   di_tune *best, double *best_seconds);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,7 @@ CU_SOURCES = [
     "noalloc.cu",
     "batch.cu",
     "warmstart.cu",
+    "tune.cu",
 ]
 
 

@@ -34,6 +34,15 @@ class di_train_opts(ctypes.Structure):
                 ("eps", c_dbl), ("seed", ctypes.c_uint64), ("stream", c_vp)]
 
 
+class di_tune(ctypes.Structure):
+    _fields_ = [("thread_max_deg", c_i32), ("warp_max_deg", c_i32), ("push_ctas_per_sm", c_i32),
+                ("reserved", c_i32)]
+
+    def as_dict(self) -> dict:
+        return {"thread_max_deg": self.thread_max_deg, "warp_max_deg": self.warp_max_deg,
+                "push_ctas_per_sm": self.push_ctas_per_sm}
+
+
 class di_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("recomputes", c_i32), ("node_diffusions", c_i64),
                 ("edge_diffusions", c_i64), ("resid_l1", c_dbl), ("err_bound", c_dbl),
@@ -85,6 +94,15 @@ SIGNATURES = {
     "di_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "di_warmstart_save": (c_int, [c_vp, ctypes.c_char_p]),
     "di_warmstart_load": (c_int, [ctypes.c_char_p, ctypes.POINTER(c_vp)]),
+    "di_tune_default": (c_int, [ctypes.POINTER(di_tune)]),
+    "di_graph_set_tune": (c_int, [c_vp, ctypes.POINTER(di_tune)]),
+    "di_graph_get_tune": (c_int, [c_vp, ctypes.POINTER(di_tune)]),
+    "di_batch_set_tune": (c_int, [c_vp, ctypes.POINTER(di_tune)]),
+    "di_batch_get_tune": (c_int, [c_vp, ctypes.POINTER(di_tune)]),
+    "di_autotune": (c_int, [c_vp, c_vp, c_dbl, c_dbl, ctypes.POINTER(di_opts), ctypes.c_char_p,
+                            ctypes.POINTER(di_tune), ctypes.POINTER(c_dbl)]),
+    "di_batch_autotune": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts), ctypes.c_char_p,
+                                  ctypes.POINTER(di_tune), ctypes.POINTER(c_dbl)]),
     "di_batch_create": (c_int, [c_vp, c_int, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "di_batch_destroy": (None, [c_vp]),
     "di_batch_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
@@ -364,6 +382,48 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+def tune_default() -> di_tune:
+    t = di_tune()
+    check(lib().di_tune_default(ctypes.byref(t)))
+    return t
+
+
+def autotune(graph: Graph, B, d: float, tol: float, opts: di_opts | None = None,
+             cache_path: str | None = None) -> tuple[di_tune, float]:
+    """Times solves for candidate push shapes, keeps the fastest in the graph."""
+    t, secs = di_tune(), c_dbl()
+    check(lib().di_autotune(graph.handle, _ptr(B), d, tol, ctypes.byref(opts) if opts is not None else None,
+                            cache_path.encode() if cache_path else None, ctypes.byref(t), ctypes.byref(secs)))
+    return t, secs.value
+
+
+def batch_autotune(batch: "Batch", B: list, d: float, tol, H: list, opts: di_opts | None = None,
+                   cache_path: str | None = None) -> tuple[di_tune, float]:
+    """Times batched solves for candidate push shapes, keeps the fastest in the batch."""
+    ni = len(batch.sizes)
+    tols = [float(tol)] * ni if isinstance(tol, (int, float)) else [float(x) for x in tol]
+    bp = (c_vp * ni)(*[_ptr(x) for x in B])
+    hp = (c_vp * ni)(*[_ptr(x) for x in H])
+    tp = (c_dbl * ni)(*tols)
+    t, secs = di_tune(), c_dbl()
+    check(lib().di_batch_autotune(batch.handle, bp, d, tp, hp, ctypes.byref(opts) if opts is not None else None,
+                                  cache_path.encode() if cache_path else None, ctypes.byref(t),
+                                  ctypes.byref(secs)))
+    return t, secs.value
+
+
+def set_tune(obj, tune: di_tune) -> None:
+    fn = lib().di_batch_set_tune if isinstance(obj, Batch) else lib().di_graph_set_tune
+    check(fn(obj.handle, ctypes.byref(tune)))
+
+
+def get_tune(obj) -> di_tune:
+    t = di_tune()
+    fn = lib().di_batch_get_tune if isinstance(obj, Batch) else lib().di_graph_get_tune
+    check(fn(obj.handle, ctypes.byref(t)))
+    return t
 
 
 def di_frontier(graph: Graph, F, fluid_fp64: bool, T: float, out_list, stream=None) -> tuple[int, float, float]:

@@ -26,6 +26,7 @@
 // with every decision taken on the device.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <new>
 #include <vector>
 
@@ -70,6 +71,7 @@ struct BState {
 struct BDesc {
     double d, alpha;
     int R, fp64, max_levels, max_body_iters, nitems, final_mode;
+    int thread_max, warp_max;  // push shape
     void *F;             // union fluid (float or double)
     double *B, *H;       // union B and history
     double *tmp, *g;     // exact-residual scratch
@@ -325,6 +327,7 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
     const int lane = threadIdx.x & 31;
     for (int sl = threadIdx.x; sl < n_hot; sl += kBThreads) s_hot[sl] = FT(0);
     const uint64_t keep = l2_keep_policy();
+    const int thread_max = desc->thread_max, warp_max = desc->warp_max;
     auto push1 = [&](int32_t c, FT w) {
         if (c >= 0) red_add_keep(F + c, w, keep);
         else atomicAdd(&s_hot[-1 - c], w);
@@ -351,10 +354,10 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
             }
         }
         const int deg = e - b;
-        if (deg <= kThreadMaxDeg) {
+        if (deg <= thread_max) {
             for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
         }
-        unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg && deg <= kWarpMaxDeg);
+        unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
         while (wm) {
             const int src = __ffs(wm) - 1;
             wm &= wm - 1;
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
             const FT mw = __shfl_sync(0xffffffffu, w, src);
             for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
         }
-        if (deg > kWarpMaxDeg) {
+        if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
             s_qb[slot] = b;
             s_qe[slot] = e;
@@ -583,6 +586,7 @@ struct di_batch {
     const double **pB_h = nullptr; // pinned mirrors
     double **pH_h = nullptr;
     int grid_scan = 0, grid_push = 0, grid_flat = 0;
+    di_tune tune = {kThreadMaxDeg, kWarpMaxDeg, 0, 0};
     SolverGraph sg[2];
     int sg_l2[2] = {0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -616,13 +620,19 @@ int occ_grid(const void *fn, int threads, size_t smem, int sms) {
     return per_sm * sms;
 }
 
+int bpush_grid(const di_batch *b) {
+    const int sms = b->u->num_sms;
+    const int want = b->tune.push_ctas_per_sm > 0 ? b->tune.push_ctas_per_sm * sms : b->grid_push;
+    return std::max(1, std::min(b->grid_push, want));
+}
+
 template <typename FT>
 void launch_blevel(di_batch *b, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl) {
     di_graph *u = b->u;
     k_bscan_level<FT><<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->st, b->item_of_chunk, u->outdeg,
                                                           b->front, b->nchunks, hw, hr, ctl);
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(u->s32) : reinterpret_cast<const FT *>(u->s64);
-    k_bpush<FT><<<b->grid_push, kBThreads, u->n_hot * sizeof(FT), s>>>(b->desc, b->items, b->st, b->item_of_chunk,
+    k_bpush<FT><<<bpush_grid(b), kBThreads, u->n_hot * sizeof(FT), s>>>(b->desc, b->items, b->st, b->item_of_chunk,
                                                                        b->front, u->rp, u->pcol, u->hot_node, u->n_hot,
                                                                        scale);
 }
@@ -637,7 +647,12 @@ void launch_bres(di_batch *b, cudaStream_t s) {
 
 di_status build_batch_graph(di_batch *b, int fp64) {
     SolverGraph &sg = b->sg[fp64];
-    if (sg.built) return DI_OK;
+    if (sg.built && sg.grid_push == bpush_grid(b)) return DI_OK;
+    if (sg.built) {   // rebuilt for another push grid
+        cudaGraphExecDestroy(sg.exec);
+        cudaGraphDestroy(sg.graph);
+        sg = SolverGraph();
+    }
     cudaStream_t cs = nullptr;
     DI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     struct StreamGuard {
@@ -679,6 +694,7 @@ di_status build_batch_graph(di_batch *b, int fp64) {
     DI_CUDA_TRY(cudaGetLastError());
     DI_CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
     sg.built = true;
+    sg.grid_push = bpush_grid(b);
     return DI_OK;
 }
 
@@ -866,6 +882,8 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
     dh.max_levels = o.max_levels;
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
     dh.nitems = b->nitems;
+    dh.thread_max = b->tune.thread_max_deg;
+    dh.warp_max = b->tune.warp_max_deg;
     dh.F = fp64 ? (void *)b->F64 : (void *)b->F32;
     dh.B = b->B;
     dh.H = b->H;
@@ -983,4 +1001,67 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
     }
     (void)recomputes;
     return rc;
+}
+
+extern "C" DI_API di_status di_batch_set_tune(di_batch *b, const di_tune *t) {
+    clear_error();
+    if (!b) { set_error("di_batch_set_tune: NULL batch"); return DI_EINVAL; }
+    DI_TRY(check_tune(t, "di_batch_set_tune"));
+    b->tune = *t;
+    return DI_OK;
+}
+
+extern "C" DI_API di_status di_batch_get_tune(const di_batch *b, di_tune *t) {
+    clear_error();
+    if (!b || !t) { set_error("di_batch_get_tune: NULL argument"); return DI_EINVAL; }
+    *t = b->tune;
+    return DI_OK;
+}
+
+// Frontier tile shape of the batched push: times complete batched solves for
+// each candidate shape and keeps the fastest.
+extern "C" DI_API di_status di_batch_autotune(di_batch *b, const double *const *B, double d, const double *tol,
+                                             double *const *H, const di_opts *opts, const char *cache_path,
+                                             di_tune *best, double *best_seconds) {
+    clear_error();
+    if (!b || !B || !H || !tol) { set_error("di_batch_autotune: NULL argument"); return DI_EINVAL; }
+    di_opts o;
+    if (opts) o = *opts; else di_opts_default(&o);
+    o.timing = 0;
+    char key[160];
+    std::snprintf(key, sizeof(key), "batch items=%d n=2^%d nnz=2^%d fp64=%d", b->nitems, ilog2_round(b->n_union),
+                  ilog2_round(b->u->nnz), o.fluid_fp64 ? 1 : 0);
+    di_tune hit;
+    if (tune_cache_lookup(cache_path, key, &hit)) {
+        b->tune = hit;
+        if (best) *best = hit;
+        if (best_seconds) *best_seconds = 0.0;
+        return DI_OK;
+    }
+    const int occ_per_sm = std::max(1, b->grid_push / std::max(1, b->u->num_sms));
+    di_tune cand[16];
+    const int nc = tune_candidates(cand, 16);
+    di_tune win = b->tune;
+    double win_s = 1e300;
+    for (int c = 0; c < nc; ++c) {
+        di_tune t = cand[c];
+        if (t.push_ctas_per_sm < 0) {
+            if (occ_per_sm < 2) continue;
+            t.push_ctas_per_sm = occ_per_sm / 2;
+        }
+        b->tune = t;
+        double secs = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {   // the first solve rebuilds the level graph
+            di_stats tot;
+            const di_status rc = di_solve_batched(b, B, d, tol, H, &o, nullptr, &tot);
+            if (rc != DI_OK && rc != DI_ENOCONV) return rc;
+            if (rep > 0) secs = tot.seconds;
+        }
+        if (secs < win_s) { win_s = secs; win = t; }
+    }
+    b->tune = win;
+    tune_cache_store(cache_path, key, win, win_s);
+    if (best) *best = win;
+    if (best_seconds) *best_seconds = win_s;
+    return DI_OK;
 }

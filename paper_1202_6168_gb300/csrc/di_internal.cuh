@@ -37,8 +37,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;                                // per thread per chunk
 constexpr int kScanChunk = kScanThreads * kScanItems;       // nodes per block iteration
 constexpr int kPushThreads = 256;                            // = frontier tile size
-constexpr int kThreadMaxDeg = 16;   // out-degree <= this: one thread pushes the row
-constexpr int kWarpMaxDeg = 512;    // <= this: one warp; above: the whole CTA
+constexpr int kThreadMaxDeg = 16;   // default: out-degree <= this: one thread pushes the row
+constexpr int kWarpMaxDeg = 512;    // default: <= this: one warp; above: the whole CTA
 constexpr int kResThreads = 256;
 constexpr int kResSeg = 8192;       // in-rows longer than this are split in segments (allocation-free path)
 constexpr int kResFine = 256;       // segment length of the exact residual's long in-rows
@@ -64,6 +64,8 @@ struct SolveDesc {
     int propagation;      // 0/1 auto (binned/flat gather for dense levels), 2 push only, 3 async push
     int push_ratio;       // dense when active edges * push_ratio >= edges
     int64_t n_nodes;
+    int thread_max;       // push shape: rows up to this many edges go to one thread
+    int warp_max;         // ... up to this to one warp, longer ones to the CTA
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -116,6 +118,7 @@ struct SolverGraph {
     int l2 = 0;           // built with the L2 window
     int prop = 0;         // built with this propagation option
     int res_form = 0;     // built with this exact-residual form
+    int grid_push = 0;    // built with this push grid
 };
 
 struct Workspace {
@@ -140,6 +143,9 @@ struct Workspace {
 };
 
 }  // namespace di
+
+constexpr int kThreadMaxDegDefault = di::kThreadMaxDeg;
+constexpr int kWarpMaxDegDefault = di::kWarpMaxDeg;
 
 struct di_graph {
     int device = 0;
@@ -186,6 +192,7 @@ struct di_graph {
     int grid_select = 0, grid_pull = 0, grid_pushw = 0, grid_flat = 0;
     int level_items = 8;          // nodes per thread per chunk of the fused level kernel
     di::Workspace ws;
+    di_tune tune = {kThreadMaxDegDefault, kWarpMaxDegDefault, 0, 0};   // push shape (di_autotune)
     di::SolverGraph sg[2];        // [fluid_fp64]
     cudaAccessPolicyWindow win[4] = {};   // L2 windows: [2 * (0: F, 1: w) + fluid_fp64]
     int win_ready[4] = {0, 0, 0, 0}, win_ok[4] = {0, 0, 0, 0};
@@ -290,6 +297,13 @@ __device__ __forceinline__ bool last_block(unsigned int *counter) {
 di_status ensure_scale(di_graph *g, double d, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
+int push_grid(const di_graph *g);
+// tune.cu: validation of a push shape, candidates, and the JSON-lines cache
+di_status check_tune(const di_tune *t, const char *who);
+int tune_candidates(di_tune *out, int cap);
+bool tune_cache_lookup(const char *path, const char *key, di_tune *out);
+void tune_cache_store(const char *path, const char *key, const di_tune &t, double seconds);
+int ilog2_round(int64_t v);
 // residual.cu: launch the exact-residual kernels (prep, segments, rows)
 void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s);
 int residual_grid(int sms);

@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
     const int lane = threadIdx.x & 31;
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
     const uint64_t keep = l2_keep_policy();
+    const int thread_max = desc->thread_max, warp_max = desc->warp_max;
 
     auto push1 = [&](int32_t c, FT w) {
         if (c >= 0) red_add_keep(F + c, w, keep);
@@ -343,10 +344,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
             my_edges += static_cast<unsigned long long>(e - b);
         }
         const int deg = e - b;
-        if (deg <= kThreadMaxDeg) {
+        if (deg <= thread_max) {
             for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
         }
-        unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg && deg <= kWarpMaxDeg);
+        unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
         while (wm) {
             const int src = __ffs(wm) - 1;
             wm &= wm - 1;
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
             const FT mw = __shfl_sync(0xffffffffu, w, src);
             for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
         }
-        if (deg > kWarpMaxDeg) {
+        if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
             s_qb[slot] = b;
             s_qe[slot] = e;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
 // kWarpGrab frontier entries with one atomic and takes them 32 at a time
 // (drain: f = atomicExch(F_i, 0), H_i += f), so drains and pushes interleave
 // finely and fluid that arrives before a node's turn goes with it.  A row of
-// at most kThreadMaxDeg edges is pushed by its own lane; a longer one by the
+// at most thread_max edges is pushed by its own lane; a longer one by the
 // whole warp (coalesced column loads).  No block-wide barrier inside the
 // loop; hot targets accumulate in shared memory and are flushed at the end.
 constexpr int kWarpGrab = 128;
@@ -408,6 +409,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
     double *__restrict__ H = desc->H;
     const int lane = threadIdx.x & 31;
     const uint64_t keep = l2_keep_policy();
+    const int thread_max = desc->thread_max;
     auto push1 = [&](int32_t c, FT w) {
         if (c >= 0) red_add_keep(F + c, w, keep);
         else atomicAdd(&s_hot[-1 - c], w);
@@ -439,9 +441,9 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
                 my_edges += static_cast<unsigned long long>(e - b);
             }
             const int deg = e - b;
-            if (deg <= kThreadMaxDeg)
+            if (deg <= thread_max)
                 for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
-            unsigned wm = __ballot_sync(0xffffffffu, deg > kThreadMaxDeg);
+            unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max);
             while (wm) {
                 const int src = __ffs(wm) - 1;
                 wm &= wm - 1;
@@ -918,11 +920,11 @@ void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
               ws.front, (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
     if (prop == 4)
-        launch_ex(k_push_warp<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
+        launch_ex(k_push_warp<FT>, push_grid(g), kPushThreads, g->n_hot * sizeof(FT), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
     else
-        launch_ex(k_push_async<FT>, g->grid_push, kPushThreads, g->n_hot * sizeof(FT), s, win,
+        launch_ex(k_push_async<FT>, push_grid(g), kPushThreads, g->n_hot * sizeof(FT), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
 }
@@ -968,7 +970,8 @@ void launch_pushw(di_graph *g, cudaStream_t s, int l2) {
 
 di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     SolverGraph &sg = g->sg[fp64];
-    if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form) return DI_OK;
+    if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form && sg.grid_push == push_grid(g))
+        return DI_OK;
     if (sg.built) {   // rebuilt with the other window setting
         cudaGraphExecDestroy(sg.exec);
         cudaGraphDestroy(sg.graph);
@@ -1053,6 +1056,7 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     sg.l2 = l2;
     sg.prop = prop;
     sg.res_form = g->res_form;
+    sg.grid_push = push_grid(g);
     return DI_OK;
 }
 
@@ -1080,6 +1084,13 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
 }
 
 }  // namespace
+
+// Push grid: the occupancy maximum, or the tuned CTAs per SM below it.
+int push_grid(const di_graph *g) {
+    const int occ = g->grid_push;
+    const int want = g->tune.push_ctas_per_sm > 0 ? g->tune.push_ctas_per_sm * g->num_sms : occ;
+    return std::max(1, std::min(occ, want));
+}
 
 di_status ensure_workspace(di_graph *g) {
     Workspace &ws = g->ws;
@@ -1169,6 +1180,8 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.propagation = o.propagation;
     dh.push_ratio = o.push_ratio > 0 ? o.push_ratio : 8;
     dh.n_nodes = g->n;
+    dh.thread_max = g->tune.thread_max_deg;
+    dh.warp_max = g->tune.warp_max_deg;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));

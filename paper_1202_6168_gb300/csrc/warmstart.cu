@@ -44,25 +44,29 @@ constexpr int kFwdThreads = 128;          // 4 warps x 16 nodes per tile
 constexpr int kBwdThreads = 256;
 constexpr int kBwdRows = 16;
 constexpr int kFeatThreads = 256;
-constexpr int kTmp = 5;                   // FP64 temporaries per node: ld, s, x2, x3, a1
+constexpr int kTmp = 5;                   // FP32 temporaries per node: ld, s, x2, x3, a1
 
 // ------------------------------------------------------------------ features
 
+// Feature arithmetic: the logarithms and reciprocals are FP32 (GB300 runs
+// FP64 at a small fraction of the FP32 rate, and the features feed a BF16
+// network); every sum over in-edges is accumulated in FP64 and rounded once.
+//
 // x0 = log(1 + indeg), x1 = log(1 + outdeg), x8 = N B_i; temporaries
 // ld_i = log(1 + indeg) and s_i = 1 / outdeg (0 for a dangling node).
 __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__restrict__ rp,
                                                             const int32_t *__restrict__ in_rp,
                                                             const double *__restrict__ B, int64_t n,
-                                                            float *__restrict__ feat, double *__restrict__ tmp) {
+                                                            float *__restrict__ feat, float *__restrict__ tmp) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int indeg = in_rp[i + 1] - in_rp[i];
         const int outdeg = rp[i + 1] - rp[i];
-        const double ld = log1p((double)indeg);
+        const float ld = log1pf((float)indeg);
         tmp[i] = ld;
-        tmp[n + i] = outdeg > 0 ? 1.0 / (double)outdeg : 0.0;
-        feat[i * kNF + 0] = (float)ld;
-        feat[i * kNF + 1] = (float)log1p((double)outdeg);
+        tmp[n + i] = outdeg > 0 ? 1.0f / (float)outdeg : 0.0f;
+        feat[i * kNF + 0] = ld;
+        feat[i * kNF + 1] = log1pf((float)outdeg);
         feat[i * kNF + 8] = (float)((double)n * B[i]);
     }
 }
@@ -71,36 +75,36 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__res
 //   HOP 1: (ld_j, ld_j, s_j) summed, maximised, summed -> x2, x3, a1
 //   HOP 2: (x2_j, x3_j, s_j a1_j)                      -> x4, x5, a2
 template <int HOP>
-__device__ __forceinline__ void feat_visit(const double *__restrict__ tmp, int64_t n, int32_t j, double &u,
+__device__ __forceinline__ void feat_visit(const float *__restrict__ tmp, int64_t n, int32_t j, double &u,
                                            double &m, double &v) {
     if (HOP == 1) {
-        const double l = tmp[j];
-        u += l;
-        m = fmax(m, l);
-        v += tmp[n + j];
+        const float l = tmp[j];
+        u += (double)l;
+        m = fmax(m, (double)l);
+        v += (double)tmp[n + j];
     } else {
-        u += tmp[2 * n + j];
-        m = fmax(m, tmp[3 * n + j]);
-        v += tmp[n + j] * tmp[4 * n + j];
+        u += (double)tmp[2 * n + j];
+        m = fmax(m, (double)tmp[3 * n + j]);
+        v += (double)(tmp[n + j] * tmp[4 * n + j]);
     }
 }
 
 // Outputs of node i from its in-row sums (u, v), max m and length len.
 template <int HOP>
-__device__ __forceinline__ void feat_emit(double *__restrict__ tmp, float *__restrict__ feat, int64_t n, int64_t i,
+__device__ __forceinline__ void feat_emit(float *__restrict__ tmp, float *__restrict__ feat, int64_t n, int64_t i,
                                           int len, double u, double m, double v) {
-    const double mean = len > 0 ? u / (double)len : 0.0;
+    const float mean = len > 0 ? (float)(u / (double)len) : 0.0f;
     if (HOP == 1) {
         tmp[2 * n + i] = mean;
-        tmp[3 * n + i] = m;
-        tmp[4 * n + i] = v;
-        feat[i * kNF + 2] = (float)mean;
+        tmp[3 * n + i] = (float)m;
+        tmp[4 * n + i] = (float)v;
+        feat[i * kNF + 2] = mean;
         feat[i * kNF + 3] = (float)m;
     } else {
-        feat[i * kNF + 4] = (float)mean;
+        feat[i * kNF + 4] = mean;
         feat[i * kNF + 5] = (float)m;
-        feat[i * kNF + 6] = (float)log1p(tmp[4 * n + i]);
-        feat[i * kNF + 7] = (float)log1p(v);
+        feat[i * kNF + 6] = log1pf(tmp[4 * n + i]);
+        feat[i * kNF + 7] = log1pf((float)v);
     }
 }
 
@@ -111,7 +115,7 @@ __device__ __forceinline__ void feat_emit(double *__restrict__ tmp, float *__res
 template <int HOP>
 __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col, int64_t n,
-                                                           float *__restrict__ feat, double *__restrict__ tmp) {
+                                                           float *__restrict__ feat, float *__restrict__ tmp) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
                                                            const int32_t *__restrict__ lseg0, int n_long,
                                                            int64_t nseg, const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col, int64_t n,
-                                                           const double *__restrict__ tmp, double *__restrict__ lacc) {
+                                                           const float *__restrict__ tmp, double *__restrict__ lacc) {
     __shared__ double su[kFeatThreads / 32], sm[kFeatThreads / 32], sv[kFeatThreads / 32];
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t row = seg_row[sg];
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
 
 template <int HOP>
 __global__ void k_feat_long(const int32_t *__restrict__ lrows, int n_long, const int32_t *__restrict__ in_rp,
-                            int64_t n, const double *__restrict__ lacc, double *__restrict__ tmp,
+                            int64_t n, const double *__restrict__ lacc, float *__restrict__ tmp,
                             float *__restrict__ feat) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_long; r += gridDim.x * blockDim.x) {
         const int32_t i = lrows[r];
@@ -568,7 +572,7 @@ struct di_model {
     // scratch, grown on demand
     int64_t feat_cap = 0;
     float *feat = nullptr;
-    double *ftmp = nullptr;
+    float *ftmp = nullptr;
     int64_t row_cap = 0;
     int32_t *idx = nullptr;
     float *y = nullptr;
@@ -598,7 +602,7 @@ di_status ensure_feat(di_model *m, int64_t n) {
     m->ftmp = nullptr;
     m->feat_cap = 0;
     DI_CUDA_TRY(cudaMalloc(&m->feat, (size_t)n * kNF * sizeof(float)));
-    DI_CUDA_TRY(cudaMalloc(&m->ftmp, (size_t)n * kTmp * sizeof(double)));
+    DI_CUDA_TRY(cudaMalloc(&m->ftmp, (size_t)n * kTmp * sizeof(float)));
     m->feat_cap = n;
     return DI_OK;
 }

@@ -74,6 +74,7 @@ class GraphSpec:
 SMALL_10K = GraphSpec(n=10_000, mean_deg=8.0, window=64, seed=0)            # N=1e4, m=8
 WEB_1M = GraphSpec(n=1_000_000, mean_deg=10.0, window=64, seed=0)           # N=1e6, m=10
 STRESS_16M = GraphSpec(n=1 << 24, mean_deg=16.0, window=256, seed=0)        # N=2^24, m=16
+MID_4M = GraphSpec(n=1 << 22, mean_deg=16.0, window=256, seed=0)            # N=2^22, m=16 (profiling size)
 
 PAGERANK_D = 0.85
 

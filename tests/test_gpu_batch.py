@@ -166,3 +166,29 @@ def test_batch_rejects_bad_arguments():
     assert e.value.status == di.DI_EINVAL
     batch.close()
     g.close()
+
+
+def test_batch_autotune_then_parity(mixed_graphs, tmp_path):
+    rng = np.random.default_rng(21)
+    graphs = [di.Graph.create(rp, col) for rp, col in mixed_graphs[:4]]
+    batch = di.Batch(graphs, [2, 1, 1, 2])
+    items = []
+    for (rp, col), r in zip(mixed_graphs[:4], [2, 1, 1, 2]):
+        for k in range(r):
+            items.append((rp, col, rhs_for(len(rp) - 1, k, rng)))
+    tols = [1e-8 * b.sum() for _, _, b in items]
+    B = [dev(b) for _, _, b in items]
+    H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
+    cache = str(tmp_path / "tune.jsonl")
+    t, secs = di.batch_autotune(batch, B, D, tols, H, None, cache)
+    assert secs > 0 and di.get_tune(batch).as_dict() == t.as_dict()
+    assert '"key": "batch items=6' in open(cache).read()
+    H = [torch.zeros_like(h) for h in H]
+    rc, st, _ = di.di_solve_batched(batch, B, D, tols, H)
+    for (rp, col, b), h, s, tol in zip(items, H, st, tols):
+        x = oracle_x(rp, col, b)
+        assert np.abs(h.cpu().numpy() - x).sum() <= 1e-6 * np.abs(x).sum()
+        stop_ok(rp, col, b, h.cpu().numpy(), tol, s.resid_l1)
+    batch.close()
+    for g in graphs:
+        g.close()

@@ -416,3 +416,48 @@ def test_solve_on_two_source_blocks_meets_the_stop(web5m):
     # (checked against the oracle's solution at a sample of nodes would need
     # its full solve; the bound and the exact residual pin the result here)
     assert np.all(h >= 0)
+
+
+# ---------------------------------------------------------------- push shapes and the autotuner
+
+@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("shape", [(1, 1, 0), (4, 64, 1), (32, 32, 0), (1024, 1 << 30, 2)])
+def test_parity_every_push_shape(web10k, prop, shape):
+    rp, col, b, x = web10k
+    g = di.Graph.create(rp, col)
+    t = di.tune_default()
+    t.thread_max_deg, t.warp_max_deg, t.push_ctas_per_sm = shape
+    di.set_tune(g, t)
+    assert di.get_tune(g).as_dict() == t.as_dict()
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    tol = 1e-8 * b.sum()
+    _, st = di.di_solve(g, dev(b), D, tol, H, None, di.opts_default(propagation=prop))
+    h = H.cpu().numpy()
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    g.close()
+
+
+def test_autotune_keeps_a_shape_and_caches_it(web10k, tmp_path):
+    rp, col, b, x = web10k
+    g = di.Graph.create(rp, col)
+    cache = str(tmp_path / "tune.jsonl")
+    tol = 1e-8 * b.sum()
+    t, secs = di.autotune(g, dev(b), D, tol, None, cache)
+    assert secs > 0 and 1 <= t.thread_max_deg <= 1024
+    assert di.get_tune(g).as_dict() == t.as_dict()
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and '"key": "solve n=2^13' in lines[0]
+    # a second graph of the same size bucket takes the cached shape without timing
+    g2 = di.Graph.create(rp, col)
+    t2, secs2 = di.autotune(g2, dev(b), D, tol, None, cache)
+    assert secs2 == 0.0 and t2.as_dict() == t.as_dict()
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    _, st = di.di_solve(g2, dev(b), D, tol, H)
+    assert np.abs(H.cpu().numpy() - x).sum() <= 1e-6 * np.abs(x).sum()
+    bad = di.tune_default()
+    bad.thread_max_deg = 0
+    with pytest.raises(di.DiError):
+        di.set_tune(g, bad)
+    g.close()
+    g2.close()

@@ -1,8 +1,10 @@
 """The learned warm start on the GPU against the warm-start oracle.
 
 Tolerances, derived from the arithmetic:
-  * features: computed in FP64 and rounded once to FP32 on both sides, so
-    they agree to 2 units in the last place of FP32 (relative 2.4e-7);
+  * features: the device evaluates log1p and 1/outdeg in FP32 (within 1
+    unit in the last place) and sums in FP64, rounding once; composing these
+    gives at most 4 FP32 units in the last place (relative 5e-7) against the
+    oracle's FP64 values rounded to FP32;
   * network output: both sides round the same operands to BF16 (the
     standardised features are chosen BF16-exact), then the device
     accumulates in FP32 where the oracle uses FP64; a first-layer activation
@@ -78,7 +80,7 @@ def test_features_match_oracle(case):
     torch.cuda.synchronize()
     want = ow.features(rp, col, b).astype(np.float32)
     got = feat.cpu().numpy()
-    np.testing.assert_allclose(got, want, rtol=2.4e-7, atol=0)
+    np.testing.assert_allclose(got, want, rtol=5e-7, atol=0)
     g.close()
     m.close()
 
