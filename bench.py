@@ -70,10 +70,11 @@ def parse():
     p.add_argument("--no-l2-window", action="store_true", help="no L2 access-policy windows")
     p.add_argument("--propagation", type=int, default=None,
                    help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push, "
-                        "4 asynchronous push with warp-level tiles")
+                        "4 asynchronous push with warp-level tiles, 5 fused select + push")
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
+    p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
     p.add_argument("--ws-train", type=int, default=200, help="warm start: training graphs")
     p.add_argument("--ws-eval", type=int, default=32, help="warm start: held-out evaluation graphs")
     p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
@@ -329,6 +330,9 @@ def run_native(args, world, rank, local):
     B = torch.from_numpy(b).cuda()
     H = torch.zeros(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+    if args.autotune:
+        di.autotune(g, B, D, tol, opts)
+    shape = di.get_tune(g).as_dict()
 
     for _ in range(max(args.warmup, 0)):
         di.di_solve(g, B, D, tol, H, None, opts)
@@ -447,8 +451,10 @@ def run_native(args, world, rank, local):
                            "l2_window": bool(opts.l2_window),
                            "propagation": ["auto: binned gather / push", "auto: flat gather / push",
                                            "push only", "asynchronous push",
-                                           "asynchronous push, warp-level tiles"][opts.propagation],
+                                           "asynchronous push, warp-level tiles",
+                                           "fused select + push, one launch per level"][opts.propagation],
                            "push_ratio": opts.push_ratio,
+                           "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
                            "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -498,6 +504,8 @@ def run_batch(args, world, rank, local):
         H.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
         tols.append(1e-8 * (1.0 - D))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # frontier tile shape of the batched push, chosen by timing (the autotuner)
+    tune, tune_s = di.batch_autotune(batch, B, D, tols, H, opts)
     for _ in range(max(args.warmup, 0)):
         di.di_solve_batched(batch, B, D, tols, H, opts)
     torch.cuda.synchronize()
@@ -568,6 +576,7 @@ def run_batch(args, world, rank, local):
                 "config": {"workload": WORKLOADS["batch-64x4"][1], "items": info["n_items"],
                            "n_union": info["n_union"], "nnz_union": info["nnz_union"],
                            "tol": "1e-8 |B|_1 per item", "l2": "flushed (256 MiB write) before each timed step",
+                           "push_shape": dict(tune.as_dict(), chosen_by="di_batch_autotune", best_s=tune_s),
                            "level_loop": "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "time_to_tol_ms": 1e3 * secs / args.steps, "gpu_launches": launches, "clocks": clocks}

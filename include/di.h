@@ -87,7 +87,9 @@ typedef struct {
                               is drained with an atomic exchange when its row is pushed, so
                               fluid arriving earlier in the level goes with it; 4: the same
                               asynchronous push with warp-level tiles (each warp drains 32
-                              frontier nodes at a time; no block-wide barrier) */
+                              frontier nodes at a time; no block-wide barrier); 5: the
+                              level in one launch - each CTA selects nodes in its chunks
+                              of F and pushes them at once, with no frontier list */
     int push_ratio;        /* auto: a level is dense (gather) when its active edges times
                               push_ratio reach the edge count; default 8 */
     int exact_residual;    /* form of the exact FP64 residual B + P H - H: 1 gather over the

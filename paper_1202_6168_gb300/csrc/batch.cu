@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
         }
         const int deg = e - b;
         if (deg <= thread_max) {
-            for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
+            auto pw = [&](int32_t c) { push1(c, w); };
+            push_range<8>(pcol, b, e, 1, pw);
         }
         unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
         while (wm) {
@@ -363,7 +364,8 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
             wm &= wm - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const FT mw = __shfl_sync(0xffffffffu, w, src);
-            for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
+            auto pw = [&](int32_t c) { push1(c, mw); };
+            push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
         }
         if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
@@ -376,7 +378,8 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
         for (int h = 0; h < qn; ++h) {
             const int32_t hb = s_qb[h], he = s_qe[h];
             const FT hw = s_qw[h];
-            for (int32_t q = hb + threadIdx.x; q < he; q += kBThreads) push1(__ldcs(pcol + q), hw);
+            auto pw = [&](int32_t c) { push1(c, hw); };
+            push_range<2>(pcol, (int64_t)hb + threadIdx.x, he, kBThreads, pw);
         }
         __syncthreads();
     }

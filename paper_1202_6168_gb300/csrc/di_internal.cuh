@@ -173,9 +173,9 @@ struct di_graph {
     int32_t *pl_b12_off = nullptr, *pl_b12_col = nullptr;   // bins 1-2 edges in bin order
     int32_t *outdeg = nullptr;                            // [n] out-degrees
     int32_t *erow = nullptr;                              // [nnz] destination row of each in-edge
-    // in-edges in source-blocked order (source block of kSrcBlock nodes, then
-    // destination row): bcol = source, brow = destination.  With one block
-    // they alias in_col / erow.
+    // in-edges in source-blocked order (source block of 2^kSrcBlockShift
+    // nodes, then destination row): bcol = source, brow = destination.  Built
+    // on first use; with one block they alias in_col / erow.
     int32_t *bcol = nullptr, *brow = nullptr;
     int n_src_blocks = 1;
     int res_form = 0;             // exact residual: 0 auto, 1 binned gather, 2 source-blocked flat gather
@@ -243,6 +243,27 @@ __device__ __forceinline__ double atomic_exch_fluid(double *p, double v) {
     return __longlong_as_double(static_cast<long long>(old));
 }
 
+// Calls push(c) for the targets c = pcol[q], q = first, first + step, ...
+// < end.  The column indices are loaded kBatch at a time before their
+// pushes are issued, so the loads of a batch are in flight together (the
+// pushes are volatile asm with a memory clobber, which would otherwise
+// serialise each load behind the previous push).
+template <int kBatch, typename Push>
+__device__ __forceinline__ void push_range(const int32_t *__restrict__ pcol, int64_t first, int64_t end, int step,
+                                           Push &push) {
+    for (int64_t q0 = first; q0 < end; q0 += (int64_t)kBatch * step) {
+        int32_t c[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int64_t q = q0 + (int64_t)k * step;
+            c[k] = q < end ? __ldcs(pcol + q) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k)
+            if (q0 + (int64_t)k * step < end) push(c[k]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -295,6 +316,8 @@ __device__ __forceinline__ bool last_block(unsigned int *counter) {
 
 // graph.cu: (re)compute d / outdeg for damping d
 di_status ensure_scale(di_graph *g, double d, cudaStream_t s);
+// graph.cu: the source-blocked in-edge order of the exact residual (lazy)
+di_status ensure_blocked_order(di_graph *g, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
 int push_grid(const di_graph *g);

@@ -191,38 +191,36 @@ __global__ void k_erow(const int32_t *__restrict__ in_rp, int64_t n, int32_t *__
         for (int32_t q = in_rp[k]; q < in_rp[k + 1]; ++q) erow[q] = (int32_t)k;
 }
 
-// Source-blocked order of the in-edges: virtual row v = (j >> shift) * n + k
-// for the edge j -> k.  Count, then fill (order inside a virtual row is
-// arbitrary).
-__global__ void k_vcount(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, int shift,
-                         int32_t *__restrict__ cnt) {
+// Source-blocked order of the in-edges, one source block at a time: count,
+// per destination row k, the in-edges whose source lies in [lo, hi), then
+// copy them in row order (the order inside a row is the in-CSR order).
+__global__ void k_blk_count(const int32_t *__restrict__ in_rp, const int32_t *__restrict__ in_col, int64_t n,
+                            int32_t lo, int32_t hi, int32_t *__restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const int64_t vb = (j >> shift) * n;
-        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) atomicAdd(&cnt[vb + col[e]], 1);
-    }
-}
-
-__global__ void k_vfill(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, int shift,
-                        int32_t *__restrict__ cursor, int32_t *__restrict__ bcol, int32_t *__restrict__ brow) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const int64_t vb = (j >> shift) * n;
-        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) {
-            const int32_t k = col[e];
-            const int32_t pos = atomicAdd(&cursor[vb + k], 1);
-            bcol[pos] = static_cast<int32_t>(j);
-            brow[pos] = k;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        int32_t c = 0;
+        for (int32_t q = in_rp[k]; q < in_rp[k + 1]; ++q) {
+            const int32_t j = in_col[q];
+            c += (j >= lo && j < hi) ? 1 : 0;
         }
+        cnt[k] = c;
     }
 }
 
-// Hot-slot codes (-1 - slot) back to node ids.
-__global__ void k_decode_hot(int32_t *__restrict__ col, int64_t nnz, const int32_t *__restrict__ hot_node) {
+__global__ void k_blk_fill(const int32_t *__restrict__ in_rp, const int32_t *__restrict__ in_col, int64_t n,
+                           int32_t lo, int32_t hi, const int32_t *__restrict__ off, int64_t base,
+                           int32_t *__restrict__ bcol, int32_t *__restrict__ brow) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-        const int32_t c = col[e];
-        if (c < 0) col[e] = hot_node[-1 - c];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        int64_t pos = base + off[k];
+        for (int32_t q = in_rp[k]; q < in_rp[k + 1]; ++q) {
+            const int32_t j = in_col[q];
+            if (j >= lo && j < hi) {
+                bcol[pos] = j;
+                brow[pos] = static_cast<int32_t>(k);
+                ++pos;
+            }
+        }
     }
 }
 
@@ -392,6 +390,63 @@ di_status build_pull_plan(di_graph *g, const std::vector<int32_t> &hin) {
 
 }  // namespace
 
+// Builds, on first use, the in-edges in source-blocked order (blocks of
+// 2^kSrcBlockShift sources, then destination row).  With one block it is the
+// in-CSR order itself.
+di_status ensure_blocked_order(di_graph *g, cudaStream_t s) {
+    if (g->bcol) return DI_OK;
+    const int64_t n = g->n, nnz = g->nnz;
+    g->n_src_blocks = (int)((n + (1LL << kSrcBlockShift) - 1) >> kSrcBlockShift);
+    if (g->n_src_blocks <= 1 || nnz == 0) {
+        g->n_src_blocks = 1;
+        g->bcol = g->in_col;
+        g->brow = g->erow;
+        return DI_OK;
+    }
+    DevPtrs tmp;
+    int32_t *cnt = nullptr, *off = nullptr, *bcol = nullptr, *brow = nullptr;
+    const int nchunks = static_cast<int>((n + kScanChunkElems - 1) / kScanChunkElems);
+    int64_t *chunk = nullptr;
+    DI_CUDA_TRY(tmp.alloc(&cnt, n));
+    DI_CUDA_TRY(tmp.alloc(&off, n + 1));
+    DI_CUDA_TRY(tmp.alloc(&chunk, nchunks));
+    DI_CUDA_TRY(tmp.alloc(&bcol, nnz));
+    DI_CUDA_TRY(tmp.alloc(&brow, nnz));
+    const int cap = g->num_sms * 16;
+    std::vector<int64_t> hc(nchunks);
+    int64_t base = 0;
+    for (int b = 0; b < g->n_src_blocks; ++b) {
+        const int64_t lo64 = (int64_t)b << kSrcBlockShift;
+        const int32_t lo = (int32_t)lo64, hi = (int32_t)std::min<int64_t>(n, lo64 + (1LL << kSrcBlockShift));
+        k_blk_count<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->in_rp, g->in_col, n, lo, hi, cnt);
+        k_chunk_sums<<<nchunks, kThreads, 0, s>>>(cnt, n, chunk);
+        DI_CUDA_TRY(cudaMemcpyAsync(hc.data(), chunk, nchunks * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t run = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int64_t v = hc[c];
+            hc[c] = run;
+            run += v;
+        }
+        DI_CUDA_TRY(cudaMemcpyAsync(chunk, hc.data(), nchunks * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_chunk_scan<<<nchunks, kThreads, 0, s>>>(cnt, n, chunk, off);
+        k_blk_fill<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->in_rp, g->in_col, n, lo, hi, off, base, bcol,
+                                                                   brow);
+        base += run;
+    }
+    DI_CUDA_TRY(cudaGetLastError());
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (base != nnz) {
+        set_error("blocked order: placed %lld of %lld in-edges", (long long)base, (long long)nnz);
+        return DI_ECUDA;
+    }
+    tmp.release(bcol);
+    tmp.release(brow);
+    g->bcol = bcol;
+    g->brow = brow;
+    return DI_OK;
+}
+
 PullPlan pull_plan_of(const di_graph *g) {
     PullPlan p;
     p.rows = g->pl_rows;
@@ -545,47 +600,6 @@ extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_
     DI_CUDA_TRY(cudaStreamSynchronize(s));
     g->n_hot = nh;
 
-    // 7. in-edges in source-blocked order for the exact residual (alias of the
-    //    in-CSR order when every source fits in one block)
-    g->n_src_blocks = (int)((n + (1LL << kSrcBlockShift) - 1) >> kSrcBlockShift);
-    if (g->n_src_blocks <= 1) {
-        g->bcol = g->in_col;
-        g->brow = g->erow;
-    } else if (nnz > 0) {
-        const int64_t nv = (int64_t)g->n_src_blocks * n;
-        if (nv + 1 > INT32_MAX) { set_error("di_graph_create: too many nodes for the blocked order"); return DI_EINVAL; }
-        int32_t *vcnt = nullptr, *voff = nullptr;
-        DI_CUDA_TRY(tmp.alloc(&vcnt, nv));
-        DI_CUDA_TRY(tmp.alloc(&voff, nv + 1));
-        DI_CUDA_TRY(cudaMemsetAsync(vcnt, 0, nv * sizeof(int32_t), s));
-        int32_t *dec = nullptr;   // targets with the hot-slot codes of pcol decoded
-        DI_CUDA_TRY(tmp.alloc(&dec, nnz));
-        DI_CUDA_TRY(cudaMemcpyAsync(dec, g->pcol, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        k_decode_hot<<<grid_for(nnz, kThreads, cap), kThreads, 0, s>>>(dec, nnz, g->hot_node);
-        k_vcount<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, dec, n, kSrcBlockShift, vcnt);
-        const int vchunks = static_cast<int>((nv + kScanChunkElems - 1) / kScanChunkElems);
-        int64_t *vchunk = nullptr;
-        DI_CUDA_TRY(tmp.alloc(&vchunk, vchunks));
-        k_chunk_sums<<<vchunks, kThreads, 0, s>>>(vcnt, nv, vchunk);
-        std::vector<int64_t> hv(vchunks);
-        DI_CUDA_TRY(cudaMemcpyAsync(hv.data(), vchunk, vchunks * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        DI_CUDA_TRY(cudaStreamSynchronize(s));
-        int64_t vrun = 0;
-        for (int c = 0; c < vchunks; ++c) {
-            const int64_t v = hv[c];
-            hv[c] = vrun;
-            vrun += v;
-        }
-        if (vrun != nnz) { set_error("di_graph_create: blocked order counted %lld edges != nnz", (long long)vrun); return DI_ECUDA; }
-        DI_CUDA_TRY(cudaMemcpyAsync(vchunk, hv.data(), vchunks * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        k_chunk_scan<<<vchunks, kThreads, 0, s>>>(vcnt, nv, vchunk, voff);
-        DI_CUDA_TRY(cudaMalloc(&g->bcol, nnz * sizeof(int32_t)));
-        DI_CUDA_TRY(cudaMalloc(&g->brow, nnz * sizeof(int32_t)));
-        k_vfill<<<grid_for(n, kThreads, cap), kThreads, 0, s>>>(g->rp, dec, n, kSrcBlockShift, voff, g->bcol,
-                                                                g->brow);
-        DI_CUDA_TRY(cudaGetLastError());
-        DI_CUDA_TRY(cudaStreamSynchronize(s));
-    }
     // 8. segments of the long in-rows (exact residual load balance), two granularities
     {
         std::vector<int32_t> hin(n + 1);

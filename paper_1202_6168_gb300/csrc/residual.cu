@@ -135,15 +135,19 @@ __global__ void __launch_bounds__(kResThreads) k_resb_init(const SolveDesc *__re
 
 // acc_k += g_j over the in-edges j -> k, taken in source-blocked order: at any
 // time the grid works inside one block of 2^22 sources, whose 32 MB of g stay
-// in L2 while the edge arrays stream.  16 consecutive edges per thread; runs
-// of equal destination are summed and added with one red.global.add.f64.
-__global__ void __launch_bounds__(kResThreads) k_resb_flat(const SolveState *__restrict__ st, int mode,
-                                                           const int32_t *__restrict__ bcol,
-                                                           const int32_t *__restrict__ brow,
-                                                           const double *__restrict__ g, double *__restrict__ acc,
-                                                           int64_t nnz) {
+// in L2 while the edge arrays stream.  8 consecutive edges per thread (two
+// int4 loads of each index array, 8 independent gathers; few registers, so
+// 6 CTAs of 256 fit per SM to hide the latency); runs of equal destination
+// are summed and added with one red.global.add.f64.
+constexpr int kResbEdges = 8;
+
+__global__ void __launch_bounds__(kResThreads, 6) k_resb_flat(const SolveState *__restrict__ st, int mode,
+                                                              const int32_t *__restrict__ bcol,
+                                                              const int32_t *__restrict__ brow,
+                                                              const double *__restrict__ g, double *__restrict__ acc,
+                                                              int64_t nnz) {
     if (mode == RES_LEVEL && !st->do_recompute) return;
-    constexpr int kE = 16;
+    constexpr int kE = kResbEdges;
     const int64_t nch = (nnz + kE - 1) / kE;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += stride) {
@@ -272,7 +276,12 @@ void launch_residual(di_graph *g, int fluid_fp64, ResMode mode, cudaStream_t s) 
     Workspace &ws = g->ws;
     if (residual_blocked(g)) {
         const int grid = g->grid_res;
-        const int flat = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)grid, (g->nnz / 16 + kResThreads) / kResThreads));
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_resb_flat, kResThreads, 0) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const int flat = (int)std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)per_sm * g->num_sms, (g->nnz / kResbEdges + kResThreads) / kResThreads));
         k_resb_init<<<grid, kResThreads, 0, s>>>(ws.desc, ws.st, (int)mode, g->s64, ws.g, ws.acc, g->n);
         k_resb_flat<<<flat, kResThreads, 0, s>>>(ws.st, (int)mode, g->bcol, g->brow, ws.g, ws.acc, g->nnz);
         if (fluid_fp64)
@@ -314,6 +323,7 @@ extern "C" DI_API di_status di_residual(di_graph *g, const double *B, double d, 
     DI_TRY(ensure_workspace(g));
     DI_TRY(ensure_scale(g, d, s));
     g->res_form = 0;
+    DI_TRY(ensure_blocked_order(g, s));
     Workspace &ws = g->ws;
     // the workspace descriptor is shared with di_solve: stage it through the pinned mirror
     DI_CUDA_TRY(cudaStreamSynchronize(s));

@@ -160,8 +160,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const SolveDesc *__restri
 // ------------------------------------------------------------------ asynchronous push level
 
 // Scan of one level of the asynchronous design: frontier compaction in node
-// order within 2048-node blocks (warp ballots, one prefix, one atomic per
-// block) with the L1 norm and max of the fluid fused into the same read.
+// order (warp ballots and one prefix per 2048-node chunk) with the L1 norm and
+// max of the fluid fused into the first read.  Two passes over each CTA's
+// chunks - count, reserve the CTA's slice with one atomic, then write - so
+// the frontier counter sees one atomic per CTA instead of one per chunk.
 // Its last CTA decides the level: push the frontier (T <- T / alpha), lower T
 // to the largest fluid after an empty scan, or request an exact residual to
 // confirm a stop (no push).  ctl: 1 in a CUDA graph, 2 host-driven.
@@ -191,46 +193,72 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_level(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     __shared__ int s_cnt[kScanItems * (kScanThreads / 32)];
-    __shared__ int s_base;
+    __shared__ int s_base, s_wcount[kScanThreads / 32];
+    // pass 1: L1 norm, max and the number of selected nodes of all this
+    // CTA's chunks; one atomic reserves the CTA's slice of the frontier
     AT acc = 0;
     FT mx = 0;
+    int my_sel = 0;
     for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
-        unsigned masks[kScanItems];
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t idx = c0 + k * kScanThreads + threadIdx.x;
             FT v = 0;
             if (idx < n) v = fabs(F[idx]);
-            const bool sel = idx < n && v >= Tc && v > FT(0);
-            masks[k] = __ballot_sync(0xffffffffu, sel);
             acc += static_cast<AT>(v);
             mx = max(mx, v);
-            if (lane == 0) s_cnt[k * (kScanThreads / 32) + warp] = __popc(masks[k]);
+            my_sel += (idx < n && v >= Tc && v > FT(0)) ? 1 : 0;
         }
-        __syncthreads();
-        if (warp == 0) {   // exclusive scan of the 64 counts in node order
-            const int a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
-            int incl = a + b;
+    }
+    my_sel = warp_sum(my_sel);
+    if (lane == 0) s_wcount[warp] = my_sel;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int total = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) total += s_wcount[w];
+        s_base = total ? atomicAdd(&st->nfront, total) : -1;
+    }
+    __syncthreads();
+    // pass 2 (only if this CTA selected anything): the same reads, now from
+    // L2, write the selected ids in node order into the reserved slice
+    int base = s_base;
+    if (base >= 0) {
+        for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
+            unsigned masks[kScanItems];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
+            for (int k = 0; k < kScanItems; ++k) {
+                const int64_t idx = c0 + k * kScanThreads + threadIdx.x;
+                FT v = 0;
+                if (idx < n) v = fabs(F[idx]);
+                const bool sel = idx < n && v >= Tc && v > FT(0);
+                masks[k] = __ballot_sync(0xffffffffu, sel);
+                if (lane == 0) s_cnt[k * (kScanThreads / 32) + warp] = __popc(masks[k]);
             }
-            const int excl = incl - a - b;
-            s_cnt[2 * lane] = excl;
-            s_cnt[2 * lane + 1] = excl + a;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane == 0) s_base = total ? atomicAdd(&st->nfront, total) : 0;
-        }
-        __syncthreads();
-        const int base = s_base;
+            __syncthreads();
+            if (warp == 0) {   // exclusive scan of the 64 counts in node order
+                const int a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
+                int incl = a + b;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            if ((masks[k] >> lane) & 1u)
-                front[base + s_cnt[k * (kScanThreads / 32) + warp] + __popc(masks[k] & lt_mask)] =
-                    static_cast<int32_t>(c0 + k * kScanThreads + threadIdx.x);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int excl = incl - a - b;
+                s_cnt[2 * lane] = excl;
+                s_cnt[2 * lane + 1] = excl + a;
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (lane == 0) s_wcount[0] = total;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) {
+                if ((masks[k] >> lane) & 1u)
+                    front[base + s_cnt[k * (kScanThreads / 32) + warp] + __popc(masks[k] & lt_mask)] =
+                        static_cast<int32_t>(c0 + k * kScanThreads + threadIdx.x);
+            }
+            base += s_wcount[0];
+            __syncthreads();
         }
-        __syncthreads();
     }
     double s = static_cast<double>(acc);
     double m = static_cast<double>(mx);
@@ -345,7 +373,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
         }
         const int deg = e - b;
         if (deg <= thread_max) {
-            for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
+            auto pw = [&](int32_t c) { push1(c, w); };
+            push_range<8>(pcol, b, e, 1, pw);
         }
         unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
         while (wm) {
@@ -353,7 +382,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
             wm &= wm - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const FT mw = __shfl_sync(0xffffffffu, w, src);
-            for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
+            auto pw = [&](int32_t c) { push1(c, mw); };
+            push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
         }
         if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
@@ -366,7 +396,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
         for (int h = 0; h < qn; ++h) {
             const int32_t hb = s_qb[h], he = s_qe[h];
             const FT hw = s_qw[h];
-            for (int32_t q = hb + threadIdx.x; q < he; q += kPushThreads) push1(__ldcs(pcol + q), hw);
+            auto pw = [&](int32_t c) { push1(c, hw); };
+            push_range<2>(pcol, (int64_t)hb + threadIdx.x, he, kPushThreads, pw);
         }
         __syncthreads();
     }
@@ -441,15 +472,18 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
                 my_edges += static_cast<unsigned long long>(e - b);
             }
             const int deg = e - b;
-            if (deg <= thread_max)
-                for (int32_t q = b; q < e; ++q) push1(__ldcs(pcol + q), w);
+            if (deg <= thread_max) {
+                auto pw = [&](int32_t c) { push1(c, w); };
+                push_range<8>(pcol, b, e, 1, pw);
+            }
             unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max);
             while (wm) {
                 const int src = __ffs(wm) - 1;
                 wm &= wm - 1;
                 const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
                 const FT mw = __shfl_sync(0xffffffffu, w, src);
-                for (int32_t q = mb + lane; q < me; q += 32) push1(__ldcs(pcol + q), mw);
+                auto pw = [&](int32_t c) { push1(c, mw); };
+            push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
             }
         }
     }
@@ -463,6 +497,157 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
     if (lane == 0 && my_nodes) {
         atomicAdd(&st->node_diff, my_nodes);
         atomicAdd(&st->edge_diff, my_edges);
+    }
+}
+
+// One threshold level in one launch (propagation 5): every CTA walks its
+// 2048-node chunks of the fluid in grid-stride order, selects |F_i| >= T
+// (the L1 norm and max of what it reads go to the control step) and pushes
+// the nodes it selected at once: f = atomicExch(F_i, 0), H_i += f, and
+// F_k += (d / outdeg_i) f over the out-row, by the node's lane for a row of
+// at most thread_max edges and by the whole warp for a longer one.  There is
+// no frontier list and no separate scan launch; fluid that reaches a chunk
+// before the CTA reads it is selected in this level, fluid that arrives
+// later waits for the next (any order converges, Sec. 2).  The last CTA to
+// finish runs the control step of the level.
+template <typename FT>
+__global__ void __launch_bounds__(kPushThreads) k_level_fused(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ rp,
+    const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node, int n_hot, const FT *__restrict__ scale,
+    int64_t n, double *__restrict__ part_sum, double *__restrict__ part_max, cudaGraphConditionalHandle h_while,
+    cudaGraphConditionalHandle h_rec, int ctl) {
+    {
+        const int done0 = st->done;
+        const int stop = done0 ? done0 : (st->level >= desc->max_levels ? 2 : 0);
+        if (stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->done = stop;
+                if (ctl == 1) {
+                    cudaGraphSetConditional(h_rec, 0);
+                    cudaGraphSetConditional(h_while, 0);
+                }
+            }
+            return;
+        }
+    }
+    using AT = typename Acc<FT>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FT *s_hot = reinterpret_cast<FT *>(smem_raw);
+    for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
+    __syncthreads();
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    double *__restrict__ H = desc->H;
+    const FT Tc = thr_cast(st->T, FT(0));
+    const int lane = threadIdx.x & 31;
+    const uint64_t keep = l2_keep_policy();
+    const int thread_max = desc->thread_max;
+    auto push1 = [&](int32_t c, FT w) {
+        if (c >= 0) red_add_keep(F + c, w, keep);
+        else atomicAdd(&s_hot[-1 - c], w);
+    };
+    AT acc = 0;
+    FT mx = 0;
+    unsigned long long my_edges = 0, my_nodes = 0;
+    for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
+#pragma unroll 1
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t idx = c0 + k * kPushThreads + threadIdx.x;
+            FT v = FT(0);
+            if (idx < n) v = F[idx];
+            const FT a = fabs(v);
+            acc += static_cast<AT>(a);
+            mx = max(mx, a);
+            const bool sel = idx < n && a >= Tc && a > FT(0);
+            if (!__any_sync(0xffffffffu, sel)) continue;
+            int32_t b = 0, e = 0;
+            FT w = FT(0);
+            if (sel) {
+                b = __ldcs(rp + idx);
+                e = __ldcs(rp + idx + 1);
+                const FT f = atomic_exch_keep(F + idx, FT(0), keep);
+                __stcs(H + idx, __ldcs(H + idx) + static_cast<double>(f));
+                w = f * __ldcs(scale + idx);
+                my_nodes += 1;
+                my_edges += static_cast<unsigned long long>(e - b);
+            }
+            const int deg = e - b;
+            if (deg <= thread_max) {
+                auto pw = [&](int32_t c) { push1(c, w); };
+                push_range<8>(pcol, b, e, 1, pw);
+            }
+            unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max);
+            while (wm) {
+                const int src = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
+                const FT mw = __shfl_sync(0xffffffffu, w, src);
+                auto pw = [&](int32_t c) { push1(c, mw); };
+                push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
+            }
+        }
+    }
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
+        const FT hv = s_hot[sl];
+        if (hv != FT(0)) red_add_keep(F + hot_node[sl], hv, keep);
+    }
+    my_edges = warp_sum(my_edges);
+    my_nodes = warp_sum(my_nodes);
+    if (lane == 0 && my_nodes) {
+        atomicAdd(&st->node_diff, my_nodes);
+        atomicAdd(&st->edge_diff, my_edges);
+        atomicAdd(&st->lvl_nodes, my_nodes);
+    }
+    double s = static_cast<double>(acc);
+    double m = static_cast<double>(mx);
+    block_sum_max<kPushThreads>(s, m);
+    if (threadIdx.x == 0) { part_sum[blockIdx.x] = s; part_max[blockIdx.x] = m; }
+    if (!last_block(&st->scan_blocks)) return;
+    double ts = 0.0, tm = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) { ts += part_sum[i]; tm = fmax(tm, part_max[i]); }
+    block_sum_max<kPushThreads>(ts, tm);
+    if (threadIdx.x != 0) return;
+
+    // control step after the level's pushes
+    const unsigned long long lnodes = st->lvl_nodes;
+    double T = st->T;
+    int level = st->level, since = st->since_recompute, iters = st->body_iters;
+    const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
+    const double tol = desc->tol, alpha = desc->alpha;
+    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    int done = 0, rec = 0;
+    if (!isfinite(ts)) {
+        done = 3;
+    } else {
+        if (lnodes > 0) {
+            level += 1;
+            since += 1;
+            T = T / alpha;
+            if (!fp64 && R > 0 && since >= R) rec = 1;
+        } else if (tm > 0.0) {
+            for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+        }
+        if (ts * est <= tol) {            // the fluid read before the pushes already meets tol
+            rec = 1;
+            st->confirming = 1;
+            st->r_confirm = ts * est;
+        }
+    }
+    iters += 1;
+    if (!done && iters >= max_iters) done = 2;
+    if (done) rec = 0;
+    st->r_scan = ts;
+    st->max_scan = tm;
+    st->T = T;
+    st->level = level;
+    st->since_recompute = since;
+    st->body_iters = iters;
+    st->lvl_nodes = 0;
+    st->do_recompute = rec;
+    if (done) st->done = done;
+    if (ctl == 1) {
+        cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
+        if (done) cudaGraphSetConditional(h_while, 0);
     }
 }
 
@@ -930,6 +1115,18 @@ void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
 }
 
 template <typename FT>
+void launch_fused(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
+                  int l2) {
+    Workspace &ws = g->ws;
+    const cudaAccessPolicyWindow *win = l2_window(g, 0, sizeof(FT) == 8, l2);
+    const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
+    const int grid = std::max(1, std::min(push_grid(g), (int)((g->n + kScanChunk - 1) / kScanChunk)));
+    launch_ex(k_level_fused<FT>, grid, kPushThreads, g->n_hot * sizeof(FT), s, win, (const SolveDesc *)ws.desc, ws.st,
+              (const int32_t *)g->rp, (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale,
+              (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
+}
+
+template <typename FT>
 void launch_select(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hp,
                    cudaGraphConditionalHandle hr, int ctl, int) {
     const cudaAccessPolicyWindow *win = nullptr;   // elementwise streaming pass
@@ -1008,7 +1205,11 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraph_t capg = nullptr;
     cudaGraph_t ended = nullptr;
     DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (prop >= 3) {
+    if (prop == 5) {
+        // body: k_level_fused -> IF(exact residual)
+        if (fp64) launch_fused<double>(g, cs, sg.h_while, sg.h_if, 1, win);
+        else launch_fused<float>(g, cs, sg.h_while, sg.h_if, 1, win);
+    } else if (prop >= 3) {
         // body: k_scan_level -> k_push_async (or k_push_warp) -> IF(exact residual)
         if (fp64) launch_async<double>(g, cs, sg.h_while, sg.h_if, 1, win, prop);
         else launch_async<float>(g, cs, sg.h_while, sg.h_if, 1, win, prop);
@@ -1078,7 +1279,7 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("di_solve: tol = %g must be finite and > 0", tol); return DI_EINVAL; }
     if (!(o->alpha > 1.0) || !std::isfinite(o->alpha)) { set_error("di_solve: alpha = %g must be > 1", o->alpha); return DI_EINVAL; }
     if (o->max_levels < 0 || o->recompute_every < 0) { set_error("di_solve: negative max_levels or recompute_every"); return DI_EINVAL; }
-    if (o->propagation < 0 || o->propagation > 4) { set_error("di_solve: propagation = %d outside [0, 4]", o->propagation); return DI_EINVAL; }
+    if (o->propagation < 0 || o->propagation > 5) { set_error("di_solve: propagation = %d outside [0, 5]", o->propagation); return DI_EINVAL; }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     return DI_OK;
 }
@@ -1161,6 +1362,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     if (!fp64 && !ws.w32) DI_CUDA_TRY(dmalloc(&ws.w32, g->n));
     DI_TRY(ensure_scale(g, d, s));
     g->res_form = o.exact_residual;
+    if (g->res_form != 1) DI_TRY(ensure_blocked_order(g, s));
     if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
 
     // descriptor (the previous call has completed: every solve synchronises)
@@ -1232,7 +1434,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             for (int l = 0; l < kBatch; ++l) {
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
-                if (o.propagation >= 3) {
+                if (o.propagation == 5) {
+                    if (fp64) launch_fused<double>(g, s, 0, 0, 2, win);
+                    else launch_fused<float>(g, s, 0, 0, 2, win);
+                } else if (o.propagation >= 3) {
                     if (fp64) launch_async<double>(g, s, 0, 0, 2, win, o.propagation);
                     else launch_async<float>(g, s, 0, 0, 2, win, o.propagation);
                 } else if (fp64) {
@@ -1247,7 +1452,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                 DI_CUDA_TRY(cudaEventRecord(e[1], s));
                 launch_residual(g, fp64, RES_LEVEL, s);
                 DI_CUDA_TRY(cudaEventRecord(e[2], s));
-                host_launches += (o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
+                host_launches += (o.propagation == 5 ? 1 : o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
             }
             DI_CUDA_TRY(cudaGetLastError());
             DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -1308,7 +1513,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         } else {
             // per live level: select + one propagation kernel; the level that
             // finds the loop finished; the exact residuals
-            launches += 2LL * st.body_iters + 1 + (long long)rk * st.recomputes;
+            launches += (o.propagation == 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
         }
         if (refresh) launches += rk;        // final residual refresh
         stats->gpu_launches = launches;

@@ -48,9 +48,36 @@ constexpr int kTmp = 5;                   // FP32 temporaries per node: ld, s, x
 
 // ------------------------------------------------------------------ features
 
-// Feature arithmetic: the logarithms and reciprocals are FP32 (GB300 runs
-// FP64 at a small fraction of the FP32 rate, and the features feed a BF16
-// network); every sum over in-edges is accumulated in FP64 and rounded once.
+// Feature arithmetic is FP32: GB300 runs FP64 at a small fraction of the
+// FP32 rate (an FP64 sum per in-edge kept its FP64 pipe 84% busy), and the
+// features feed a BF16 network.  Sums over in-edges are compensated
+// (Neumaier): the running sum carries its rounding errors in a second float,
+// so the result is within about 2 units in the last place of the exact sum
+// of the (non-negative) terms whatever the row length.
+struct CSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ void add(const CSum &o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+__device__ __forceinline__ CSum warp_csum(CSum v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        CSum w;
+        w.s = __shfl_xor_sync(0xffffffffu, v.s, o);
+        w.c = __shfl_xor_sync(0xffffffffu, v.c, o);
+        v.add(w);
+    }
+    return v;
+}
 //
 // x0 = log(1 + indeg), x1 = log(1 + outdeg), x8 = N B_i; temporaries
 // ld_i = log(1 + indeg) and s_i = 1 / outdeg (0 for a dangling node).
@@ -75,36 +102,36 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__res
 //   HOP 1: (ld_j, ld_j, s_j) summed, maximised, summed -> x2, x3, a1
 //   HOP 2: (x2_j, x3_j, s_j a1_j)                      -> x4, x5, a2
 template <int HOP>
-__device__ __forceinline__ void feat_visit(const float *__restrict__ tmp, int64_t n, int32_t j, double &u,
-                                           double &m, double &v) {
+__device__ __forceinline__ void feat_visit(const float *__restrict__ tmp, int64_t n, int32_t j, CSum &u, float &m,
+                                           CSum &v) {
     if (HOP == 1) {
         const float l = tmp[j];
-        u += (double)l;
-        m = fmax(m, (double)l);
-        v += (double)tmp[n + j];
+        u.add(l);
+        m = fmaxf(m, l);
+        v.add(tmp[n + j]);
     } else {
-        u += (double)tmp[2 * n + j];
-        m = fmax(m, (double)tmp[3 * n + j]);
-        v += (double)(tmp[n + j] * tmp[4 * n + j]);
+        u.add(tmp[2 * n + j]);
+        m = fmaxf(m, tmp[3 * n + j]);
+        v.add(tmp[n + j] * tmp[4 * n + j]);
     }
 }
 
 // Outputs of node i from its in-row sums (u, v), max m and length len.
 template <int HOP>
 __device__ __forceinline__ void feat_emit(float *__restrict__ tmp, float *__restrict__ feat, int64_t n, int64_t i,
-                                          int len, double u, double m, double v) {
-    const float mean = len > 0 ? (float)(u / (double)len) : 0.0f;
+                                          int len, float u, float m, float v) {
+    const float mean = len > 0 ? u / (float)len : 0.0f;
     if (HOP == 1) {
         tmp[2 * n + i] = mean;
-        tmp[3 * n + i] = (float)m;
-        tmp[4 * n + i] = (float)v;
+        tmp[3 * n + i] = m;
+        tmp[4 * n + i] = v;
         feat[i * kNF + 2] = mean;
-        feat[i * kNF + 3] = (float)m;
+        feat[i * kNF + 3] = m;
     } else {
         feat[i * kNF + 4] = mean;
-        feat[i * kNF + 5] = (float)m;
+        feat[i * kNF + 5] = m;
         feat[i * kNF + 6] = log1pf(tmp[4 * n + i]);
-        feat[i * kNF + 7] = log1pf((float)v);
+        feat[i * kNF + 7] = log1pf(v);
     }
 }
 
@@ -124,7 +151,8 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__rest
         int32_t b = 0, e = 0;
         if (i < n) { b = in_rp[i]; e = in_rp[i + 1]; }
         const int len = e - b;
-        double u = 0.0, m = 0.0, v = 0.0;
+        CSum u, v;
+        float m = 0.f;
         if (len <= 32)
             for (int32_t q = b; q < e; ++q) feat_visit<HOP>(tmp, n, in_col[q], u, m, v);
         unsigned big = __ballot_sync(0xffffffffu, len > 32 && len <= kBin4Max);
@@ -132,14 +160,15 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__rest
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
-            double pu = 0.0, pm = 0.0, pv = 0.0;
+            CSum pu, pv;
+            float pm = 0.f;
             for (int32_t q = mb + lane; q < me; q += 32) feat_visit<HOP>(tmp, n, in_col[q], pu, pm, pv);
-            pu = warp_sum(pu);
+            pu = warp_csum(pu);
             pm = warp_max(pm);
-            pv = warp_sum(pv);
+            pv = warp_csum(pv);
             if (lane == src) { u = pu; m = pm; v = pv; }
         }
-        if (i < n && len <= kBin4Max) feat_emit<HOP>(tmp, feat, n, i, len, u, m, v);
+        if (i < n && len <= kBin4Max) feat_emit<HOP>(tmp, feat, n, i, len, u.value(), m, v.value());
     }
 }
 
@@ -153,22 +182,26 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
                                                            int64_t nseg, const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col, int64_t n,
                                                            const float *__restrict__ tmp, double *__restrict__ lacc) {
-    __shared__ double su[kFeatThreads / 32], sm[kFeatThreads / 32], sv[kFeatThreads / 32];
+    __shared__ CSum su[kFeatThreads / 32], sv[kFeatThreads / 32];
+    __shared__ float sm[kFeatThreads / 32];
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t row = seg_row[sg];
         const int32_t b = seg_beg[sg];
         const int32_t end = in_rp[row + 1];
         const int32_t e = b + kPullSeg < end ? b + kPullSeg : end;
-        double u = 0.0, m = 0.0, v = 0.0;
-        for (int32_t q = b + threadIdx.x; q < e; q += kFeatThreads) feat_visit<HOP>(tmp, n, in_col[q], u, m, v);
-        u = warp_sum(u);
-        m = warp_max(m);
-        v = warp_sum(v);
+        CSum cu, cv;
+        float cm = 0.f;
+        for (int32_t q = b + threadIdx.x; q < e; q += kFeatThreads) feat_visit<HOP>(tmp, n, in_col[q], cu, cm, cv);
+        cu = warp_csum(cu);
+        cm = warp_max(cm);
+        cv = warp_csum(cv);
         const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) { su[w] = u; sm[w] = m; sv[w] = v; }
+        if (l == 0) { su[w] = cu; sm[w] = cm; sv[w] = cv; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int k = 1; k < kFeatThreads / 32; ++k) { u += su[k]; m = fmax(m, sm[k]); v += sv[k]; }
+            for (int k = 1; k < kFeatThreads / 32; ++k) { cu.add(su[k]); cm = fmaxf(cm, sm[k]); cv.add(sv[k]); }
+            // one FP64 atomic per segment: the few hub rows add their segments exactly
+            const double u = (double)cu.s + (double)cu.c, m = (double)cm, v = (double)cv.s + (double)cv.c;
             int lo = 0, hi = n_long;                 // long row r: lseg0[r] <= sg < lseg0[r + 1]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) / 2;
@@ -189,7 +222,8 @@ __global__ void k_feat_long(const int32_t *__restrict__ lrows, int n_long, const
                             float *__restrict__ feat) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_long; r += gridDim.x * blockDim.x) {
         const int32_t i = lrows[r];
-        feat_emit<HOP>(tmp, feat, n, i, in_rp[i + 1] - in_rp[i], lacc[3 * r], lacc[3 * r + 1], lacc[3 * r + 2]);
+        feat_emit<HOP>(tmp, feat, n, i, in_rp[i + 1] - in_rp[i], (float)lacc[3 * r], (float)lacc[3 * r + 1],
+                       (float)lacc[3 * r + 2]);
     }
 }
 

@@ -325,7 +325,7 @@ def test_device_resident_csr_input(web10k):
 
 # ---------------------------------------------------------------- every propagation mode
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_parity_every_propagation_mode(web10k, prop, fp64):
     rp, col, b, x = web10k
@@ -336,7 +336,7 @@ def test_parity_every_propagation_mode(web10k, prop, fp64):
         check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5])
 def test_personalised_sparse_levels_every_mode(prop):
     # a personalised right-hand side keeps the early frontiers tiny (scatter levels)
     rp, col = gg.generate(gg.GraphSpec(n=30000, mean_deg=9, seed=8))
@@ -348,7 +348,7 @@ def test_personalised_sparse_levels_every_mode(prop):
     check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [1, 3])
+@pytest.mark.parametrize("prop", [1, 3, 5])
 def test_timing_mode_matches(web10k, prop):
     rp, col, b, x = web10k
     tol = 1e-8 * b.sum()
@@ -420,7 +420,7 @@ def test_solve_on_two_source_blocks_meets_the_stop(web5m):
 
 # ---------------------------------------------------------------- push shapes and the autotuner
 
-@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("prop", [3, 4, 5])
 @pytest.mark.parametrize("shape", [(1, 1, 0), (4, 64, 1), (32, 32, 0), (1024, 1 << 30, 2)])
 def test_parity_every_push_shape(web10k, prop, shape):
     rp, col, b, x = web10k
