@@ -172,6 +172,24 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
+def level_traffic(workload: str, prec: str, propagation: int):
+    """DRAM bytes (read + write) of one level's kernels (selection + push),
+    averaged over the levels of one solve, from the ncu capture summarised in
+    profiles/level_traffic.txt (lines: workload precision propagation bytes);
+    None when no capture of this configuration is recorded."""
+    path = os.path.join(REPO, "profiles", "level_traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and not line.startswith("#") and parts[0] == workload and parts[1] == prec \
+                        and parts[2] == str(propagation):
+                    return float(parts[3])
+    except OSError:
+        return None
+    return None
+
+
 def cpu_baseline(rp, col, b, tol):
     """The CPU oracle as it stands, on one host core, one full solve."""
     from oracle import diter as od
@@ -376,7 +394,7 @@ def run_native(args, world, rank, local):
                                l2_window=opts.l2_window, propagation=opts.propagation,
                                push_ratio=opts.push_ratio, exact_residual=opts.exact_residual)
         te = tn = 0
-        tpush = trec = 0.0
+        tpush = trec = tsel = 0.0
         npush = 0
         reps = min(3, max(args.steps, 1))
         for _ in range(reps):
@@ -386,27 +404,20 @@ def run_native(args, world, rank, local):
             tn += ts.node_diffusions
             tpush += ts.level_seconds
             trec += ts.recompute_seconds
+            tsel += ts.select_seconds
             npush += ts.level_launches
         alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
         achieved = alg_bytes / tpush / 1e9
         peak, peak_src = measured_hbm_peak()
-        traffic = None
-        prof = os.path.join(REPO, "profiles", "push_traffic.json")
-        if os.path.exists(prof):
-            try:
-                with open(prof) as f:
-                    pt = json.load(f)
-                if pt.get("workload") == args.workload and pt.get("precision") == prec:
-                    traffic = pt.get("dram_bytes_per_launch")
-            except (OSError, ValueError):
-                traffic = None
+        traffic = level_traffic(args.workload, prec, opts.propagation)
         extras["roofline"] = {"bound": "hbm", "kernel": f"k_level<{'double' if args.fp64 else 'float'}> (scan + push)",
                               "achieved": achieved, "peak": peak, "unit": "GB/s",
                               "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
                               "traffic": traffic,
                               "alg_bytes_per_launch": alg_bytes / max(npush, 1),
                               "avg_launch_us": 1e6 * tpush / max(npush, 1),
-                              "seconds": {"level": tpush, "recompute_and_empty_launches": trec},
+                              "seconds": {"level": tpush, "of_which_selection": tsel,
+                                          "recompute_and_empty_launches": trec},
                               "measured_by": "CUDA events around every level kernel of host-driven solves"}
         # end to end through the host-buffer entry point: H2D of B, D2H of H
         Bh = torch.from_numpy(b).pin_memory()

@@ -122,6 +122,8 @@ typedef struct {
     int32_t recompute_launches;/* exact residual recomputations */
     int32_t body_iterations;   /* iterations of the device-side level loop */
     int32_t reserved;
+    double select_seconds;     /* timing mode, propagation 3/4: the frontier-selection part of
+                                  level_seconds */
 } di_stats;
 
 /* Library version string. */

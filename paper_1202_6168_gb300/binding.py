@@ -49,7 +49,7 @@ class di_stats(ctypes.Structure):
                 ("b_l1", c_dbl), ("f0_l1", c_dbl), ("seconds", c_dbl), ("warm_used", c_i32),
                 ("status", c_i32), ("gpu_launches", c_i64), ("level_seconds", c_dbl),
                 ("recompute_seconds", c_dbl), ("level_launches", c_i32), ("recompute_launches", c_i32),
-                ("body_iterations", c_i32), ("reserved", c_i32)]
+                ("body_iterations", c_i32), ("reserved", c_i32), ("select_seconds", c_dbl)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

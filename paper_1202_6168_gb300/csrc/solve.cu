@@ -1098,11 +1098,12 @@ void launch_ex(Kern kernel, int grid, int block, size_t smem, cudaStream_t s, co
 
 template <typename FT>
 void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
-                  int l2, int prop) {
+                  int l2, int prop, cudaEvent_t mid = nullptr) {
     Workspace &ws = g->ws;
     const cudaAccessPolicyWindow *win = l2_window(g, 0, sizeof(FT) == 8, l2);
     launch_ex(k_scan_level<FT>, g->grid_scan, kScanThreads, 0, s, nullptr, (const SolveDesc *)ws.desc, ws.st,
               ws.front, (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
+    if (mid) cudaEventRecord(mid, s);   // timing mode: end of the selection
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
     if (prop == 4)
         launch_ex(k_push_warp<FT>, push_grid(g), kPushThreads, g->n_hot * sizeof(FT), s, win,
@@ -1417,7 +1418,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     }
     DI_CUDA_TRY(cudaGetLastError());
 
-    double t_level = 0.0, t_rec = 0.0;
+    double t_level = 0.0, t_rec = 0.0, t_sel = 0.0;
     int live_iters = 0;
     long long host_launches = 0;   // timing mode: kernels launched by the host loop
     if (!o.timing) {
@@ -1434,12 +1435,13 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             for (int l = 0; l < kBatch; ++l) {
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
+                DI_CUDA_TRY(cudaEventRecord(e[3], s));
                 if (o.propagation == 5) {
                     if (fp64) launch_fused<double>(g, s, 0, 0, 2, win);
                     else launch_fused<float>(g, s, 0, 0, 2, win);
                 } else if (o.propagation >= 3) {
-                    if (fp64) launch_async<double>(g, s, 0, 0, 2, win, o.propagation);
-                    else launch_async<float>(g, s, 0, 0, 2, win, o.propagation);
+                    if (fp64) launch_async<double>(g, s, 0, 0, 2, win, o.propagation, e[3]);
+                    else launch_async<float>(g, s, 0, 0, 2, win, o.propagation, e[3]);
                 } else if (fp64) {
                     launch_select<double>(g, s, 0, 0, 0, 2, win);
                     launch_pull<double>(g, s, win, o.propagation);
@@ -1459,12 +1461,14 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             DI_CUDA_TRY(cudaStreamSynchronize(s));
             const int live = std::min(kBatch, ws.st_h->body_iters - live_iters);
             for (int l = 0; l < live; ++l) {
-                float a = 0.f, c = 0.f;
+                float a = 0.f, c = 0.f, sel = 0.f;
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventElapsedTime(&a, e[0], e[1]));
                 DI_CUDA_TRY(cudaEventElapsedTime(&c, e[1], e[2]));
+                DI_CUDA_TRY(cudaEventElapsedTime(&sel, e[0], e[3]));
                 t_level += a * 1e-3;
                 t_rec += c * 1e-3;
+                t_sel += sel * 1e-3;
             }
             live_iters = ws.st_h->body_iters;
             if (ws.st_h->done) break;
@@ -1522,6 +1526,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         stats->level_launches = o.timing ? live_iters : 0;
         stats->recompute_launches = st.recomputes;
         stats->body_iterations = st.body_iters;
+        stats->select_seconds = t_sel;
     }
     return rc;
 }
