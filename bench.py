@@ -447,6 +447,10 @@ def run_native(args, world, rank, local):
             extras["check"] = {"resid_l1_oracle_fp64": r_cpu, "tol": tol,
                                "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
                                "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
+            if n <= 4_000_000:
+                # error against the oracle's FP64 solution (solved to 1e-14 |B|_1)
+                x = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum()).H
+                extras["check"]["rel_l1_err_vs_oracle_x"] = float(np.abs(h - x).sum() / np.abs(x).sum())
             extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol)
 
     if rank == 0:
