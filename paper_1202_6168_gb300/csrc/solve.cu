@@ -36,6 +36,41 @@ struct Acc<double> { using T = double; };
 __device__ __forceinline__ float thr_cast(double T, float) { return __double2float_ru(T); }
 __device__ __forceinline__ double thr_cast(double T, double) { return T; }
 
+template <typename FT>
+struct Vec4;   // 4 consecutive fluid values per load
+template <>
+struct Vec4<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float *p) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ void store(float *p) const {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ __forceinline__ void load_cs(const float *p) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double *p) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ void store(double *p) const {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+    __device__ __forceinline__ void load_cs(const double *p) {
+        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p)),
+                      b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
 // ------------------------------------------------------------------ init (cold start)
 
 template <typename FT>
@@ -160,15 +195,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const SolveDesc *__restri
 // ------------------------------------------------------------------ asynchronous push level
 
 // Scan of one level of the asynchronous design: frontier compaction in node
-// order (warp ballots and one prefix per 2048-node chunk) with the L1 norm and
-// max of the fluid fused into the first read.  Two passes over each CTA's
+// order (4 nodes per thread with vector loads, a warp prefix and one block
+// prefix per 2048-node chunk) with the L1 norm and max of the fluid fused into
+// the first read.  Two passes over each CTA's
 // chunks - count, reserve the CTA's slice with one atomic, then write - so
 // the frontier counter sees one atomic per CTA instead of one per chunk.
 // Its last CTA decides the level: push the frontier (T <- T / alpha), lower T
 // to the largest fluid after an empty scan, or request an exact residual to
 // confirm a stop (no push).  ctl: 1 in a CUDA graph, 2 host-driven.
 template <typename FT>
-__global__ void __launch_bounds__(kScanThreads) k_scan_level(
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front, int64_t n,
     double *__restrict__ part_sum, double *__restrict__ part_max, cudaGraphConditionalHandle h_while,
     cudaGraphConditionalHandle h_rec, int ctl) {
@@ -191,23 +227,45 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_level(
     const FT *__restrict__ F = static_cast<const FT *>(desc->F);
     const FT Tc = thr_cast(st->T, FT(0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    __shared__ int s_cnt[kScanItems * (kScanThreads / 32)];
-    __shared__ int s_base, s_wcount[kScanThreads / 32];
+    // vector layout of a 2048-node chunk: item k (0, 1), thread t, nodes
+    // c0 + 1024 k + 4 t + j (j = 0..3), which is node order; the fluid vector
+    // is padded with zeros to a multiple of 4 nodes
+    constexpr int kVItems = kScanChunk / (4 * kScanThreads);
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_off[kVItems * kWarps];
+    __shared__ int s_base, s_wcount[kWarps];
+    auto sel_mask = [&](const Vec4<FT> &f, int64_t i0) {
+        unsigned msk = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const FT a = fabs(f.v[j]);
+            if (i0 + j < n && a >= Tc && a > FT(0)) msk |= 1u << j;
+        }
+        return msk;
+    };
     // pass 1: L1 norm, max and the number of selected nodes of all this
     // CTA's chunks; one atomic reserves the CTA's slice of the frontier
     AT acc = 0;
     FT mx = 0;
     int my_sel = 0;
     for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
+        Vec4<FT> f[kVItems];
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int64_t idx = c0 + k * kScanThreads + threadIdx.x;
-            FT v = 0;
-            if (idx < n) v = fabs(F[idx]);
-            acc += static_cast<AT>(v);
-            mx = max(mx, v);
-            my_sel += (idx < n && v >= Tc && v > FT(0)) ? 1 : 0;
+        for (int k = 0; k < kVItems; ++k) {
+            const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+            if (i0 < n) f[k].load(F + i0);
+            else f[k].v[0] = f[k].v[1] = f[k].v[2] = f[k].v[3] = FT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kVItems; ++k) {
+            const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const FT a = fabs(f[k].v[j]);
+                acc += static_cast<AT>(a);
+                mx = max(mx, a);
+            }
+            my_sel += __popc(sel_mask(f[k], i0));
         }
     }
     my_sel = warp_sum(my_sel);
@@ -215,7 +273,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_level(
     __syncthreads();
     if (threadIdx.x == 0) {
         int total = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) total += s_wcount[w];
+        for (int w = 0; w < kWarps; ++w) total += s_wcount[w];
         s_base = total ? atomicAdd(&st->nfront, total) : -1;
     }
     __syncthreads();
@@ -224,37 +282,43 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_level(
     int base = s_base;
     if (base >= 0) {
         for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
-            unsigned masks[kScanItems];
+            unsigned msk[kVItems];
+            int excl[kVItems];
 #pragma unroll
-            for (int k = 0; k < kScanItems; ++k) {
-                const int64_t idx = c0 + k * kScanThreads + threadIdx.x;
-                FT v = 0;
-                if (idx < n) v = fabs(F[idx]);
-                const bool sel = idx < n && v >= Tc && v > FT(0);
-                masks[k] = __ballot_sync(0xffffffffu, sel);
-                if (lane == 0) s_cnt[k * (kScanThreads / 32) + warp] = __popc(masks[k]);
-            }
-            __syncthreads();
-            if (warp == 0) {   // exclusive scan of the 64 counts in node order
-                const int a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
-                int incl = a + b;
+            for (int k = 0; k < kVItems; ++k) {
+                const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+                Vec4<FT> f;
+                if (i0 < n) f.load(F + i0);
+                else f.v[0] = f.v[1] = f.v[2] = f.v[3] = FT(0);
+                msk[k] = sel_mask(f, i0);
+                const int c = __popc(msk[k]);
+                int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int t = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += t;
                 }
-                const int excl = incl - a - b;
-                s_cnt[2 * lane] = excl;
-                s_cnt[2 * lane + 1] = excl + a;
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (lane == 0) s_wcount[0] = total;
+                excl[k] = incl - c;
+                if (lane == 31) s_off[k * kWarps + warp] = incl;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {   // exclusive scan of the (item, warp) totals in node order
+                int run = 0;
+                for (int q = 0; q < kVItems * kWarps; ++q) {
+                    const int v = s_off[q];
+                    s_off[q] = run;
+                    run += v;
+                }
+                s_wcount[0] = run;
             }
             __syncthreads();
 #pragma unroll
-            for (int k = 0; k < kScanItems; ++k) {
-                if ((masks[k] >> lane) & 1u)
-                    front[base + s_cnt[k * (kScanThreads / 32) + warp] + __popc(masks[k] & lt_mask)] =
-                        static_cast<int32_t>(c0 + k * kScanThreads + threadIdx.x);
+            for (int k = 0; k < kVItems; ++k) {
+                int pos = base + s_off[k * kWarps + warp] + excl[k];
+                const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((msk[k] >> j) & 1u) front[pos++] = static_cast<int32_t>(i0 + j);
             }
             base += s_wcount[0];
             __syncthreads();
@@ -350,13 +414,20 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
     };
 
     unsigned long long my_edges = 0, my_nodes = 0;
+    // tiles are claimed two at a time (one atomic on the shared counter per
+    // 512 frontier entries) and pushed one after the other
+    unsigned pair = 0;
+    int sub = 2;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = atomicAdd(&st->tile_ctr, 1u);
-            s_qn = 0;
+        if (sub == 2) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(&st->tile_ctr, 2u);
+            sub = 0;
         }
+        if (threadIdx.x == 0) s_qn = 0;
         __syncthreads();
-        const int64_t first = (int64_t)s_tile * kPushThreads;
+        pair = s_tile;
+        const int64_t first = (int64_t)(pair + sub) * kPushThreads;
+        ++sub;
         if (first >= count) break;
         const int64_t idx = first + threadIdx.x;
         int32_t b = 0, e = 0;
@@ -667,40 +738,6 @@ enum : int { P2_NONE = 0, P2_PULL = 1, P2_PUSH = 2 };
 // active edges are a large share of all edges, scatter from the active nodes
 // otherwise), the next threshold, and whether an exact FP64 residual must
 // follow (FP32 fluid refresh, or confirmation of a stop).
-template <typename FT>
-struct Vec4;   // 4 consecutive fluid values per load
-template <>
-struct Vec4<float> {
-    float v[4];
-    __device__ __forceinline__ void load(const float *p) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-    __device__ __forceinline__ void store(float *p) const {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-    __device__ __forceinline__ void load_cs(const float *p) {
-        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-};
-template <>
-struct Vec4<double> {
-    double v[4];
-    __device__ __forceinline__ void load(const double *p) {
-        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    __device__ __forceinline__ void store(double *p) const {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-    }
-    __device__ __forceinline__ void load_cs(const double *p) {
-        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p)),
-                      b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-};
 
 // Selection and drain (Sec. 2.4 selection, Eqs. defF/defH drain): for every
 // node with |F_i| >= T: H_i += F_i, F_i = 0, w_i = (d / outdeg_i) F_i; every
@@ -1298,7 +1335,8 @@ di_status ensure_workspace(di_graph *g) {
     Workspace &ws = g->ws;
     if (ws.ready) return DI_OK;
     const int64_t n = g->n;
-    g->grid_scan = std::max(1, std::min<int>(occupancy_grid((const void *)k_scan<float>, kScanThreads, 0, g->num_sms),
+    g->grid_scan = std::max(1, std::min<int>(occupancy_grid((const void *)k_scan_level<float>, kScanThreads, 0,
+                                                            g->num_sms),
                                              (int)((n + kScanChunk - 1) / kScanChunk)));
     {
         const int sel = occupancy_grid((const void *)k_select<double>, kLevelThreads, 0, g->num_sms);
@@ -1357,9 +1395,17 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     DI_TRY(ensure_workspace(g));
     Workspace &ws = g->ws;
     const int fp64 = o.fluid_fp64 ? 1 : 0;
-    if (fp64 && !ws.F64) DI_CUDA_TRY(dmalloc(&ws.F64, g->n));
+    // fluid vectors padded with zeros to a multiple of 4 nodes (vector loads of the selection)
+    const int64_t npad = (g->n + 3) / 4 * 4;
+    if (fp64 && !ws.F64) {
+        DI_CUDA_TRY(dmalloc(&ws.F64, npad));
+        DI_CUDA_TRY(cudaMemset(ws.F64, 0, npad * sizeof(double)));
+    }
     if (fp64 && !ws.w64) DI_CUDA_TRY(dmalloc(&ws.w64, g->n));
-    if (!fp64 && !ws.F32) DI_CUDA_TRY(dmalloc(&ws.F32, g->n));
+    if (!fp64 && !ws.F32) {
+        DI_CUDA_TRY(dmalloc(&ws.F32, npad));
+        DI_CUDA_TRY(cudaMemset(ws.F32, 0, npad * sizeof(float)));
+    }
     if (!fp64 && !ws.w32) DI_CUDA_TRY(dmalloc(&ws.w32, g->n));
     DI_TRY(ensure_scale(g, d, s));
     g->res_form = o.exact_residual;
