@@ -29,6 +29,11 @@
  *     same test with tol = (1-d) Target_Error);
  *   - warm start: H_0 given, F_0 = B + P H_0 - H_0 (signed fluid is selected
  *     on |F_i| and r is the L1 norm).
+ *
+ * Optional weighted selection (Sec. 2.4 names the ideal order as the argmax of
+ * F_i / ((#in_i + 1)(#out_i + 1)) and approximates it by a threshold sweep):
+ * with weights w_i the sweep selects |F_i| w_i >= T instead, T_0 and the
+ * empty-level rule use max_i |F_i| w_i, and r stays sum_i |F_i|.
  */
 #include <stdint.h>
 #include <math.h>
@@ -66,7 +71,8 @@ double oracle_residual(int64_t n, const int64_t *row_ptr, const int32_t *col,
  */
 int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *B,
                  double d, double tol, double alpha, int64_t max_levels, int warm,
-                 double *H, double *F, oracle_stats *st, double *trace, int64_t trace_cap) {
+                 double *H, double *F, oracle_stats *st, double *trace, int64_t trace_cap,
+                 const double *w) {
     if (n < 0 || !(alpha > 1.0) || !(tol >= 0.0) || max_levels < 0) return 1;
     if (warm) {
         oracle_residual(n, row_ptr, col, B, d, H, F);
@@ -74,7 +80,10 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
         for (int64_t i = 0; i < n; ++i) { F[i] = B[i]; H[i] = 0.0; }
     }
     double T = 0.0;
-    for (int64_t i = 0; i < n; ++i) if (fabs(F[i]) > T) T = fabs(F[i]);
+    for (int64_t i = 0; i < n; ++i) {
+        double score = w ? fabs(F[i]) * w[i] : fabs(F[i]);
+        if (score > T) T = score;
+    }
 
     oracle_stats s = {0, 0, 0, 0.0, 0.0};
     int status = 4;
@@ -83,7 +92,8 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
         for (int64_t i = 0; i < n; ++i) {
             double a = fabs(F[i]);
             r += a;
-            if (a > mx) mx = a;
+            double score = w ? a * w[i] : a;
+            if (score > mx) mx = score;
         }
         s.resid_l1 = r;
         if (r <= tol) { status = 0; break; }
@@ -92,7 +102,8 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
 
         for (int64_t i = 0; i < n; ++i) {  /* one cyclic sweep at threshold T */
             double sent = F[i];
-            if (fabs(sent) < T) continue;
+            double score = w ? fabs(sent) * w[i] : fabs(sent);
+            if (score < T || sent == 0.0) continue;
             H[i] += sent;
             F[i] = 0.0;
             int64_t deg = row_ptr[i + 1] - row_ptr[i];

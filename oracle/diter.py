@@ -38,7 +38,7 @@ def _lib():
             vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
             lib.oracle_diter.restype = ci
             lib.oracle_diter.argtypes = [i64, vp, vp, vp, dbl, dbl, dbl, i64, ci, vp, vp,
-                                         ctypes.POINTER(_Stats), vp, i64]
+                                         ctypes.POINTER(_Stats), vp, i64, vp]
             lib.oracle_residual.restype = dbl
             lib.oracle_residual.argtypes = [i64, vp, vp, vp, dbl, vp, vp]
             _LIB = lib
@@ -66,11 +66,24 @@ def _csr(row_ptr, col):
     return rp, cl
 
 
+def selection_weights(row_ptr, col) -> np.ndarray:
+    """w_i = 1 / ((#in_i + 1)(#out_i + 1)): the weight of the selection score
+    F_i / ((#in_i + 1)(#out_i + 1)) of Sec. 2.4 (edges counted with multiplicity)."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    n = len(rp) - 1
+    indeg = np.bincount(np.asarray(col, dtype=np.int64), minlength=n)
+    outdeg = np.diff(rp)
+    return 1.0 / ((indeg + 1.0) * (outdeg + 1.0))
+
+
 def d_iteration(row_ptr, col, B, d: float = 0.85, tol: float = 1e-14, alpha: float = 1.5,
-                max_levels: int = 100_000, H0=None, trace: bool = False) -> OracleResult:
-    """Sequential cyclic-threshold D-iteration in FP64 until sum|F| <= tol."""
+                max_levels: int = 100_000, H0=None, trace: bool = False,
+                weighted: bool = False) -> OracleResult:
+    """Sequential cyclic-threshold D-iteration in FP64 until sum|F| <= tol.
+    weighted: select on |F_i| / ((#in_i + 1)(#out_i + 1)) (Sec. 2.4)."""
     rp, cl = _csr(row_ptr, col)
     n = len(rp) - 1
+    w = np.ascontiguousarray(selection_weights(row_ptr, col)) if weighted else None
     B = np.ascontiguousarray(B, dtype=np.float64)
     assert B.shape == (n,)
     H = np.zeros(n, dtype=np.float64) if H0 is None else np.array(H0, dtype=np.float64, copy=True)
@@ -80,7 +93,7 @@ def d_iteration(row_ptr, col, B, d: float = 0.85, tol: float = 1e-14, alpha: flo
     status = _lib().oracle_diter(n, rp.ctypes.data, cl.ctypes.data, B.ctypes.data, d, tol, alpha,
                                  max_levels, 0 if H0 is None else 1, H.ctypes.data, F.ctypes.data,
                                  ctypes.byref(st), tr.ctypes.data if trace else None,
-                                 len(tr) if trace else 0)
+                                 len(tr) if trace else 0, w.ctypes.data if weighted else None)
     if status == 1:
         raise ValueError("oracle rejected its arguments")
     return OracleResult(H=H, F=F, status=status, levels=st.levels,

@@ -289,3 +289,77 @@ def test_pin_detects_a_wrong_damping():
     x = np.linalg.solve(np.eye(30) - od.dense_p(rp, col, D), b)
     wrong = od.d_iteration(rp, col, b, 0.8, tol=1e-15)
     assert np.abs(wrong.H - x).sum() > 1e-6 * np.abs(x).sum()
+
+
+# ---------------------------------------------------------------- weighted selection (Sec. 2.4 score)
+
+def weighted_sweep_by_loops(rp, col, b, tol, alpha=1.5, max_levels=10_000):
+    """The weighted cyclic threshold sweep with plain Python loops:
+    select |F_i| / ((#in_i + 1)(#out_i + 1)) >= T, T0 = the largest score."""
+    n = len(rp) - 1
+    indeg = [0] * n
+    for e in range(len(col)):
+        indeg[int(col[e])] += 1
+    w = [1.0 / ((indeg[i] + 1.0) * (rp[i + 1] - rp[i] + 1.0)) for i in range(n)]
+    F = [float(x) for x in b]
+    H = [0.0] * n
+    T = max(abs(F[i]) * w[i] for i in range(n))
+    nodes = edges = levels = 0
+    while True:
+        r = sum(abs(x) for x in F)
+        if r <= tol or levels >= max_levels:
+            break
+        mx = max(abs(F[i]) * w[i] for i in range(n))
+        while T > mx:
+            T /= alpha
+        for i in range(n):
+            sent = F[i]
+            if abs(sent) * w[i] < T or sent == 0.0:
+                continue
+            H[i] += sent
+            F[i] = 0.0
+            nodes += 1
+            deg = int(rp[i + 1] - rp[i])
+            if deg == 0:
+                continue
+            p = D / deg
+            for e in range(rp[i], rp[i + 1]):
+                F[int(col[e])] += sent * p
+            edges += deg
+        levels += 1
+        T /= alpha
+    return np.array(H), nodes, edges, levels
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_weighted_selection_matches_a_loop_restatement(seed):
+    rng = np.random.default_rng(300 + seed)
+    rp, col = random_graph(40, rng, p_dangling=0.2, max_deg=8)
+    b = rng.random(40) * 0.02
+    tol = 1e-10
+    h_ref, nodes, edges, levels = weighted_sweep_by_loops(rp, col, b, tol)
+    r = od.d_iteration(rp, col, b, D, tol=tol, weighted=True)
+    assert (r.node_diffusions, r.edge_diffusions, r.levels) == (nodes, edges, levels)
+    np.testing.assert_allclose(r.H, h_ref, rtol=1e-14, atol=1e-18)
+
+
+def test_weighted_selection_reaches_x():
+    rng = np.random.default_rng(310)
+    rp, col = random_graph(150, rng, max_deg=10)
+    b = rng.random(150) * 0.01
+    x = np.linalg.solve(np.eye(150) - od.dense_p(rp, col, D), b)
+    r = od.d_iteration(rp, col, b, D, tol=1e-16 * b.sum(), weighted=True)
+    assert r.status == 0
+    assert np.abs(r.H - x).sum() <= 1e-13 * np.abs(x).sum()
+
+
+def test_weighted_equals_raw_when_every_node_has_the_same_degrees():
+    # a directed cycle: every score is |F_i| / 4, so both rules select the same sets
+    n = 64
+    rp, col = csr_from_edges(n, [(k, (k + 1) % n) for k in range(n)])
+    rng = np.random.default_rng(311)
+    b = rng.random(n)
+    a = od.d_iteration(rp, col, b, D, tol=1e-12)
+    w = od.d_iteration(rp, col, b, D, tol=1e-12, weighted=True)
+    assert (a.levels, a.node_diffusions, a.edge_diffusions) == (w.levels, w.node_diffusions, w.edge_diffusions)
+    np.testing.assert_array_equal(a.H, w.H)
