@@ -75,9 +75,12 @@ def parse():
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
     p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
+    p.add_argument("--weighted", action="store_true",
+                   help="select on |F_i| / ((in_i + 1)(out_i + 1)) (the score of the paper's ideal order)")
     p.add_argument("--ws-train", type=int, default=200, help="warm start: training graphs")
     p.add_argument("--ws-eval", type=int, default=32, help="warm start: held-out evaluation graphs")
     p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
+    p.add_argument("--ws-lr", type=float, default=1e-3, help="warm start: Adam learning rate")
     p.add_argument("--host-loop", action="store_true",
                    help="host-driven levels with per-kernel events (profilers cannot see kernels in "
                         "graphs with conditional nodes)")
@@ -343,6 +346,8 @@ def run_native(args, world, rank, local):
         opts.push_ratio = args.push_ratio
     if args.exact_residual is not None:
         opts.exact_residual = args.exact_residual
+    if args.weighted:
+        opts.selection = 1
 
     g = di.Graph.create(rp, col, stream=stream)
     B = torch.from_numpy(b).cuda()
@@ -392,7 +397,8 @@ def run_native(args, world, rank, local):
         topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
                                alpha=opts.alpha, recompute_every=opts.recompute_every,
                                l2_window=opts.l2_window, propagation=opts.propagation,
-                               push_ratio=opts.push_ratio, exact_residual=opts.exact_residual)
+                               push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
+                               selection=opts.selection)
         te = tn = 0
         tpush = trec = tsel = 0.0
         npush = 0
@@ -471,6 +477,7 @@ def run_native(args, world, rank, local):
                            "push_ratio": opts.push_ratio,
                            "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
+                           "selection": ["|F_i| >= T", "|F_i| / ((in_i+1)(out_i+1)) >= T"][opts.selection],
                            "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "time_to_tol_ms": 1e3 * secs_max / args.steps,
@@ -529,19 +536,34 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    edges = launches = 0
+    edges = launches = nodes = levels_sum = 0
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
         _, st, tot = di.di_solve_batched(batch, B, D, tols, H, opts)
         ev1[k].record(stream)
         edges += tot.edge_diffusions
+        nodes += tot.node_diffusions
+        levels_sum += tot.body_iterations
         launches += tot.gpu_launches
     torch.cuda.synchronize()
     clocks = sampler.stop()
     secs = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) * 1e-3
+    secs_rank = secs
     secs, edges_all = aggregate_over_ranks(secs, edges, world, "cuda")
     extras = {}
+    if rank == 0:
+        # whole-solve roofline: every launch of the batched solve, algorithmic bytes
+        # of the level kernels (per edge, per node, and a scan of the union per level)
+        n_union = batch.info()["n_union"]
+        alg = EDGE_BYTES[prec] * edges + NODE_BYTES[prec] * nodes + SCAN_BYTES[prec] * n_union * levels_sum
+        peak, peak_src = measured_hbm_peak()
+        extras["roofline"] = {"bound": "hbm", "kernel": "whole batched solve (k_bscan_level + k_bpush + "
+                                                        "exact residuals, all launches)",
+                              "achieved": alg / secs_rank / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / secs_rank / 1e9 / peak, "peak_source": f"{peak_src} (hbm_gbs)",
+                              "traffic": None, "alg_bytes_per_step": alg / args.steps,
+                              "measured_by": "CUDA events around every timed di_solve_batched"}
     if rank == 0 and not args.no_extras:
         # the same 256 solves one di_solve call at a time
         torch.cuda.synchronize()
@@ -628,7 +650,7 @@ def run_warmstart(args, world, rank, local):
     t_gen = time.perf_counter() - t_gen
     model = di.Model.create(7)
     t0 = time.perf_counter()
-    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=args.ws_epochs, batch=65536, lr=1e-3,
+    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=args.ws_epochs, batch=65536, lr=args.ws_lr,
                                                              stream=stream.cuda_stream))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -666,6 +688,33 @@ def run_warmstart(args, world, rank, local):
                     times.append(ev[0].elapsed_time(ev[1]))
             res[label] = {"ms": statistics.median(times), "edges": st.edge_diffusions, "levels": st.levels,
                           "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1, "resid": st.resid_l1}
+        if not rows:
+            # the inference parts alone on the first held-out graph: features and the network
+            feat = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+            yv = torch.empty(n, dtype=torch.float32, device="cuda")
+            t_feat, t_fwd = [], []
+            for rep in range(5):
+                flush.zero_()
+                ev[0].record(stream)
+                model.features(g, b, feat, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_feat.append(ev[0].elapsed_time(ev[1]))
+                flush.zero_()
+                ev[0].record(stream)
+                model.forward(feat, n, yv, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_fwd.append(ev[0].elapsed_time(ev[1]))
+            fwd_s = statistics.median(t_fwd[1:]) * 1e-3
+            peak, peak_src = measured_hbm_peak()
+            infer_parts = {"features_ms": statistics.median(t_feat[1:]), "network_ms": fwd_s * 1e3,
+                           "network_roofline": {"bound": "hbm", "kernel": "k_mlp_fwd (BF16 mma.sync)",
+                                                "achieved": (36 + 4) * n / fwd_s / 1e9, "peak": peak,
+                                                "unit": "GB/s", "frac": (36 + 4) * n / fwd_s / 1e9 / peak,
+                                                "peak_source": f"{peak_src} (hbm_gbs)",
+                                                "tflops": 2 * (16 * 64 + 64 * 64 + 64) * n / fwd_s / 1e12,
+                                                "bytes_per_node": "36 B features in, 4 B prediction out"}}
         rows.append(res)
         g.close()
     cold = [r["cold"]["ms"] for r in rows]
@@ -675,10 +724,12 @@ def run_warmstart(args, world, rank, local):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS["warmstart"][1], "train_graphs": args.ws_train,
                        "train_nodes": train_nodes, "eval_graphs": args.ws_eval, "epochs": args.ws_epochs,
+                       "lr": args.ws_lr,
                        "tol": "1e-8 |B|_1", "timed": "warm: features + network + F0 + solve; cold: solve",
                        "l2": "flushed (256 MiB write) before each timed solve"},
             "cold_ms": statistics.mean(cold), "warm_ms": statistics.mean(warm),
             "speedup": statistics.mean(cold) / statistics.mean(warm),
+            "inference": infer_parts,
             "warm_used": sum(r["warm"]["warm_used"] for r in rows),
             "f0_over_b_mean": statistics.mean(r["warm"]["f0_over_b"] for r in rows),
             "edges_cold": statistics.mean(r["cold"]["edges"] for r in rows),

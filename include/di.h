@@ -97,6 +97,11 @@ typedef struct {
                               2 in-edges in source-blocked order (blocks of 2^22 sources,
                               so the gathered H stays in L2), runs added with FP64 reds;
                               0 (default) = 2 */
+    int selection;         /* frontier rule: 0 (default) |F_i| >= T; 1 the weighted score
+                              |F_i| / ((#in_i + 1)(#out_i + 1)) >= T that Sec. 2.4 names as
+                              the ideal diffusion order (T_0 and the empty-level rule then
+                              use the largest score; the stop rule keeps |F|_1).
+                              Needs propagation 3 or 4 */
     long long spin_limit;  /* iteration limit of every bounded device wait */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
 } di_opts;
@@ -134,7 +139,7 @@ DI_API const char *di_last_error(void);
 
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 8, max_levels 100000,
  * cold start (fallback on when warm), L2 window on, timing off,
- * propagation 3, push_ratio 8, exact_residual 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+ * propagation 3, push_ratio 8, exact_residual 0, selection 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*

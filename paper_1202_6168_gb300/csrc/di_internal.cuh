@@ -66,6 +66,7 @@ struct SolveDesc {
     int64_t n_nodes;
     int thread_max;       // push shape: rows up to this many edges go to one thread
     int warp_max;         // ... up to this to one warp, longer ones to the CTA
+    const void *iw;       // weighted selection: 1 / ((in + 1)(out + 1)) per node (FT), else NULL
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -187,6 +188,9 @@ struct di_graph {
     double scale_d = -1.0;
     float *s32 = nullptr;
     double *s64 = nullptr;
+    // weighted selection (Sec. 2.4 score): 1 / ((in + 1)(out + 1)), built on first use
+    float *iw32 = nullptr;
+    double *iw64 = nullptr;
     // grid sizes (persistent kernels)
     int grid_scan = 0, grid_push = 0, grid_res = 0, grid_level = 0;
     int grid_select = 0, grid_pull = 0, grid_pushw = 0, grid_flat = 0;
@@ -318,6 +322,8 @@ __device__ __forceinline__ bool last_block(unsigned int *counter) {
 di_status ensure_scale(di_graph *g, double d, cudaStream_t s);
 // graph.cu: the source-blocked in-edge order of the exact residual (lazy)
 di_status ensure_blocked_order(di_graph *g, cudaStream_t s);
+// graph.cu: the selection weights 1 / ((in + 1)(out + 1)) (lazy)
+di_status ensure_selection_weights(di_graph *g, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
 int push_grid(const di_graph *g);

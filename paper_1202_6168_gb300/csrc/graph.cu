@@ -224,6 +224,18 @@ __global__ void k_blk_fill(const int32_t *__restrict__ in_rp, const int32_t *__r
     }
 }
 
+// 1 / ((in + 1)(out + 1)) in FP64 and its FP32 rounding.
+__global__ void k_sel_weights(const int32_t *__restrict__ rp, const int32_t *__restrict__ in_rp, int64_t n,
+                              double *__restrict__ w64, float *__restrict__ w32) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double in = (double)(in_rp[i + 1] - in_rp[i]), out = (double)(rp[i + 1] - rp[i]);
+        const double w = 1.0 / ((in + 1.0) * (out + 1.0));
+        w64[i] = w;
+        w32[i] = (float)w;
+    }
+}
+
 __global__ void k_outdeg(const int32_t *__restrict__ rp, int64_t n, int32_t *__restrict__ deg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) deg[i] = rp[i + 1] - rp[i];
@@ -272,7 +284,7 @@ void free_graph(di_graph *g) {
     void *dev[] = {g->rp, g->pcol, g->hot_node, g->in_rp, g->in_col, g->long_rows, g->long_seg0,
                    g->seg_row, g->seg_beg, g->frows, g->fseg0, g->fseg_row, g->fseg_beg,
                    g->pl_rows, g->pl_seg_row, g->pl_seg_beg, g->pl_lrows, g->pl_lseg0, g->pl_b12_off,
-                   g->pl_b12_col, g->outdeg, g->erow, g->s32, g->s64, g->ws.F32, g->ws.F64, g->ws.w32, g->ws.w64, g->ws.front, g->ws.g, g->ws.acc,
+                   g->pl_b12_col, g->outdeg, g->erow, g->s32, g->s64, g->iw32, g->iw64, g->ws.F32, g->ws.F64, g->ws.w32, g->ws.w64, g->ws.front, g->ws.g, g->ws.acc,
                    g->ws.seg_part, g->ws.part_sum, g->ws.part_max, g->ws.desc, g->ws.st,
                    g->ws.hostB, g->ws.hostH, g->ws.hostF};
     for (void *q : dev)
@@ -444,6 +456,19 @@ di_status ensure_blocked_order(di_graph *g, cudaStream_t s) {
     tmp.release(brow);
     g->bcol = bcol;
     g->brow = brow;
+    return DI_OK;
+}
+
+di_status ensure_selection_weights(di_graph *g, cudaStream_t s) {
+    if (g->iw64) return DI_OK;
+    const int64_t npad = (g->n + 3) / 4 * 4;   // padded like the fluid (vector loads)
+    DI_CUDA_TRY(cudaMalloc(&g->iw64, npad * sizeof(double)));
+    DI_CUDA_TRY(cudaMalloc(&g->iw32, npad * sizeof(float)));
+    DI_CUDA_TRY(cudaMemsetAsync(g->iw64, 0, npad * sizeof(double), s));
+    DI_CUDA_TRY(cudaMemsetAsync(g->iw32, 0, npad * sizeof(float), s));
+    k_sel_weights<<<grid_for(g->n, kThreads, g->num_sms * 16), kThreads, 0, s>>>(g->rp, g->in_rp, g->n, g->iw64,
+                                                                                g->iw32);
+    DI_CUDA_TRY(cudaGetLastError());
     return DI_OK;
 }
 

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
     const double *__restrict__ B = desc->B;
     double *__restrict__ H = desc->H;
     FT *__restrict__ F = static_cast<FT *>(desc->F);
+    const FT *__restrict__ iw = static_cast<const FT *>(desc->iw);
     double s = 0.0, m = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -88,7 +89,8 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
         F[i] = f;
         H[i] = 0.0;
         s += fabs(b);
-        m = fmax(m, fabs(static_cast<double>(f)));
+        const FT score = iw ? fabs(f) * iw[i] : fabs(f);
+        m = fmax(m, static_cast<double>(score));
     }
     block_sum_max<kScanThreads>(s, m);
     if (threadIdx.x == 0) { part_sum[blockIdx.x] = s; part_max[blockIdx.x] = m; }
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
         st->b_l1 = ts;
         st->f0_l1 = ts;
         st->r_exact = ts;   // F_0 = B exactly: this is the exact residual of H_0 = 0
-        st->T = tm;         // T_0 = max |F_0|
+        st->T = tm;         // T_0 = max |F_0| (weighted: the largest score)
         if (!isfinite(ts)) st->done = 3;
         else if (ts <= desc->tol) st->done = 1;
     }
@@ -234,14 +236,21 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int s_off[kVItems * kWarps];
     __shared__ int s_base, s_wcount[kWarps];
-    auto sel_mask = [&](const Vec4<FT> &f, int64_t i0) {
+    // weighted selection (Sec. 2.4 score): |F_i| w_i >= T, w_i = 1 / ((in + 1)(out + 1))
+    const FT *__restrict__ iw = static_cast<const FT *>(desc->iw);
+    auto sel_mask = [&](const Vec4<FT> &f, const Vec4<FT> &w, int64_t i0) {
         unsigned msk = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const FT a = fabs(f.v[j]);
-            if (i0 + j < n && a >= Tc && a > FT(0)) msk |= 1u << j;
+            const FT score = iw ? a * w.v[j] : a;
+            if (i0 + j < n && score >= Tc && a > FT(0)) msk |= 1u << j;
         }
         return msk;
+    };
+    auto load_w = [&](Vec4<FT> &w, int64_t i0) {
+        if (iw && i0 < n) w.load(iw + i0);
+        else w.v[0] = w.v[1] = w.v[2] = w.v[3] = FT(1);
     };
     // pass 1: L1 norm, max and the number of selected nodes of all this
     // CTA's chunks; one atomic reserves the CTA's slice of the frontier
@@ -259,13 +268,15 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 #pragma unroll
         for (int k = 0; k < kVItems; ++k) {
             const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+            Vec4<FT> w;
+            load_w(w, i0);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const FT a = fabs(f[k].v[j]);
                 acc += static_cast<AT>(a);
-                mx = max(mx, a);
+                mx = max(mx, iw ? a * w.v[j] : a);   // the control lowers T against the largest score
             }
-            my_sel += __popc(sel_mask(f[k], i0));
+            my_sel += __popc(sel_mask(f[k], w, i0));
         }
     }
     my_sel = warp_sum(my_sel);
@@ -287,10 +298,11 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 #pragma unroll
             for (int k = 0; k < kVItems; ++k) {
                 const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
-                Vec4<FT> f;
+                Vec4<FT> f, w;
                 if (i0 < n) f.load(F + i0);
                 else f.v[0] = f.v[1] = f.v[2] = f.v[3] = FT(0);
-                msk[k] = sel_mask(f, i0);
+                load_w(w, i0);
+                msk[k] = sel_mask(f, w, i0);
                 const int c = __popc(msk[k]);
                 int incl = c;
 #pragma unroll
@@ -1319,6 +1331,11 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (o->max_levels < 0 || o->recompute_every < 0) { set_error("di_solve: negative max_levels or recompute_every"); return DI_EINVAL; }
     if (o->propagation < 0 || o->propagation > 5) { set_error("di_solve: propagation = %d outside [0, 5]", o->propagation); return DI_EINVAL; }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
+    if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
+    if (o->selection == 1 && o->propagation != 3 && o->propagation != 4) {
+        set_error("di_solve: the weighted selection needs propagation 3 or 4 (got %d)", o->propagation);
+        return DI_EINVAL;
+    }
     return DI_OK;
 }
 
@@ -1357,7 +1374,9 @@ di_status ensure_workspace(di_graph *g) {
             (int)std::max<int64_t>(1, std::min<int64_t>(flat, (fchunks + kLevelThreads - 1) / kLevelThreads));
     }
     g->grid_res = residual_grid(g->num_sms);
-    const int parts = std::max({g->grid_scan, g->grid_select, residual_partials(g)});
+    // one partial per CTA of every kernel that reduces across CTAs (the fused
+    // level kernel runs on the push grid)
+    const int parts = std::max({g->grid_scan, g->grid_select, residual_partials(g), g->grid_push});
     const PullPlan pl = pull_plan_of(g);
     const int64_t nseg5 = pl.task_off[5] - pl.task_off[4];
     DI_CUDA_TRY(dmalloc(&ws.front, n));
@@ -1408,6 +1427,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     }
     if (!fp64 && !ws.w32) DI_CUDA_TRY(dmalloc(&ws.w32, g->n));
     DI_TRY(ensure_scale(g, d, s));
+    if (o.selection == 1) DI_TRY(ensure_selection_weights(g, s));
     g->res_form = o.exact_residual;
     if (g->res_form != 1) DI_TRY(ensure_blocked_order(g, s));
     if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
@@ -1431,6 +1451,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.n_nodes = g->n;
     dh.thread_max = g->tune.thread_max_deg;
     dh.warp_max = g->tune.warp_max_deg;
+    dh.iw = o.selection == 1 ? (fp64 ? (const void *)g->iw64 : (const void *)g->iw32) : nullptr;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));

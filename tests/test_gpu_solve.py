@@ -461,3 +461,45 @@ def test_autotune_keeps_a_shape_and_caches_it(web10k, tmp_path):
         di.set_tune(g, bad)
     g.close()
     g2.close()
+
+
+# ---------------------------------------------------------------- weighted selection (Sec. 2.4 score)
+
+@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_weighted_selection_parity(web10k, prop, fp64):
+    rp, col, b, x = web10k
+    tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, selection=1)
+    assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+    f_cpu = check_stop(rp, col, b, h, st, tol)
+    assert_residual_close(f, f_cpu, rp, col, b, h)
+
+
+def test_weighted_selection_personalised_and_warm():
+    rp, col = gg.generate(gg.GraphSpec(n=30000, mean_deg=9, seed=8))
+    b = gg.personalised_b(30000, 4242)
+    x = oracle_x(rp, col, b)
+    tol = 1e-8 * b.sum()
+    h, st, _, _ = solve(rp, col, b, tol, selection=1)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    rng = np.random.default_rng(16)
+    h0 = x * (1 + 0.1 * rng.standard_normal(len(x)))
+    h, st, _, _ = solve(rp, col, b, tol, h0=h0, selection=1)
+    assert st.warm_used == 1
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+
+
+def test_weighted_selection_needs_a_selection_kernel(web10k):
+    rp, col, b, _ = web10k
+    g = di.Graph.create(rp, col)
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    for prop in (0, 1, 2, 5):
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(propagation=prop, selection=1))
+        assert e.value.status == di.DI_EINVAL
+    with pytest.raises(di.DiError):
+        di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(selection=2))
+    g.close()
