@@ -196,7 +196,9 @@ DI_API di_status di_solve_host(di_graph *g, const double *B, double d, double to
  * Exact residual (the invariant F_n = B + P H_n - H_n that Eqs. defF/defH
  * imply): F = B + P H - H in FP64 for device vectors B, H (n doubles) into
  * the device vector F (n doubles); *r_l1 (host, may be NULL) receives
- * |F|_1.  Gathers over in-edges, no atomics.  Synchronous when r_l1 != NULL.
+ * |F|_1.  Gathers over the in-edges in source-blocked order (form 2 of
+ * di_opts.exact_residual) and adds runs of equal destination with FP64
+ * reds.  Synchronous when r_l1 != NULL.
  */
 DI_API di_status di_residual(di_graph *g, const double *B, double d, const double *H,
                              double *F, double *r_l1, void *stream);

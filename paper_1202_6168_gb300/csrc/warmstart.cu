@@ -7,8 +7,8 @@
 // that H0_i = exp(y_i) / N starts the solve close to X.
 //
 //   k_feat_node / k_feat_hop<1,2> - features from degree aggregates over the
-//       in-edges (warp-cooperative row gathers on the transpose, FP64
-//       arithmetic, FP32 output): log in/out-degree, 1- and 2-hop mean and
+//       in-edges (row gathers on the transpose, FP32 arithmetic with
+//       compensated sums): log in/out-degree, 1- and 2-hop mean and
 //       max of neighbour log-degree, log(1 + N (Q u)_i), log(1 + N (Q^2 u)_i),
 //       N B_i;
 //   k_mlp_fwd  - the network 9 -> 64 -> 64 -> 1 (ReLU) on the tensor cores:
@@ -44,7 +44,6 @@ constexpr int kFwdThreads = 128;          // 4 warps x 16 nodes per tile
 constexpr int kBwdThreads = 256;
 constexpr int kBwdRows = 16;
 constexpr int kFeatThreads = 256;
-constexpr int kTmp = 5;                   // FP32 temporaries per node: ld, s, x2, x3, a1
 
 // ------------------------------------------------------------------ features
 
@@ -79,19 +78,24 @@ __device__ __forceinline__ CSum warp_csum(CSum v) {
     return v;
 }
 //
-// x0 = log(1 + indeg), x1 = log(1 + outdeg), x8 = N B_i; temporaries
-// ld_i = log(1 + indeg) and s_i = 1 / outdeg (0 for a dangling node).
+// Per-node temporaries, laid out so that a gather over an in-edge j -> i
+// reads one 32-byte sector: t1[j] = (ld_j, s_j) with ld_j = log(1 + indeg_j)
+// and s_j = 1 / outdeg_j (0 for a dangling node); t2[j] = (x2_j, x3_j,
+// s_j a1_j, a1_j) from the first hop.
+__host__ __device__ __forceinline__ int64_t tmp_t2_offset(int64_t n) { return (2 * n + 3) & ~int64_t(3); }
+__host__ __device__ __forceinline__ int64_t tmp_floats(int64_t n) { return tmp_t2_offset(n) + 4 * n; }
+
+// x0 = log(1 + indeg), x1 = log(1 + outdeg), x8 = N B_i, and t1.
 __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__restrict__ rp,
                                                             const int32_t *__restrict__ in_rp,
                                                             const double *__restrict__ B, int64_t n,
-                                                            float *__restrict__ feat, float *__restrict__ tmp) {
+                                                            float *__restrict__ feat, float2 *__restrict__ t1) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int indeg = in_rp[i + 1] - in_rp[i];
         const int outdeg = rp[i + 1] - rp[i];
         const float ld = log1pf((float)indeg);
-        tmp[i] = ld;
-        tmp[n + i] = outdeg > 0 ? 1.0f / (float)outdeg : 0.0f;
+        t1[i] = make_float2(ld, outdeg > 0 ? 1.0f / (float)outdeg : 0.0f);
         feat[i * kNF + 0] = ld;
         feat[i * kNF + 1] = log1pf((float)outdeg);
         feat[i * kNF + 8] = (float)((double)n * B[i]);
@@ -102,36 +106,67 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__res
 //   HOP 1: (ld_j, ld_j, s_j) summed, maximised, summed -> x2, x3, a1
 //   HOP 2: (x2_j, x3_j, s_j a1_j)                      -> x4, x5, a2
 template <int HOP>
-__device__ __forceinline__ void feat_visit(const float *__restrict__ tmp, int64_t n, int32_t j, CSum &u, float &m,
-                                           CSum &v) {
-    if (HOP == 1) {
-        const float l = tmp[j];
-        u.add(l);
-        m = fmaxf(m, l);
-        v.add(tmp[n + j]);
-    } else {
-        u.add(tmp[2 * n + j]);
-        m = fmaxf(m, tmp[3 * n + j]);
-        v.add(tmp[n + j] * tmp[4 * n + j]);
+struct FeatVal;
+template <>
+struct FeatVal<1> {
+    float2 v;
+    __device__ __forceinline__ void load(const float2 *__restrict__ t1, const float4 *__restrict__, int32_t j) {
+        v = __ldg(t1 + j);
+    }
+    __device__ __forceinline__ void visit(CSum &u, float &m, CSum &w) const {
+        u.add(v.x);
+        m = fmaxf(m, v.x);
+        w.add(v.y);
+    }
+};
+template <>
+struct FeatVal<2> {
+    float4 v;
+    __device__ __forceinline__ void load(const float2 *__restrict__, const float4 *__restrict__ t2, int32_t j) {
+        v = __ldg(t2 + j);
+    }
+    __device__ __forceinline__ void visit(CSum &u, float &m, CSum &w) const {
+        u.add(v.x);
+        m = fmaxf(m, v.y);
+        w.add(v.z);
+    }
+};
+
+// In-edges [b, e) of one row in order, four gathers issued before they are
+// accumulated (the sums keep the edge order).
+template <int HOP>
+__device__ __forceinline__ void feat_row(const int32_t *__restrict__ in_col, int32_t b, int32_t e,
+                                         const float2 *__restrict__ t1, const float4 *__restrict__ t2, CSum &u,
+                                         float &m, CSum &w) {
+    int32_t q = b;
+    for (; q + 4 <= e; q += 4) {
+        FeatVal<HOP> x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k].load(t1, t2, __ldg(in_col + q + k));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k].visit(u, m, w);
+    }
+    for (; q < e; ++q) {
+        FeatVal<HOP> x;
+        x.load(t1, t2, __ldg(in_col + q));
+        x.visit(u, m, w);
     }
 }
 
-// Outputs of node i from its in-row sums (u, v), max m and length len.
+// Outputs of node i from its in-row sums (u, w), max m and length len.
 template <int HOP>
-__device__ __forceinline__ void feat_emit(float *__restrict__ tmp, float *__restrict__ feat, int64_t n, int64_t i,
-                                          int len, float u, float m, float v) {
+__device__ __forceinline__ void feat_emit(const float2 *__restrict__ t1, float4 *__restrict__ t2,
+                                          float *__restrict__ feat, int64_t i, int len, float u, float m, float w) {
     const float mean = len > 0 ? u / (float)len : 0.0f;
     if (HOP == 1) {
-        tmp[2 * n + i] = mean;
-        tmp[3 * n + i] = m;
-        tmp[4 * n + i] = v;
+        t2[i] = make_float4(mean, m, t1[i].y * w, w);
         feat[i * kNF + 2] = mean;
         feat[i * kNF + 3] = m;
     } else {
         feat[i * kNF + 4] = mean;
         feat[i * kNF + 5] = m;
-        feat[i * kNF + 6] = log1pf(tmp[4 * n + i]);
-        feat[i * kNF + 7] = log1pf(v);
+        feat[i * kNF + 6] = log1pf(t2[i].w);
+        feat[i * kNF + 7] = log1pf(w);
     }
 }
 
@@ -142,7 +177,8 @@ __device__ __forceinline__ void feat_emit(float *__restrict__ tmp, float *__rest
 template <int HOP>
 __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col, int64_t n,
-                                                           float *__restrict__ feat, float *__restrict__ tmp) {
+                                                           float *__restrict__ feat, float2 *__restrict__ t1,
+                                                           float4 *__restrict__ t2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -151,24 +187,27 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__rest
         int32_t b = 0, e = 0;
         if (i < n) { b = in_rp[i]; e = in_rp[i + 1]; }
         const int len = e - b;
-        CSum u, v;
+        CSum u, w;
         float m = 0.f;
-        if (len <= 32)
-            for (int32_t q = b; q < e; ++q) feat_visit<HOP>(tmp, n, in_col[q], u, m, v);
+        if (len <= 32) feat_row<HOP>(in_col, b, e, t1, t2, u, m, w);
         unsigned big = __ballot_sync(0xffffffffu, len > 32 && len <= kBin4Max);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
-            CSum pu, pv;
+            CSum pu, pw;
             float pm = 0.f;
-            for (int32_t q = mb + lane; q < me; q += 32) feat_visit<HOP>(tmp, n, in_col[q], pu, pm, pv);
+            for (int32_t q = mb + lane; q < me; q += 32) {
+                FeatVal<HOP> x;
+                x.load(t1, t2, __ldg(in_col + q));
+                x.visit(pu, pm, pw);
+            }
             pu = warp_csum(pu);
             pm = warp_max(pm);
-            pv = warp_csum(pv);
-            if (lane == src) { u = pu; m = pm; v = pv; }
+            pw = warp_csum(pw);
+            if (lane == src) { u = pu; m = pm; w = pw; }
         }
-        if (i < n && len <= kBin4Max) feat_emit<HOP>(tmp, feat, n, i, len, u.value(), m, v.value());
+        if (i < n && len <= kBin4Max) feat_emit<HOP>(t1, t2, feat, i, len, u.value(), m, w.value());
     }
 }
 
@@ -180,8 +219,9 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
                                                            const int32_t *__restrict__ seg_beg,
                                                            const int32_t *__restrict__ lseg0, int n_long,
                                                            int64_t nseg, const int32_t *__restrict__ in_rp,
-                                                           const int32_t *__restrict__ in_col, int64_t n,
-                                                           const float *__restrict__ tmp, double *__restrict__ lacc) {
+                                                           const int32_t *__restrict__ in_col,
+                                                           const float2 *__restrict__ t1,
+                                                           const float4 *__restrict__ t2, double *__restrict__ lacc) {
     __shared__ CSum su[kFeatThreads / 32], sv[kFeatThreads / 32];
     __shared__ float sm[kFeatThreads / 32];
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
@@ -191,7 +231,11 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
         const int32_t e = b + kPullSeg < end ? b + kPullSeg : end;
         CSum cu, cv;
         float cm = 0.f;
-        for (int32_t q = b + threadIdx.x; q < e; q += kFeatThreads) feat_visit<HOP>(tmp, n, in_col[q], cu, cm, cv);
+        for (int32_t q = b + threadIdx.x; q < e; q += kFeatThreads) {
+            FeatVal<HOP> x;
+            x.load(t1, t2, __ldg(in_col + q));
+            x.visit(cu, cm, cv);
+        }
         cu = warp_csum(cu);
         cm = warp_max(cm);
         cv = warp_csum(cv);
@@ -218,11 +262,11 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
 
 template <int HOP>
 __global__ void k_feat_long(const int32_t *__restrict__ lrows, int n_long, const int32_t *__restrict__ in_rp,
-                            int64_t n, const double *__restrict__ lacc, float *__restrict__ tmp,
-                            float *__restrict__ feat) {
+                            const double *__restrict__ lacc, const float2 *__restrict__ t1,
+                            float4 *__restrict__ t2, float *__restrict__ feat) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_long; r += gridDim.x * blockDim.x) {
         const int32_t i = lrows[r];
-        feat_emit<HOP>(tmp, feat, n, i, in_rp[i + 1] - in_rp[i], (float)lacc[3 * r], (float)lacc[3 * r + 1],
+        feat_emit<HOP>(t1, t2, feat, i, in_rp[i + 1] - in_rp[i], (float)lacc[3 * r], (float)lacc[3 * r + 1],
                        (float)lacc[3 * r + 2]);
     }
 }
@@ -636,7 +680,7 @@ di_status ensure_feat(di_model *m, int64_t n) {
     m->ftmp = nullptr;
     m->feat_cap = 0;
     DI_CUDA_TRY(cudaMalloc(&m->feat, (size_t)n * kNF * sizeof(float)));
-    DI_CUDA_TRY(cudaMalloc(&m->ftmp, (size_t)n * kTmp * sizeof(float)));
+    DI_CUDA_TRY(cudaMalloc(&m->ftmp, (size_t)tmp_floats(n) * sizeof(float)));
     m->feat_cap = n;
     return DI_OK;
 }
@@ -681,23 +725,25 @@ di_status features_into(di_model *m, di_graph *g, const double *B, float *feat, 
         m->lacc_cap = n_long;
     }
     const int cap = g->num_sms * 8;
-    k_feat_node<<<grid_of(g->n, kFeatThreads, cap), kFeatThreads, 0, s>>>(g->rp, g->in_rp, B, g->n, feat, m->ftmp);
+    float2 *t1 = reinterpret_cast<float2 *>(m->ftmp);
+    float4 *t2 = reinterpret_cast<float4 *>(m->ftmp + tmp_t2_offset(g->n));
+    k_feat_node<<<grid_of(g->n, kFeatThreads, cap), kFeatThreads, 0, s>>>(g->rp, g->in_rp, B, g->n, feat, t1);
     const int hop_grid = grid_of((g->n + 31) / 32, kFeatThreads / 32, cap);
     const int seg_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, cap));
     const int long_grid = grid_of(n_long, 128, cap);
-    k_feat_hop<1><<<hop_grid, kFeatThreads, 0, s>>>(g->in_rp, g->in_col, g->n, feat, m->ftmp);
+    k_feat_hop<1><<<hop_grid, kFeatThreads, 0, s>>>(g->in_rp, g->in_col, g->n, feat, t1, t2);
     if (n_long > 0) {
         DI_CUDA_TRY(cudaMemsetAsync(m->lacc, 0, (size_t)3 * n_long * sizeof(double), s));
         k_feat_seg<1><<<seg_grid, kFeatThreads, 0, s>>>(g->pl_seg_row, g->pl_seg_beg, g->pl_lseg0, n_long, nseg,
-                                                        g->in_rp, g->in_col, g->n, m->ftmp, m->lacc);
-        k_feat_long<1><<<long_grid, 128, 0, s>>>(g->pl_lrows, n_long, g->in_rp, g->n, m->lacc, m->ftmp, feat);
+                                                        g->in_rp, g->in_col, t1, t2, m->lacc);
+        k_feat_long<1><<<long_grid, 128, 0, s>>>(g->pl_lrows, n_long, g->in_rp, m->lacc, t1, t2, feat);
     }
-    k_feat_hop<2><<<hop_grid, kFeatThreads, 0, s>>>(g->in_rp, g->in_col, g->n, feat, m->ftmp);
+    k_feat_hop<2><<<hop_grid, kFeatThreads, 0, s>>>(g->in_rp, g->in_col, g->n, feat, t1, t2);
     if (n_long > 0) {
         DI_CUDA_TRY(cudaMemsetAsync(m->lacc, 0, (size_t)3 * n_long * sizeof(double), s));
         k_feat_seg<2><<<seg_grid, kFeatThreads, 0, s>>>(g->pl_seg_row, g->pl_seg_beg, g->pl_lseg0, n_long, nseg,
-                                                        g->in_rp, g->in_col, g->n, m->ftmp, m->lacc);
-        k_feat_long<2><<<long_grid, 128, 0, s>>>(g->pl_lrows, n_long, g->in_rp, g->n, m->lacc, m->ftmp, feat);
+                                                        g->in_rp, g->in_col, t1, t2, m->lacc);
+        k_feat_long<2><<<long_grid, 128, 0, s>>>(g->pl_lrows, n_long, g->in_rp, m->lacc, t1, t2, feat);
     }
     DI_CUDA_TRY(cudaGetLastError());
     return DI_OK;

@@ -384,6 +384,48 @@ def test_warm_start_every_residual_form(web10k, form):
     check_stop(rp, col, b, h, st, tol)
 
 
+@pytest.mark.parametrize("nnz", [0, 1, 2047, 2048, 4096, 6143, 2048 * 37 + 5])
+def test_blocked_residual_ragged_edge_counts(nnz):
+    # the flat gather takes 8 in-edges per thread with vector loads and
+    # clips the last group: edge counts around those boundaries, none, one
+    rng = np.random.default_rng(nnz + 1)
+    n = 3000
+    src = rng.integers(0, n, size=nnz)
+    dst = rng.integers(0, n, size=nnz)
+    rp, col = csr_from_edges(n, list(zip(src.tolist(), dst.tolist())))
+    assert len(col) == nnz
+    h, b = rng.random(n), rng.random(n)
+    g = di.Graph.create(rp, col)
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = di.di_residual(g, dev(b), D, dev(h), F)
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    assert_residual_close(F.cpu().numpy(), f_cpu, rp, col, b, h)
+    assert r == pytest.approx(r_cpu, rel=1e-13)
+    g.close()
+
+
+@pytest.mark.parametrize("edges_per_node", [5.6, 11.2])
+def test_blocked_residual_many_grid_strides(edges_per_node):
+    # uniformly random in-edges (no locality) and enough of them that every
+    # thread of the grid loops several times; repeated calls agree with the
+    # oracle each time
+    rng = np.random.default_rng(int(edges_per_node * 10))
+    n = 1_000_000
+    nnz = int(n * edges_per_node) + 777
+    src = np.sort(rng.integers(0, n, size=nnz))
+    col = rng.integers(0, n, size=nnz).astype(np.int32)
+    rp = np.concatenate(([0], np.cumsum(np.bincount(src, minlength=n)))).astype(np.int64)
+    h, b = rng.random(n), rng.random(n)
+    g = di.Graph.create(rp, col)
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    for _ in range(3):
+        r = di.di_residual(g, dev(b), D, dev(h), F)
+        assert_residual_close(F.cpu().numpy(), f_cpu, rp, col, b, h)
+        assert r == pytest.approx(r_cpu, rel=1e-13)
+    g.close()
+
+
 @pytest.fixture(scope="module")
 def web5m():
     """More than 2^22 nodes: the exact residual runs over two source blocks."""
