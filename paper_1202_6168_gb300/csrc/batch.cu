@@ -413,58 +413,67 @@ __global__ void __launch_bounds__(kBThreads) k_bres_prep(const BDesc *__restrict
     }
 }
 
-// tmp_k += sum of g_j over the in-edges j -> k of the rows of items with rec
-// set: 16 consecutive in-edges per thread, runs of equal destination summed
-// and added with one red.global.add.f64.
+// tmp_k += sum of g_j over the in-edges j -> k of the items with rec set:
+// 16 consecutive in-edges per thread, runs of equal destination summed and
+// added with one red.global.add.f64.  The in-edges of item t are the union
+// in-CSR range [e_off[t], e_off[t + 1]) (items own disjoint node ranges, in
+// order), so only the ranges of the items that recompute are read; chunks
+// are aligned to the union's edge index (vector loads) and masked to the
+// range.
 __global__ void __launch_bounds__(kBThreads) k_bres_flat(const BDesc *__restrict__ desc,
-                                                         const BItem *__restrict__ items,
-                                                         const int32_t *__restrict__ item_of_chunk,
+                                                         const BItem *__restrict__ items, int nitems,
+                                                         const int64_t *__restrict__ e_off,
                                                          const int32_t *__restrict__ in_col,
                                                          const int32_t *__restrict__ erow, int64_t nnz) {
     const double *__restrict__ g = desc->g;
     double *__restrict__ tmp = desc->tmp;
-    const int64_t nch = (nnz + kBFlatEdges - 1) / kBFlatEdges;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += stride) {
-        const int64_t e0 = c * kBFlatEdges;
-        int32_t col[kBFlatEdges], row[kBFlatEdges];
-        if (e0 + kBFlatEdges <= nnz) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int t = 0; t < nitems; ++t) {
+        if (!items[t].rec) continue;
+        const int64_t eb = e_off[t], ee = e_off[t + 1];
+        if (eb >= ee) continue;
+        const int64_t cb = eb / kBFlatEdges, ce = (ee + kBFlatEdges - 1) / kBFlatEdges;
+        for (int64_t c = cb + tid; c < ce; c += stride) {
+            const int64_t e0 = c * kBFlatEdges;
+            int32_t col[kBFlatEdges], row[kBFlatEdges];
+            if (e0 + kBFlatEdges <= nnz) {
 #pragma unroll
-            for (int v = 0; v < kBFlatEdges / 4; ++v) {
-                const int4 a = __ldcs(reinterpret_cast<const int4 *>(in_col + e0) + v);
-                const int4 b = __ldcs(reinterpret_cast<const int4 *>(erow + e0) + v);
-                col[4 * v] = a.x; col[4 * v + 1] = a.y; col[4 * v + 2] = a.z; col[4 * v + 3] = a.w;
-                row[4 * v] = b.x; row[4 * v + 1] = b.y; row[4 * v + 2] = b.z; row[4 * v + 3] = b.w;
+                for (int v = 0; v < kBFlatEdges / 4; ++v) {
+                    const int4 a = __ldcs(reinterpret_cast<const int4 *>(in_col + e0) + v);
+                    const int4 b = __ldcs(reinterpret_cast<const int4 *>(erow + e0) + v);
+                    col[4 * v] = a.x; col[4 * v + 1] = a.y; col[4 * v + 2] = a.z; col[4 * v + 3] = a.w;
+                    row[4 * v] = b.x; row[4 * v + 1] = b.y; row[4 * v + 2] = b.z; row[4 * v + 3] = b.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kBFlatEdges; ++k) {
+                    const bool ok = e0 + k < nnz;
+                    col[k] = ok ? in_col[e0 + k] : 0;
+                    row[k] = ok ? erow[e0 + k] : -1;
+                }
             }
-        } else {
+            double val[kBFlatEdges];
 #pragma unroll
             for (int k = 0; k < kBFlatEdges; ++k) {
-                const bool ok = e0 + k < nnz;
-                col[k] = ok ? in_col[e0 + k] : 0;
-                row[k] = ok ? erow[e0 + k] : -1;
+                const bool on = e0 + k >= eb && e0 + k < ee;
+                if (!on) row[k] = -1;
+                val[k] = on ? g[col[k]] : 0.0;
             }
-        }
-        // rows of one 16-edge run span at most a few items: test each row's item
-        double val[kBFlatEdges];
+            int32_t cur = row[0];
+            double acc = val[0];
 #pragma unroll
-        for (int k = 0; k < kBFlatEdges; ++k) {
-            const bool on = row[k] >= 0 && items[item_of_chunk[row[k] >> kBChunkShift]].rec;
-            if (!on) row[k] = -1;
-            val[k] = on ? g[col[k]] : 0.0;
-        }
-        int32_t cur = row[0];
-        double acc = val[0];
-#pragma unroll
-        for (int k = 1; k < kBFlatEdges; ++k) {
-            if (row[k] != cur) {
-                if (cur >= 0) red_add(tmp + cur, acc);
-                cur = row[k];
-                acc = val[k];
-            } else {
-                acc += val[k];
+            for (int k = 1; k < kBFlatEdges; ++k) {
+                if (row[k] != cur) {
+                    if (cur >= 0) red_add(tmp + cur, acc);
+                    cur = row[k];
+                    acc = val[k];
+                } else {
+                    acc += val[k];
+                }
             }
+            if (cur >= 0) red_add(tmp + cur, acc);
         }
-        if (cur >= 0) red_add(tmp + cur, acc);
     }
 }
 
@@ -577,6 +586,7 @@ struct di_batch {
     int32_t *item_of_chunk = nullptr;
     int64_t *d_base = nullptr;
     int32_t *d_nloc = nullptr;
+    int64_t *d_eoff = nullptr;           // per item: first union in-edge (nitems + 1 entries)
     double *B = nullptr, *H = nullptr, *tmp = nullptr, *g = nullptr;
     float *F32 = nullptr;
     double *F64 = nullptr;
@@ -603,7 +613,7 @@ void free_batch(di_batch *b) {
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
         if (sg.graph) cudaGraphDestroy(sg.graph);
     }
-    void *dev[] = {b->item_of_chunk, b->d_base, b->d_nloc, b->B, b->H, b->tmp, b->g, b->F32, b->F64, b->front,
+    void *dev[] = {b->item_of_chunk, b->d_base, b->d_nloc, b->d_eoff, b->B, b->H, b->tmp, b->g, b->F32, b->F64, b->front,
                    b->items, b->st, b->desc, (void *)b->pB, (void *)b->pH};
     for (void *q : dev)
         if (q) cudaFree(q);
@@ -644,7 +654,8 @@ template <typename FT>
 void launch_bres(di_batch *b, cudaStream_t s) {
     di_graph *u = b->u;
     k_bres_prep<<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->item_of_chunk, u->s64, b->nchunks);
-    k_bres_flat<<<b->grid_flat, kBThreads, 0, s>>>(b->desc, b->items, b->item_of_chunk, u->in_col, u->erow, u->nnz);
+    k_bres_flat<<<b->grid_flat, kBThreads, 0, s>>>(b->desc, b->items, b->nitems, b->d_eoff, u->in_col, u->erow,
+                                                   u->nnz);
     k_bres_fin<FT><<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->st, b->item_of_chunk, b->nchunks);
 }
 
@@ -766,6 +777,9 @@ di_status batch_create_impl(const di_graph *const *graphs, int ng, const int *nr
     DI_CUDA_TRY(cudaMemcpy(b->d_base, b->base.data(), b->nitems * sizeof(int64_t), cudaMemcpyHostToDevice));
     DI_CUDA_TRY(cudaMalloc(&b->d_nloc, b->nitems * sizeof(int32_t)));
     DI_CUDA_TRY(cudaMemcpy(b->d_nloc, nl32.data(), b->nitems * sizeof(int32_t), cudaMemcpyHostToDevice));
+    edge0.push_back(nnz_union);
+    DI_CUDA_TRY(cudaMalloc(&b->d_eoff, edge0.size() * sizeof(int64_t)));
+    DI_CUDA_TRY(cudaMemcpy(b->d_eoff, edge0.data(), edge0.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     const size_t nb = (size_t)n_union;
     DI_CUDA_TRY(cudaMalloc(&b->B, nb * sizeof(double)));
     DI_CUDA_TRY(cudaMalloc(&b->H, nb * sizeof(double)));

@@ -78,27 +78,25 @@ __device__ __forceinline__ CSum warp_csum(CSum v) {
     return v;
 }
 //
-// Per-node temporaries, laid out so that a gather over an in-edge j -> i
-// reads one 32-byte sector: t1[j] = (ld_j, s_j) with ld_j = log(1 + indeg_j)
-// and s_j = 1 / outdeg_j (0 for a dangling node); t2[j] = (x2_j, x3_j,
-// s_j a1_j, a1_j) from the first hop.
-__host__ __device__ __forceinline__ int64_t tmp_t2_offset(int64_t n) { return (2 * n + 3) & ~int64_t(3); }
-__host__ __device__ __forceinline__ int64_t tmp_floats(int64_t n) { return tmp_t2_offset(n) + 4 * n; }
+// Per-node temporaries, 16 bytes each, so that a gather over an in-edge
+// j -> i reads one 32-byte sector: t1[j] = (x0_j, s_j, x1_j, x8_j) with
+// x0 = log(1 + indeg), s = 1 / outdeg (0 for a dangling node), x1 =
+// log(1 + outdeg), x8 = N B; t2[j] = (x2_j, x3_j, s_j a1_j, a1_j) from the
+// first hop.  Only the second hop writes the 36-byte feature rows, each one
+// whole: writing a few columns per pass made DRAM fill and write back the
+// whole feature array on every pass.
+__host__ __device__ __forceinline__ int64_t tmp_floats(int64_t n) { return 8 * n; }
 
-// x0 = log(1 + indeg), x1 = log(1 + outdeg), x8 = N B_i, and t1.
 __global__ void __launch_bounds__(kFeatThreads) k_feat_node(const int32_t *__restrict__ rp,
                                                             const int32_t *__restrict__ in_rp,
                                                             const double *__restrict__ B, int64_t n,
-                                                            float *__restrict__ feat, float2 *__restrict__ t1) {
+                                                            float4 *__restrict__ t1) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int indeg = in_rp[i + 1] - in_rp[i];
         const int outdeg = rp[i + 1] - rp[i];
-        const float ld = log1pf((float)indeg);
-        t1[i] = make_float2(ld, outdeg > 0 ? 1.0f / (float)outdeg : 0.0f);
-        feat[i * kNF + 0] = ld;
-        feat[i * kNF + 1] = log1pf((float)outdeg);
-        feat[i * kNF + 8] = (float)((double)n * B[i]);
+        t1[i] = make_float4(log1pf((float)indeg), outdeg > 0 ? 1.0f / (float)outdeg : 0.0f, log1pf((float)outdeg),
+                            (float)((double)n * B[i]));
     }
 }
 
@@ -109,8 +107,8 @@ template <int HOP>
 struct FeatVal;
 template <>
 struct FeatVal<1> {
-    float2 v;
-    __device__ __forceinline__ void load(const float2 *__restrict__ t1, const float4 *__restrict__, int32_t j) {
+    float4 v;
+    __device__ __forceinline__ void load(const float4 *__restrict__ t1, const float4 *__restrict__, int32_t j) {
         v = __ldg(t1 + j);
     }
     __device__ __forceinline__ void visit(CSum &u, float &m, CSum &w) const {
@@ -122,7 +120,7 @@ struct FeatVal<1> {
 template <>
 struct FeatVal<2> {
     float4 v;
-    __device__ __forceinline__ void load(const float2 *__restrict__, const float4 *__restrict__ t2, int32_t j) {
+    __device__ __forceinline__ void load(const float4 *__restrict__, const float4 *__restrict__ t2, int32_t j) {
         v = __ldg(t2 + j);
     }
     __device__ __forceinline__ void visit(CSum &u, float &m, CSum &w) const {
@@ -136,7 +134,7 @@ struct FeatVal<2> {
 // accumulated (the sums keep the edge order).
 template <int HOP>
 __device__ __forceinline__ void feat_row(const int32_t *__restrict__ in_col, int32_t b, int32_t e,
-                                         const float2 *__restrict__ t1, const float4 *__restrict__ t2, CSum &u,
+                                         const float4 *__restrict__ t1, const float4 *__restrict__ t2, CSum &u,
                                          float &m, CSum &w) {
     int32_t q = b;
     for (; q + 4 <= e; q += 4) {
@@ -153,20 +151,26 @@ __device__ __forceinline__ void feat_row(const int32_t *__restrict__ in_col, int
     }
 }
 
-// Outputs of node i from its in-row sums (u, w), max m and length len.
+// Outputs of node i from its in-row sums (u, w), max m and length len: the
+// first hop fills t2[i], the second writes the node's whole feature row.
 template <int HOP>
-__device__ __forceinline__ void feat_emit(const float2 *__restrict__ t1, float4 *__restrict__ t2,
+__device__ __forceinline__ void feat_emit(const float4 *__restrict__ t1, float4 *__restrict__ t2,
                                           float *__restrict__ feat, int64_t i, int len, float u, float m, float w) {
     const float mean = len > 0 ? u / (float)len : 0.0f;
     if (HOP == 1) {
         t2[i] = make_float4(mean, m, t1[i].y * w, w);
-        feat[i * kNF + 2] = mean;
-        feat[i * kNF + 3] = m;
     } else {
-        feat[i * kNF + 4] = mean;
-        feat[i * kNF + 5] = m;
-        feat[i * kNF + 6] = log1pf(t2[i].w);
-        feat[i * kNF + 7] = log1pf(w);
+        const float4 a = t1[i], b = t2[i];
+        float *__restrict__ f = feat + i * kNF;
+        f[0] = a.x;
+        f[1] = a.z;
+        f[2] = b.x;
+        f[3] = b.y;
+        f[4] = mean;
+        f[5] = m;
+        f[6] = log1pf(b.w);
+        f[7] = log1pf(w);
+        f[8] = a.w;
     }
 }
 
@@ -177,7 +181,7 @@ __device__ __forceinline__ void feat_emit(const float2 *__restrict__ t1, float4 
 template <int HOP>
 __global__ void __launch_bounds__(kFeatThreads) k_feat_hop(const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col, int64_t n,
-                                                           float *__restrict__ feat, float2 *__restrict__ t1,
+                                                           float *__restrict__ feat, float4 *__restrict__ t1,
                                                            float4 *__restrict__ t2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
                                                            const int32_t *__restrict__ lseg0, int n_long,
                                                            int64_t nseg, const int32_t *__restrict__ in_rp,
                                                            const int32_t *__restrict__ in_col,
-                                                           const float2 *__restrict__ t1,
+                                                           const float4 *__restrict__ t1,
                                                            const float4 *__restrict__ t2, double *__restrict__ lacc) {
     __shared__ CSum su[kFeatThreads / 32], sv[kFeatThreads / 32];
     __shared__ float sm[kFeatThreads / 32];
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_feat_seg(const int32_t *__rest
 
 template <int HOP>
 __global__ void k_feat_long(const int32_t *__restrict__ lrows, int n_long, const int32_t *__restrict__ in_rp,
-                            const double *__restrict__ lacc, const float2 *__restrict__ t1,
+                            const double *__restrict__ lacc, const float4 *__restrict__ t1,
                             float4 *__restrict__ t2, float *__restrict__ feat) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_long; r += gridDim.x * blockDim.x) {
         const int32_t i = lrows[r];
@@ -725,9 +729,9 @@ di_status features_into(di_model *m, di_graph *g, const double *B, float *feat, 
         m->lacc_cap = n_long;
     }
     const int cap = g->num_sms * 8;
-    float2 *t1 = reinterpret_cast<float2 *>(m->ftmp);
-    float4 *t2 = reinterpret_cast<float4 *>(m->ftmp + tmp_t2_offset(g->n));
-    k_feat_node<<<grid_of(g->n, kFeatThreads, cap), kFeatThreads, 0, s>>>(g->rp, g->in_rp, B, g->n, feat, t1);
+    float4 *t1 = reinterpret_cast<float4 *>(m->ftmp);
+    float4 *t2 = reinterpret_cast<float4 *>(m->ftmp) + g->n;
+    k_feat_node<<<grid_of(g->n, kFeatThreads, cap), kFeatThreads, 0, s>>>(g->rp, g->in_rp, B, g->n, t1);
     const int hop_grid = grid_of((g->n + 31) / 32, kFeatThreads / 32, cap);
     const int seg_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, cap));
     const int long_grid = grid_of(n_long, 128, cap);
