@@ -66,7 +66,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip e2e, roofline and CPU baseline legs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the oracle check only")
     p.add_argument("--alpha", type=float, default=None, help="threshold decay (library default if unset)")
-    p.add_argument("--recompute-every", type=int, default=None, help="exact FP64 residual period (levels)")
+    p.add_argument("--recompute-every", type=int, default=None,
+                   help="exact FP64 residual every this many levels (stress-16m: 8, its configuration's rule)")
+    p.add_argument("--recompute-drop", type=float, default=None,
+                   help="exact FP64 residual when |F|_1 fell by this factor (library default 1024; stress-16m: off)")
     p.add_argument("--no-l2-window", action="store_true", help="no L2 access-policy windows")
     p.add_argument("--propagation", type=int, default=None,
                    help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push, "
@@ -338,8 +341,13 @@ def run_native(args, world, rank, local):
                            timing=1 if args.host_loop else 0, l2_window=0 if args.no_l2_window else 1)
     if args.alpha is not None:
         opts.alpha = args.alpha
+    if args.workload == "stress-16m":
+        # this workload fixes the refinement schedule: an exact FP64 residual every 8 levels
+        opts.recompute_every, opts.recompute_drop = 8, 0.0
     if args.recompute_every is not None:
         opts.recompute_every = args.recompute_every
+    if args.recompute_drop is not None:
+        opts.recompute_drop = args.recompute_drop
     if args.propagation is not None:
         opts.propagation = args.propagation
     if args.push_ratio is not None:
@@ -396,6 +404,7 @@ def run_native(args, world, rank, local):
         # every push launch of instrumented solves (host-driven levels)
         topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
                                alpha=opts.alpha, recompute_every=opts.recompute_every,
+                               recompute_drop=opts.recompute_drop,
                                l2_window=opts.l2_window, propagation=opts.propagation,
                                push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
                                selection=opts.selection)
@@ -468,6 +477,7 @@ def run_native(args, world, rank, local):
                 "config": {"workload": desc, "n": n, "nnz": nnz, "n_dangling": info["n_dangling"],
                            "n_hot_targets": info["n_hot"], "d": D, "tol": tol, "tol_rel_b_l1": 1e-8,
                            "fluid": prec, "history": "f64", "recompute_every": opts.recompute_every,
+                           "recompute_drop": opts.recompute_drop,
                            "alpha": opts.alpha, "l2": "flushed (256 MiB write) before each timed step",
                            "l2_window": bool(opts.l2_window),
                            "propagation": ["auto: binned gather / push", "auto: flat gather / push",
@@ -613,6 +623,7 @@ def run_batch(args, world, rank, local):
                 "config": {"workload": WORKLOADS["batch-64x4"][1], "items": info["n_items"],
                            "n_union": info["n_union"], "nnz_union": info["nnz_union"],
                            "tol": "1e-8 |B|_1 per item", "l2": "flushed (256 MiB write) before each timed step",
+                           "recompute_every": opts.recompute_every, "recompute_drop": opts.recompute_drop,
                            "push_shape": dict(tune.as_dict(), chosen_by="di_batch_autotune", best_s=tune_s),
                            "level_loop": "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -726,7 +737,8 @@ def run_warmstart(args, world, rank, local):
                        "train_nodes": train_nodes, "eval_graphs": args.ws_eval, "epochs": args.ws_epochs,
                        "lr": args.ws_lr,
                        "tol": "1e-8 |B|_1", "timed": "warm: features + network + F0 + solve; cold: solve",
-                       "l2": "flushed (256 MiB write) before each timed solve"},
+                       "l2": "flushed (256 MiB write) before each timed solve",
+                       "recompute_every": opts_c.recompute_every, "recompute_drop": opts_c.recompute_drop},
             "cold_ms": statistics.mean(cold), "warm_ms": statistics.mean(warm),
             "speedup": statistics.mean(cold) / statistics.mean(warm),
             "inference": infer_parts,

@@ -71,7 +71,7 @@ typedef struct {
     double alpha;          /* threshold decay T <- T/alpha, > 1; default 1.5 (Sec. 2.4) */
     int fluid_fp64;        /* 1: fluid F in FP64; 0: FP32 fluid, FP64 history (default) */
     int recompute_every;   /* FP32 fluid: exact FP64 residual F = B + P H - H every this
-                              many levels; 0 = only to confirm the stop.  default 8 */
+                              many levels; 0 (default) = no level rule */
     int max_levels;        /* level cap -> DI_ENOCONV; default 100000 */
     int warm_start;        /* 1: H holds H0 on entry and F0 = B + P H0 - H0; the first
                               threshold is then |F0|_1 / N (a cold start uses max |F0|) */
@@ -102,6 +102,12 @@ typedef struct {
                               the ideal diffusion order (T_0 and the empty-level rule then
                               use the largest score; the stop rule keeps |F|_1).
                               Needs propagation 3 or 4 */
+    double recompute_drop; /* FP32 fluid: exact FP64 residual whenever the running |F|_1
+                              has fallen by this factor since the last exact value, so
+                              that the FP32 rounding of the pushes stays a fraction of
+                              about 2^-24 * recompute_drop of the residual; 0 = no drop
+                              rule, else > 1; default 1024.  Either rule, and every stop
+                              request, triggers an exact recomputation */
     long long spin_limit;  /* iteration limit of every bounded device wait */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
 } di_opts;
@@ -137,9 +143,10 @@ DI_API const char *di_version(void);
 /* Message of the last failed call on this thread ("" if none). */
 DI_API const char *di_last_error(void);
 
-/* Defaults: alpha 1.5, FP32 fluid, recompute_every 8, max_levels 100000,
- * cold start (fallback on when warm), L2 window on, timing off,
- * propagation 3, push_ratio 8, exact_residual 0, selection 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+/* Defaults: alpha 1.5, FP32 fluid, recompute_every 0, recompute_drop 1024,
+ * max_levels 100000, cold start (fallback on when warm), L2 window on,
+ * timing off, propagation 3, push_ratio 8, exact_residual 0, selection 0,
+ * spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*

@@ -30,7 +30,8 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     std::memset(o, 0, sizeof(*o));
     o->alpha = 1.5;
     o->fluid_fp64 = 0;
-    o->recompute_every = 8;
+    o->recompute_every = 0;
+    o->recompute_drop = 1024.0;
     o->max_levels = 100000;
     o->warm_start = 0;
     o->warm_fallback = 1;

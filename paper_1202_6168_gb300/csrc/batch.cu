@@ -70,6 +70,7 @@ struct BState {
 
 struct BDesc {
     double d, alpha;
+    double drop;         // exact recompute when an item's |F|_1 fell this much since its last one (0 = none)
     int R, fp64, max_levels, max_body_iters, nitems, final_mode;
     int thread_max, warp_max;  // push shape
     void *F;             // union fluid (float or double)
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
     // control step of every item (one thread per item)
     const double alpha = desc->alpha;
     const int R = desc->R, fp64 = desc->fp64, max_levels = desc->max_levels;
+    const double drop = desc->drop;
     int any_rec = 0, live = 0;
     for (int t = threadIdx.x; t < desc->nitems; t += blockDim.x) {
         BItem &it = items[t];
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
                 it.node_diff += nsel;
                 it.edge_diff += esel;
                 T /= alpha;
-                if (!fp64 && R > 0 && it.since >= R) rec = 1;
+                // refinement: every R levels, or once |F|_1 fell by drop since the last exact value
+                if (!fp64 && ((R > 0 && it.since >= R) || (drop > 0.0 && ts * est * drop <= it.r_exact))) rec = 1;
             }
             it.T = T;
         }
@@ -865,6 +868,10 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
     if (!(d > 0.0 && d < 1.0)) { set_error("di_solve_batched: d = %g outside (0, 1)", d); return DI_EINVAL; }
     if (!(o.alpha > 1.0) || !std::isfinite(o.alpha)) { set_error("di_solve_batched: alpha = %g must be > 1", o.alpha); return DI_EINVAL; }
     if (o.max_levels < 0 || o.recompute_every < 0) { set_error("di_solve_batched: negative max_levels or recompute_every"); return DI_EINVAL; }
+    if (!(o.recompute_drop == 0.0 || (o.recompute_drop > 1.0 && std::isfinite(o.recompute_drop)))) {
+        set_error("di_solve_batched: recompute_drop = %g must be 0 or a finite factor > 1", o.recompute_drop);
+        return DI_EINVAL;
+    }
     if (o.warm_start) { set_error("di_solve_batched: warm starts are not supported in a batch"); return DI_EINVAL; }
     for (int t = 0; t < b->nitems; ++t) {
         if (!B[t] || !H[t]) { set_error("di_solve_batched: NULL B or H of item %d", t); return DI_EINVAL; }
@@ -895,6 +902,7 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
     dh.d = d;
     dh.alpha = o.alpha;
     dh.R = o.recompute_every;
+    dh.drop = o.recompute_drop;
     dh.fp64 = fp64;
     dh.max_levels = o.max_levels;
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);

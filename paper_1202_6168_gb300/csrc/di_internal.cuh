@@ -58,7 +58,8 @@ struct SolveDesc {
     void *F;              // internal fluid (float or double)
     double d, tol, alpha;
     int max_levels;
-    int recompute_every;  // FP32 fluid: exact recompute period (levels)
+    int recompute_every;  // FP32 fluid: exact recompute period (levels), 0 = none
+    double recompute_drop;// FP32 fluid: exact recompute when |F|_1 fell this much since the last, 0 = none
     int fluid_fp64;
     int max_body_iters;   // absolute cap on loop iterations (safety net)
     int propagation;      // 0/1 auto (binned/flat gather for dense levels), 2 push only, 3 async push

@@ -108,6 +108,20 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
     }
 }
 
+// Exact recomputation as iterative refinement (FP32 fluid only): every
+// recompute_every levels, and whenever the running |F|_1 estimate r has
+// fallen by the factor recompute_drop since the last exact residual.  The
+// FP32 pushes round each target to 2^-24 of its value, so the drift they add
+// between two recomputations stays a small multiple of 2^-24 * recompute_drop
+// of the current residual.
+__device__ __forceinline__ bool refine_due(const SolveDesc *__restrict__ desc, const SolveState *__restrict__ st,
+                                           int since, double r) {
+    if (desc->fluid_fp64) return false;
+    const int R = desc->recompute_every;
+    const double drop = desc->recompute_drop;
+    return (R > 0 && since >= R) || (drop > 0.0 && r * drop <= st->r_exact);
+}
+
 // |B|_1 only (warm start)
 __global__ void __launch_bounds__(kScanThreads) k_bnorm(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                         int64_t n, double *__restrict__ part_sum,
@@ -352,7 +366,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     int level = st->level, since = st->since_recompute, iters = st->body_iters;
     const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
-    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    const int max_iters = desc->max_body_iters;
     int done = 0, rec = 0, push = 0;
     if (!isfinite(ts)) {
         done = 3;
@@ -368,7 +382,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
         level += 1;
         since += 1;
         T = T / alpha;
-        if (!fp64 && R > 0 && since >= R) rec = 1;
+        if (refine_due(desc, st, since, ts * est)) rec = 1;
     }
     iters += 1;
     if (!done && iters >= max_iters) done = 2;
@@ -697,7 +711,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     int level = st->level, since = st->since_recompute, iters = st->body_iters;
     const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
-    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    const int max_iters = desc->max_body_iters;
     int done = 0, rec = 0;
     if (!isfinite(ts)) {
         done = 3;
@@ -706,7 +720,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
             level += 1;
             since += 1;
             T = T / alpha;
-            if (!fp64 && R > 0 && since >= R) rec = 1;
+            if (refine_due(desc, st, since, ts * est)) rec = 1;
         } else if (tm > 0.0) {
             for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
         }
@@ -866,7 +880,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_select(
     int level = st->level, since = st->since_recompute, iters = st->body_iters;
     const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
-    const int R = desc->recompute_every, fp64 = desc->fluid_fp64, max_iters = desc->max_body_iters;
+    const int max_iters = desc->max_body_iters;
     int done = 0, rec = 0, p2 = P2_NONE;
     if (!isfinite(ts)) {
         done = 3;
@@ -889,7 +903,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_select(
             rec = 1;                      // stop request: confirm on the exact residual
             st->confirming = 1;
             st->r_confirm = ts * est;
-        } else if (!fp64 && R > 0 && since >= R) {
+        } else if (refine_due(desc, st, since, ts * est)) {
             rec = 1;
         }
     }
@@ -1329,6 +1343,10 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("di_solve: tol = %g must be finite and > 0", tol); return DI_EINVAL; }
     if (!(o->alpha > 1.0) || !std::isfinite(o->alpha)) { set_error("di_solve: alpha = %g must be > 1", o->alpha); return DI_EINVAL; }
     if (o->max_levels < 0 || o->recompute_every < 0) { set_error("di_solve: negative max_levels or recompute_every"); return DI_EINVAL; }
+    if (!(o->recompute_drop == 0.0 || (o->recompute_drop > 1.0 && std::isfinite(o->recompute_drop)))) {
+        set_error("di_solve: recompute_drop = %g must be 0 or a finite factor > 1", o->recompute_drop);
+        return DI_EINVAL;
+    }
     if (o->propagation < 0 || o->propagation > 5) { set_error("di_solve: propagation = %d outside [0, 5]", o->propagation); return DI_EINVAL; }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
@@ -1444,6 +1462,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.alpha = o.alpha;
     dh.max_levels = o.max_levels;
     dh.recompute_every = o.recompute_every;
+    dh.recompute_drop = o.recompute_drop;
     dh.fluid_fp64 = fp64;
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
     dh.propagation = o.propagation;

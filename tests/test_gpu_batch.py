@@ -149,6 +149,30 @@ def test_batch_timing_mode_matches():
     g.close()
 
 
+@pytest.mark.parametrize("every,drop", [(8, 0.0), (0, 64.0)])
+def test_batch_refinement_schedules(mixed_graphs, every, drop):
+    rng = np.random.default_rng(every + 1)
+    graphs = [di.Graph.create(rp, col) for rp, col in mixed_graphs[:4]]
+    batch = di.Batch(graphs, [1, 2, 1, 1])
+    items = []
+    for (rp, col), r in zip(mixed_graphs[:4], [1, 2, 1, 1]):
+        for k in range(r):
+            items.append((rp, col, rhs_for(len(rp) - 1, k, rng)))
+    tols = [1e-8 * b.sum() for _, _, b in items]
+    H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
+    rc, st, _ = di.di_solve_batched(batch, [dev(b) for _, _, b in items], D, tols, H,
+                                    di.opts_default(recompute_every=every, recompute_drop=drop))
+    for (rp, col, b), h, s, tol in zip(items, H, st, tols):
+        x = oracle_x(rp, col, b)
+        assert np.abs(h.cpu().numpy() - x).sum() <= 1e-6 * np.abs(x).sum()
+        stop_ok(rp, col, b, h.cpu().numpy(), tol, s.resid_l1)
+        if every:
+            assert s.recomputes >= s.levels // every
+    batch.close()
+    for g in graphs:
+        g.close()
+
+
 def test_batch_rejects_bad_arguments():
     rp, col = csr_from_edges(3, [(0, 1), (1, 2)])
     g = di.Graph.create(rp, col)
@@ -163,6 +187,9 @@ def test_batch_rejects_bad_arguments():
         assert e.value.status == di.DI_EINVAL
     with pytest.raises(di.DiError) as e:
         di.di_solve_batched(batch, B, D, 1e-8, H, di.opts_default(warm_start=1))
+    assert e.value.status == di.DI_EINVAL
+    with pytest.raises(di.DiError) as e:
+        di.di_solve_batched(batch, B, D, 1e-8, H, di.opts_default(recompute_drop=0.9))
     assert e.value.status == di.DI_EINVAL
     batch.close()
     g.close()

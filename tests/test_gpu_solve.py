@@ -311,7 +311,30 @@ def test_invalid_inputs_are_rejected():
         with pytest.raises(di.DiError) as e:
             di.di_solve(g, B, d, tol, H)
         assert e.value.status == di.DI_EINVAL
+    for drop in (0.5, 1.0, -2.0, float("inf"), float("nan")):
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, B, D, 1e-8, H, None, di.opts_default(recompute_drop=drop))
+        assert e.value.status == di.DI_EINVAL
     g.close()
+
+
+@pytest.mark.parametrize("every,drop", [(0, 1024.0), (8, 0.0), (3, 16.0), (0, 0.0)])
+def test_refinement_schedules(web10k, every, drop):
+    # exact FP64 recomputations every `every` levels and/or whenever |F|_1 fell
+    # by `drop`; (0, 0) leaves only the confirmations of stop requests.  Any
+    # schedule reaches the same X within the FP32 tolerance and stops on an
+    # exact residual below tol.
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, recompute_every=every, recompute_drop=drop)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    assert st.recomputes >= 1
+    if every:
+        assert st.recomputes >= st.levels // every
+    if drop:
+        # one recomputation at least per factor `drop` of the residual's fall
+        assert st.recomputes >= int(np.log(b.sum() / tol) / np.log(drop))
 
 
 def test_device_resident_csr_input(web10k):
