@@ -362,7 +362,8 @@ DI_API di_status di_warmstart_train(di_model *m, di_graph *const *graphs, int ng
                                     const double *const *X, const di_train_opts *opts, double *final_loss);
 
 /* H0 = exp(y) / N for every node of g (device H0, n doubles) from the
- * features of g and B (device).  Asynchronous on stream. */
+ * features of g and B (device); the exponential is taken in FP32 (any H0 is
+ * a valid start, and F0 is formed from it exactly).  Asynchronous on stream. */
 DI_API di_status di_warmstart_infer(di_model *m, di_graph *g, const double *B, double *H0, void *stream);
 
 /* Model file: header, step, state, Adam moments (little-endian floats). */

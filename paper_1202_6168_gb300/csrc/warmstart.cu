@@ -301,7 +301,7 @@ struct FwdArgs {
     const __nv_bfloat16 *wbf; // BF16 W1 [64][16] then W2 [64][64]
     const float *norm;        // mu[9], sd[9]
     float *y;                 // FWD_Y / FWD_TRAIN: prediction per row
-    double *h0;               // FWD_H0: exp(y) / N per node
+    double *h0;               // FWD_H0: expf(y) / N per node
     double inv_n;
     // training
     const float *target;      // per node
@@ -407,9 +407,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_mlp_fwd(const FwdArgs a) {
         p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
         const float y0 = p0 + sb3, y1 = p1 + sb3;
         if (MODE == FWD_H0) {
+            // H0 is only a start (F0 is formed from it exactly), so the
+            // exponential is taken in FP32: an FP64 exp per node would run on
+            // GB300's narrow FP64 pipe
             if (tig == 0) {
-                if (v0) a.h0[r0] = exp((double)y0) * a.inv_n;
-                if (v1) a.h0[r1] = exp((double)y1) * a.inv_n;
+                if (v0) a.h0[r0] = (double)expf(y0) * a.inv_n;
+                if (v1) a.h0[r1] = (double)expf(y1) * a.inv_n;
             }
             continue;
         }
