@@ -108,7 +108,9 @@ typedef struct {
                               about 2^-24 * recompute_drop of the residual; 0 = no drop
                               rule, else > 1; default 1024.  Either rule, and every stop
                               request, triggers an exact recomputation */
-    long long spin_limit;  /* iteration limit of every bounded device wait */
+    long long spin_limit;  /* iteration limit of a bounded device wait.  Reserved: no
+                              kernel of this library waits on another CTA (cross-CTA
+                              decisions use a last-block counter), so it is unused */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
 } di_opts;
 

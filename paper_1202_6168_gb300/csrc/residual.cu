@@ -6,10 +6,16 @@
 // rounding that FP32 pushes accumulate, gives the exact stopping residual
 // |F|_1, and forms the warm-start fluid F_0.
 //
-// (P H)_k = sum over in-edges j -> k of g_j, g_j = (d / outdeg_j) H_j, is a
-// gather over the transpose with the binned pull plan of pull.cuh: no
-// atomics and a fixed summation order per graph object (rows longer than
-// 4096 in-edges are summed in segments whose partials are added in order).
+// (P H)_k = sum over in-edges j -> k of g_j, g_j = (d / outdeg_j) H_j, in
+// one of two forms:
+//   source-blocked (default): the in-edges ordered by block of 2^22 sources,
+//     then by destination, so that the grid gathers from one 32 MB block of
+//     g at a time (L2-resident); runs of equal destination are summed per
+//     thread and added with FP64 reds (k_resb_*);
+//   binned: a gather over the transpose with the binned pull plan of
+//     pull.cuh, with no atomics and a fixed summation order per graph object
+//     (rows longer than 4096 in-edges are summed in segments whose partials
+//     are added in order) (k_res_*).
 #include <algorithm>
 
 #include "di_internal.cuh"
