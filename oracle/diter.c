@@ -30,6 +30,11 @@
  *   - warm start: H_0 given, F_0 = B + P H_0 - H_0 (signed fluid is selected
  *     on |F_i| and r is the L1 norm).
  *
+ * Optional dangling completion (Sec. 2.2 notes that the dangling columns of
+ * Q may be completed by 1/N, which makes Q stochastic): with dangling != 0,
+ * column j of Q for a node without out-edges is the uniform 1/N, so
+ * diffusing such a node adds d F_j / N to every node k, itself included.
+ *
  * Optional weighted selection (Sec. 2.4 names the ideal order as the argmax of
  * F_i / ((#in_i + 1)(#out_i + 1)) and approximates it by a threshold sweep):
  * with weights w_i the sweep selects |F_i| w_i >= T instead, T_0 and the
@@ -47,13 +52,18 @@ typedef struct {
     double threshold;         /* T at return */
 } oracle_stats;
 
-/* F = B + P H - H, column by column (FP64); returns sum |F_i|. */
+/* F = B + P H - H, column by column (FP64); returns sum |F_i|.  With
+ * dangling != 0 a column without out-edges is d/N in every row. */
 double oracle_residual(int64_t n, const int64_t *row_ptr, const int32_t *col,
-                       const double *B, double d, const double *H, double *F) {
+                       const double *B, double d, const double *H, double *F, int dangling) {
     for (int64_t k = 0; k < n; ++k) F[k] = B[k] - H[k];
     for (int64_t j = 0; j < n; ++j) {
         int64_t deg = row_ptr[j + 1] - row_ptr[j];
-        if (deg == 0) continue;
+        if (deg == 0) {
+            if (dangling)
+                for (int64_t k = 0; k < n; ++k) F[k] += d / (double)n * H[j];
+            continue;
+        }
         double p = d / (double)deg;
         for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) F[col[e]] += p * H[j];
     }
@@ -72,10 +82,10 @@ double oracle_residual(int64_t n, const int64_t *row_ptr, const int32_t *col,
 int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *B,
                  double d, double tol, double alpha, int64_t max_levels, int warm,
                  double *H, double *F, oracle_stats *st, double *trace, int64_t trace_cap,
-                 const double *w) {
+                 const double *w, int dangling) {
     if (n < 0 || !(alpha > 1.0) || !(tol >= 0.0) || max_levels < 0) return 1;
     if (warm) {
-        oracle_residual(n, row_ptr, col, B, d, H, F);
+        oracle_residual(n, row_ptr, col, B, d, H, F, dangling);
     } else {
         for (int64_t i = 0; i < n; ++i) { F[i] = B[i]; H[i] = 0.0; }
     }
@@ -108,7 +118,11 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
             F[i] = 0.0;
             int64_t deg = row_ptr[i + 1] - row_ptr[i];
             s.node_diffusions += 1;
-            if (deg == 0) continue;
+            if (deg == 0) {
+                if (dangling)                   /* the uniform column: d/N to every node */
+                    for (int64_t k = 0; k < n; ++k) F[k] += sent * (d / (double)n);
+                continue;
+            }
             double p = d / (double)deg;     /* p_ki, the same for every child k */
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) F[col[e]] += sent * p;
             s.edge_diffusions += deg;

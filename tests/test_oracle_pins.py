@@ -363,3 +363,94 @@ def test_weighted_equals_raw_when_every_node_has_the_same_degrees():
     w = od.d_iteration(rp, col, b, D, tol=1e-12, weighted=True)
     assert (a.levels, a.node_diffusions, a.edge_diffusions) == (w.levels, w.node_diffusions, w.edge_diffusions)
     np.testing.assert_array_equal(a.H, w.H)
+
+
+# ---------------------------------------------------------------- 1/N completion of dangling columns (Sec. 2.2)
+
+def exact_solve_completed(rp, col, b, d=Fraction(17, 20)):
+    """(I - P) X = B over the rationals when every column without out-edges
+    is d/N in every row (Sec. 2.2's completion), by Gauss-Jordan elimination."""
+    n = len(rp) - 1
+    A = [[Fraction(int(i == k)) for k in range(n)] for i in range(n)]
+    for j in range(n):
+        deg = int(rp[j + 1] - rp[j])
+        if deg == 0:
+            for i in range(n):
+                A[i][j] -= d / n
+        for e in range(rp[j], rp[j + 1]):
+            A[int(col[e])][j] -= d / deg
+    rhs = [Fraction(x) for x in b]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if A[r][c] != 0)
+        A[c], A[piv] = A[piv], A[c]
+        rhs[c], rhs[piv] = rhs[piv], rhs[c]
+        for r in range(n):
+            if r != c and A[r][c] != 0:
+                f = A[r][c] / A[c][c]
+                A[r] = [a - f * p for a, p in zip(A[r], A[c])]
+                rhs[r] -= f * rhs[c]
+    return [rhs[i] / A[i][i] for i in range(n)]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_completion_matches_exact_rational_solution(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(3, 10))
+    rp, col = random_graph(n, rng, p_dangling=0.4)
+    b = [Fraction(int(rng.integers(0, 7)), 100) for _ in range(n)]
+    b[0] += Fraction(1, 50)
+    x = np.array([float(v) for v in exact_solve_completed(rp, col, b)])
+    res = od.d_iteration(rp, col, np.array([float(v) for v in b]), D, tol=1e-17, dangling=True)
+    assert res.status == 0
+    assert np.abs(res.H - x).sum() <= 1e-14 * np.abs(x).sum()
+
+
+def test_completion_makes_the_pagerank_mass_one():
+    # completed columns sum to d, so 1'X = 1'B / (1 - d) = 1 for B = (1-d)/N,
+    # whatever the share of dangling nodes (without the completion it is < 1)
+    rp, col = gg.generate(gg.GraphSpec(n=3000, mean_deg=6.0, seed=21, p_dangling=0.3))
+    assert np.sum(np.diff(rp) == 0) > 500
+    b = gg.uniform_b(3000, D)
+    res = od.d_iteration(rp, col, b, D, tol=1e-14, dangling=True)
+    assert res.H.sum() == pytest.approx(1.0, abs=1e-12)
+    plain = od.d_iteration(rp, col, b, D, tol=1e-14)
+    assert plain.H.sum() < 0.9
+
+
+def test_completion_on_a_graph_without_edges():
+    # every column is d/N everywhere: X_k = B_k + d * sum(B) / ((1 - d) N)
+    n = 7
+    rp, col = csr_from_edges(n, [])
+    b = np.array([0.1, 0.0, 0.3, 0.05, 0.0, 0.2, 0.01])
+    res = od.d_iteration(rp, col, b, D, tol=1e-16, dangling=True)
+    want = b + D * b.sum() / ((1 - D) * n)
+    np.testing.assert_allclose(res.H, want, rtol=1e-13)
+
+
+def test_completion_residual_and_invariant():
+    # F_n = B + P H_n - H_n with the completed P after any number of sweeps,
+    # and the residual helper equals an independent dense matvec
+    rng = np.random.default_rng(33)
+    rp, col = random_graph(60, rng, p_dangling=0.3)
+    b = rng.random(60)
+    P = np.zeros((60, 60))
+    for j in range(60):
+        deg = rp[j + 1] - rp[j]
+        if deg == 0:
+            P[:, j] = D / 60
+        for e in range(rp[j], rp[j + 1]):
+            P[col[e], j] += D / deg
+    for levels in (1, 3, 7):
+        res = od.d_iteration(rp, col, b, D, tol=0.0, max_levels=levels, dangling=True)
+        np.testing.assert_allclose(res.F, b + P @ res.H - res.H, atol=1e-14)
+        f, r = od.residual(rp, col, b, D, res.H, dangling=True)
+        np.testing.assert_allclose(f, res.F, atol=1e-14)
+        assert r == pytest.approx(np.abs(res.F).sum(), rel=1e-12)
+
+
+def test_completion_power_iteration_agrees():
+    rp, col = gg.generate(gg.GraphSpec(n=2000, mean_deg=5.0, seed=22, p_dangling=0.25))
+    b = gg.uniform_b(2000, D)
+    x, _ = od.power_iteration(rp, col, b, D, dangling=True)
+    res = od.d_iteration(rp, col, b, D, tol=1e-14, dangling=True)
+    assert np.abs(res.H - x).sum() <= 1e-12
