@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
     p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
+    p.add_argument("--dangling", action="store_true",
+                   help="complete the dangling columns by 1/N (standard PageRank normalisation)")
     p.add_argument("--weighted", action="store_true",
                    help="select on |F_i| / ((in_i + 1)(out_i + 1)) (the score of the paper's ideal order)")
     p.add_argument("--ws-train", type=int, default=200, help="warm start: training graphs")
@@ -196,11 +198,11 @@ def level_traffic(workload: str, prec: str, propagation: int):
     return None
 
 
-def cpu_baseline(rp, col, b, tol):
+def cpu_baseline(rp, col, b, tol, dangling=False):
     """The CPU oracle as it stands, on one host core, one full solve."""
     from oracle import diter as od
     t0 = time.perf_counter()
-    r = od.d_iteration(rp, col, b, D, tol=tol)
+    r = od.d_iteration(rp, col, b, D, tol=tol, dangling=dangling)
     dt = time.perf_counter() - t0
     return {"value": r.edge_diffusions / dt, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
             "sample": f"one full sequential FP64 solve of the same graph to the same tol "
@@ -356,6 +358,8 @@ def run_native(args, world, rank, local):
         opts.exact_residual = args.exact_residual
     if args.weighted:
         opts.selection = 1
+    if args.dangling:
+        opts.dangling = 1
 
     g = di.Graph.create(rp, col, stream=stream)
     B = torch.from_numpy(b).cuda()
@@ -407,7 +411,7 @@ def run_native(args, world, rank, local):
                                recompute_drop=opts.recompute_drop,
                                l2_window=opts.l2_window, propagation=opts.propagation,
                                push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
-                               selection=opts.selection)
+                               selection=opts.selection, dangling=opts.dangling)
         te = tn = 0
         tpush = trec = tsel = 0.0
         npush = 0
@@ -458,15 +462,19 @@ def run_native(args, world, rank, local):
             # error of the result against the exact residual bound, and the CPU oracle
             h = H.cpu().numpy()
             from oracle import diter as od
-            _, r_cpu = od.residual(rp, col, b, D, h)
+            dang = bool(opts.dangling)
+            _, r_cpu = od.residual(rp, col, b, D, h, dangling=dang)
             extras["check"] = {"resid_l1_oracle_fp64": r_cpu, "tol": tol,
                                "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
                                "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
-            if n <= 4_000_000:
+            # the oracle spreads a dangling diffusion over all N nodes one by one,
+            # which is too slow beyond small graphs: no oracle solve then
+            if n <= (100_000 if dang else 4_000_000):
                 # error against the oracle's FP64 solution (solved to 1e-14 |B|_1)
-                x = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum()).H
+                x = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum(), dangling=dang).H
                 extras["check"]["rel_l1_err_vs_oracle_x"] = float(np.abs(h - x).sum() / np.abs(x).sum())
-            extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol)
+            if not dang or n <= 100_000:
+                extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol, dang)
 
     if rank == 0:
         info = g.info()
@@ -488,6 +496,7 @@ def run_native(args, world, rank, local):
                            "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
                            "selection": ["|F_i| >= T", "|F_i| / ((in_i+1)(out_i+1)) >= T"][opts.selection],
+                           "dangling": ["zero columns", "uniform 1/N completion"][opts.dangling],
                            "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "time_to_tol_ms": 1e3 * secs_max / args.steps,

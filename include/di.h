@@ -3,7 +3,8 @@
  *
  * The library solves X = P X + B (Eq. 1) for a sparse contractive P of the
  * PageRank form P = d Q (Eq. 2), q_kj = 1/#out_j for every edge j -> k and a
- * zero column for a dangling j (Sec. 2.2), by fluid diffusion (D-iteration,
+ * zero column for a dangling j, or optionally its 1/N completion (Sec. 2.2),
+ * by fluid diffusion (D-iteration,
  * Eqs. defF/defH): diffusing node i moves its fluid F_i into its history H_i
  * and adds p_ki F_i to the fluid of every child k.  Nodes are chosen by the
  * cyclic threshold rule of Sec. 2.4: every node with |F_i| >= T diffuses,
@@ -102,6 +103,13 @@ typedef struct {
                               the ideal diffusion order (T_0 and the empty-level rule then
                               use the largest score; the stop rule keeps |F|_1).
                               Needs propagation 3 or 4 */
+    int dangling;          /* columns of nodes without out-edges: 0 (default) zero, so
+                              sum X < 1; 1 the uniform 1/N completion of Sec. 2.2
+                              (p_kj = d/N for every k), which makes the columns of Q
+                              stochastic.  The fluid a dangling node drains is spread
+                              over all nodes as one uniform add in the next frontier
+                              selection; the exact residual adds d/N sum_dangling H_j.
+                              Needs propagation 3 or 4 and exact_residual 0 or 2 */
     double recompute_drop; /* FP32 fluid: exact FP64 residual whenever the running |F|_1
                               has fallen by this factor since the last exact value, so
                               that the FP32 rounding of the pushes stays a fraction of
@@ -148,7 +156,7 @@ DI_API const char *di_last_error(void);
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 0, recompute_drop 1024,
  * max_levels 100000, cold start (fallback on when warm), L2 window on,
  * timing off, propagation 3, push_ratio 8, exact_residual 0, selection 0,
- * spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+ * dangling 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*

@@ -53,20 +53,23 @@ typedef struct {
 } oracle_stats;
 
 /* F = B + P H - H, column by column (FP64); returns sum |F_i|.  With
- * dangling != 0 a column without out-edges is d/N in every row. */
+ * dangling != 0 a column without out-edges is d/N in every row, so those
+ * columns add d/N times the sum of H over the dangling nodes to every row. */
 double oracle_residual(int64_t n, const int64_t *row_ptr, const int32_t *col,
                        const double *B, double d, const double *H, double *F, int dangling) {
+    double h_dangling = 0.0;
     for (int64_t k = 0; k < n; ++k) F[k] = B[k] - H[k];
     for (int64_t j = 0; j < n; ++j) {
         int64_t deg = row_ptr[j + 1] - row_ptr[j];
         if (deg == 0) {
-            if (dangling)
-                for (int64_t k = 0; k < n; ++k) F[k] += d / (double)n * H[j];
+            h_dangling += H[j];
             continue;
         }
         double p = d / (double)deg;
         for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) F[col[e]] += p * H[j];
     }
+    if (dangling)
+        for (int64_t k = 0; k < n; ++k) F[k] += d / (double)n * h_dangling;
     double r = 0.0;
     for (int64_t k = 0; k < n; ++k) r += fabs(F[k]);
     return r;

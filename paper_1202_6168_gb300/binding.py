@@ -25,7 +25,7 @@ class di_opts(ctypes.Structure):
     _fields_ = [("alpha", c_dbl), ("fluid_fp64", c_int), ("recompute_every", c_int),
                 ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
                 ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int), ("exact_residual", c_int), ("selection", c_int),
-                ("recompute_drop", c_dbl), ("spin_limit", ctypes.c_longlong),
+                ("dangling", c_int), ("recompute_drop", c_dbl), ("spin_limit", ctypes.c_longlong),
                 ("stream", c_vp)]
 
 

@@ -41,6 +41,7 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->push_ratio = 8;
     o->exact_residual = 0;
     o->selection = 0;
+    o->dangling = 0;
     o->spin_limit = 1LL << 26;
     o->stream = nullptr;
     return DI_OK;

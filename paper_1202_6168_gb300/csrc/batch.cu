@@ -873,6 +873,7 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
         return DI_EINVAL;
     }
     if (o.warm_start) { set_error("di_solve_batched: warm starts are not supported in a batch"); return DI_EINVAL; }
+    if (o.dangling) { set_error("di_solve_batched: the 1/N dangling completion is not supported in a batch"); return DI_EINVAL; }
     for (int t = 0; t < b->nitems; ++t) {
         if (!B[t] || !H[t]) { set_error("di_solve_batched: NULL B or H of item %d", t); return DI_EINVAL; }
         if (!(tol[t] > 0.0) || !std::isfinite(tol[t])) {

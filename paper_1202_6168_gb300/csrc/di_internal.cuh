@@ -68,6 +68,7 @@ struct SolveDesc {
     int thread_max;       // push shape: rows up to this many edges go to one thread
     int warp_max;         // ... up to this to one warp, longer ones to the CTA
     const void *iw;       // weighted selection: 1 / ((in + 1)(out + 1)) per node (FT), else NULL
+    int dangling;         // 1: columns of dangling nodes completed by d/N (uniform)
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -103,6 +104,8 @@ struct SolveState {
     unsigned int res_blocks;
     unsigned int init_blocks;
     int pad;
+    double dang_acc;            // fluid drained from dangling nodes since the last selection
+    double dang_h;              // exact residual: sum of H over the dangling nodes
 };
 
 enum ResMode : int {

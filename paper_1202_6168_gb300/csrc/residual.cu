@@ -123,19 +123,30 @@ __global__ void __launch_bounds__(kResThreads) k_res_long(
 
 // ------------------------------------------------------------------ source-blocked form
 
-// acc = B - H and g = (d / outdeg) H.
+// acc = B - H and g = (d / outdeg) H.  With the 1/N completion of dangling
+// columns (Sec. 2.2) the sum of H over the dangling nodes (s = 0) goes to
+// st->dang_h, one FP64 atomic per CTA.
 __global__ void __launch_bounds__(kResThreads) k_resb_init(const SolveDesc *__restrict__ desc,
-                                                           const SolveState *__restrict__ st, int mode,
+                                                           SolveState *__restrict__ st, int mode,
                                                            const double *__restrict__ s64, double *__restrict__ g,
                                                            double *__restrict__ acc, int64_t n) {
     if (mode == RES_LEVEL && !st->do_recompute) return;
     const double *__restrict__ B = desc->B;
     const double *__restrict__ H = desc->H;
+    const bool dang = desc->dangling != 0;
+    double hd = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double h = H[i];
-        g[i] = s64[i] * h;
+        const double s = s64[i];
+        g[i] = s * h;
         acc[i] = B[i] - h;
+        if (dang && s == 0.0) hd += h;
+    }
+    if (dang) {
+        double dummy = 0.0;
+        block_sum_max<kResThreads>(hd, dummy);
+        if (threadIdx.x == 0 && hd != 0.0) atomicAdd(&st->dang_h, hd);
     }
 }
 
@@ -203,10 +214,12 @@ __global__ void __launch_bounds__(kResThreads) k_resb_fin(const SolveDesc *__res
     if (mode == RES_LEVEL && !st->do_recompute) return;
     FT *__restrict__ Ffl = (mode == RES_LEVEL || mode == RES_WARM_INIT) ? static_cast<FT *>(desc->F) : nullptr;
     double *__restrict__ F64 = mode == RES_WARM_INIT ? nullptr : desc->F_out;
+    // the completed dangling columns add d/N sum_dangling H_j to every row
+    const double ud = desc->dangling ? desc->d * st->dang_h / (double)n : 0.0;
     double lsum = 0.0, lmax = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double f = acc[i];
+        const double f = acc[i] + ud;
         if (Ffl) Ffl[i] = static_cast<FT>(f);
         if (F64) F64[i] = f;
         lsum += fabs(f);
@@ -225,6 +238,7 @@ __global__ void __launch_bounds__(kResThreads) k_resb_fin(const SolveDesc *__res
     }
     block_sum_max<kResThreads>(s, m);
     if (threadIdx.x != 0) return;
+    st->dang_h = 0.0;                       // every CTA read it before this, the last one
     res_control(desc, st, mode, s, m);
 }
 
@@ -236,6 +250,8 @@ __device__ void res_control(const SolveDesc *__restrict__ desc, SolveState *__re
                             double m) {
     st->r_exact = s;
     st->max_exact = m;
+    // the exact F already holds the fluid that dangling nodes drained
+    if (mode == RES_LEVEL || mode == RES_WARM_INIT) st->dang_acc = 0.0;
     if (mode == RES_LEVEL) {
         st->recomputes += 1;
         st->since_recompute = 0;

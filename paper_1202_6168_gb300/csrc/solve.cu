@@ -240,8 +240,13 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
         }
     }
     using AT = typename Acc<FT>::T;
-    const FT *__restrict__ F = static_cast<const FT *>(desc->F);
+    // not __restrict__: with the dangling completion pass 1 writes F and pass 2 reads it back
+    FT *F = static_cast<FT *>(desc->F);
     const FT Tc = thr_cast(st->T, FT(0));
+    // 1/N completion (Sec. 2.2): the fluid that dangling nodes drained since the
+    // last selection reaches every node as d / N of it; added here, before the
+    // test, and stored (the last CTA clears the accumulator)
+    const FT u = desc->dangling ? static_cast<FT>(desc->d * st->dang_acc / (double)n) : FT(0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // vector layout of a 2048-node chunk: item k (0, 1), thread t, nodes
     // c0 + 1024 k + 4 t + j (j = 0..3), which is node order; the fluid vector
@@ -278,6 +283,17 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
             const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
             if (i0 < n) f[k].load(F + i0);
             else f[k].v[0] = f[k].v[1] = f[k].v[2] = f[k].v[3] = FT(0);
+        }
+        if (u != FT(0)) {
+#pragma unroll
+            for (int k = 0; k < kVItems; ++k) {
+                const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
+                if (i0 >= n) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j < n) f[k].v[j] += u;   // the zero padding past n stays zero
+                f[k].store(F + i0);
+            }
         }
 #pragma unroll
         for (int k = 0; k < kVItems; ++k) {
@@ -391,6 +407,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     st->max_scan = tm;
     st->nfront = 0;
     st->tile_ctr = 0;
+    st->dang_acc = 0.0;                 // every CTA added it before this, the last one
     st->push_count = push;
     st->T = T;
     st->level = level;
@@ -412,7 +429,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 // or by the whole CTA.  Targets of very high in-degree are accumulated in
 // shared memory per CTA and flushed once.
 template <typename FT>
-__global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+__global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 6 : 8)
+    k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                        const int32_t *__restrict__ front,
                                                        const int32_t *__restrict__ rp,
                                                        const int32_t *__restrict__ pcol,
@@ -426,10 +444,12 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
     __shared__ int s_qn;
     __shared__ int32_t s_qb[kPushThreads], s_qe[kPushThreads];
     __shared__ FT s_qw[kPushThreads];
+    __shared__ double s_dang;    // fluid drained from dangling nodes (1/N completion)
 
     FT *__restrict__ F = static_cast<FT *>(desc->F);
     double *__restrict__ H = desc->H;
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_dang = 0.0;   // ordered before any add by the loop's first barrier
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max, warp_max = desc->warp_max;
@@ -463,7 +483,9 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
             b = __ldcs(rp + i);
             e = __ldcs(rp + i + 1);
             const FT f = atomic_exch_keep(F + i, FT(0), keep);
-            __stcs(H + i, __ldcs(H + i) + static_cast<double>(f));   // i appears once per frontier
+            const double fd = static_cast<double>(f);
+            __stcs(H + i, __ldcs(H + i) + fd);   // i appears once per frontier
+            if (e == b && desc->dangling) atomicAdd(&s_dang, fd);   // 1/N completion
             w = f * __ldcs(scale + i);
             my_nodes += 1;
             my_edges += static_cast<unsigned long long>(e - b);
@@ -509,6 +531,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_async(const SolveDesc *__
         atomicAdd(&st->node_diff, my_nodes);
         atomicAdd(&st->edge_diff, my_edges);
     }
+    if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_acc, s_dang);
 }
 
 // Push of the asynchronous design, warp-level form: every warp claims
@@ -531,6 +554,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
     if (count == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FT *s_hot = reinterpret_cast<FT *>(smem_raw);
+    __shared__ double s_dang;    // fluid drained from dangling nodes (1/N completion)
+    if (threadIdx.x == 0) s_dang = 0.0;
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
     __syncthreads();
     FT *__restrict__ F = static_cast<FT *>(desc->F);
@@ -567,6 +592,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
                 w = f * __ldcs(scale + i);
                 my_nodes += 1;
                 my_edges += static_cast<unsigned long long>(e - b);
+                if (e == b && desc->dangling) atomicAdd(&s_dang, static_cast<double>(f));   // 1/N completion
             }
             const int deg = e - b;
             if (deg <= thread_max) {
@@ -595,6 +621,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
         atomicAdd(&st->node_diff, my_nodes);
         atomicAdd(&st->edge_diff, my_edges);
     }
+    if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_acc, s_dang);
 }
 
 // One threshold level in one launch (propagation 5): every CTA walks its
@@ -1350,6 +1377,12 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (o->propagation < 0 || o->propagation > 5) { set_error("di_solve: propagation = %d outside [0, 5]", o->propagation); return DI_EINVAL; }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
+    if (o->dangling < 0 || o->dangling > 1) { set_error("di_solve: dangling = %d outside [0, 1]", o->dangling); return DI_EINVAL; }
+    if (o->dangling == 1 && ((o->propagation != 3 && o->propagation != 4) || o->exact_residual == 1)) {
+        set_error("di_solve: the 1/N dangling completion needs propagation 3 or 4 and exact_residual 0 or 2 "
+                  "(got %d, %d)", o->propagation, o->exact_residual);
+        return DI_EINVAL;
+    }
     if (o->selection == 1 && o->propagation != 3 && o->propagation != 4) {
         set_error("di_solve: the weighted selection needs propagation 3 or 4 (got %d)", o->propagation);
         return DI_EINVAL;
@@ -1471,6 +1504,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.thread_max = g->tune.thread_max_deg;
     dh.warp_max = g->tune.warp_max_deg;
     dh.iw = o.selection == 1 ? (fp64 ? (const void *)g->iw64 : (const void *)g->iw32) : nullptr;
+    dh.dangling = o.dangling;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));

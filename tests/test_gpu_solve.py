@@ -568,3 +568,93 @@ def test_weighted_selection_needs_a_selection_kernel(web10k):
     with pytest.raises(di.DiError):
         di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(selection=2))
     g.close()
+
+
+# ---------------------------------------------------------------- 1/N completion of dangling columns (Sec. 2.2)
+
+@pytest.fixture(scope="module")
+def web10k_completed():
+    rp, col = gg.generate(gg.SMALL_10K)
+    b = gg.uniform_b(gg.SMALL_10K.n, D)
+    r = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum(), dangling=True)
+    assert r.status == 0
+    return rp, col, b, r.H
+
+
+def check_stop_completed(rp, col, b, h, st, tol):
+    """As check_stop, for the completed P.  Every F_k then holds the same term
+    (d/N) sum_dangling H_j, so the rounding of that one sum (recursive
+    summation: at most n_dangling eps sum|H_j| on each side) shifts all N
+    residual elements alike and adds up coherently in |F|_1: the allowance
+    grows by 2 d n_dangling eps sum_dangling |H_j|."""
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h, dangling=True)
+    eps = np.finfo(np.float64).eps
+    dang = np.diff(rp) == 0
+    floor = 64 * eps * (np.abs(b).sum() + 2 * np.abs(h).sum())
+    floor += 2 * D * dang.sum() * eps * np.abs(h[dang]).sum()
+    assert r_cpu <= tol * (1 + 1e-9) + floor
+    assert abs(st.resid_l1 - r_cpu) <= 1e-9 * max(r_cpu, tol) + floor
+    return f_cpu
+
+
+@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
+    rp, col, b, x = web10k_completed
+    assert np.sum(np.diff(rp) == 0) > 500          # about 10% of the nodes are dangling
+    tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, dangling=1)
+    assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+    f_cpu = check_stop_completed(rp, col, b, h, st, tol)
+    np.testing.assert_allclose(f, f_cpu, atol=1e-15 + 1e-9 * tol)
+    # the completed columns are stochastic: 1'H is within the error bound of 1'X = 1
+    assert abs(h.sum() - 1.0) <= st.resid_l1 / (1 - D) * 1.001 + 1e-12
+
+
+def test_dangling_completion_personalised_and_warm(web10k_completed):
+    rp, col, b, x = web10k_completed
+    # a personalised right-hand side (sparse early levels)
+    bp = gg.personalised_b(len(b), 1234)
+    xp = od.d_iteration(rp, col, bp, D, tol=1e-14 * bp.sum(), dangling=True).H
+    h, st, _, _ = solve(rp, col, bp, 1e-8 * bp.sum(), propagation=4, dangling=1)
+    assert np.abs(h - xp).sum() <= 1e-6 * np.abs(xp).sum()
+    check_stop_completed(rp, col, bp, h, st, 1e-8 * bp.sum())
+    # a warm start: F0 = B + P H0 - H0 with the completed P (small enough that
+    # the start is kept: |F0|_1 <= |B|_1)
+    rng = np.random.default_rng(44)
+    h0 = x * (1 + 0.05 * rng.standard_normal(len(x)))
+    h, st, _, _ = solve(rp, col, b, 1e-8 * b.sum(), h0=h0, propagation=3, dangling=1)
+    _, f0 = od.residual(rp, col, b, D, h0, dangling=True)
+    assert f0 < b.sum() and st.warm_used == 1
+    assert st.f0_l1 == pytest.approx(f0, rel=1e-12)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop_completed(rp, col, b, h, st, 1e-8 * b.sum())
+
+
+def test_dangling_completion_on_two_source_blocks(web5m):
+    # more than 2^22 nodes: the dangling sum of the exact residual spans both blocks
+    rp, col, b = web5m
+    tol = 1e-8 * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, propagation=4, dangling=1)
+    assert st.recomputes >= 1
+    f_cpu = check_stop_completed(rp, col, b, h, st, tol)
+    np.testing.assert_allclose(f, f_cpu, atol=1e-15 + 1e-9 * tol)
+    assert abs(h.sum() - 1.0) <= st.resid_l1 / (1 - D) * 1.001 + 1e-9
+
+
+def test_dangling_completion_rejects_unsupported_modes():
+    rp, col = csr_from_edges(3, [(0, 1), (1, 2)])
+    g = di.Graph.create(rp, col)
+    B = dev(np.ones(3))
+    H = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for opt in (dict(dangling=2), dict(dangling=1, propagation=5), dict(dangling=1, propagation=0),
+                dict(dangling=1, exact_residual=1)):
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, B, D, 1e-8, H, None, di.opts_default(**opt))
+        assert e.value.status == di.DI_EINVAL
+    batch = di.Batch([g], [1])
+    with pytest.raises(di.DiError) as e:
+        di.di_solve_batched(batch, [B], D, 1e-8, [H], di.opts_default(dangling=1))
+    assert e.value.status == di.DI_EINVAL
+    batch.close()
+    g.close()
