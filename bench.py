@@ -428,7 +428,9 @@ def run_native(args, world, rank, local):
         alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
         achieved = alg_bytes / tpush / 1e9
         peak, peak_src = measured_hbm_peak()
-        traffic = level_traffic(args.workload, prec, opts.propagation)
+        # the recorded captures ran with the default selection and zero dangling columns
+        traffic = (level_traffic(args.workload, prec, opts.propagation)
+                   if not (opts.selection or opts.dangling) else None)
         extras["roofline"] = {"bound": "hbm", "kernel": f"k_level<{'double' if args.fp64 else 'float'}> (scan + push)",
                               "achieved": achieved, "peak": peak, "unit": "GB/s",
                               "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
