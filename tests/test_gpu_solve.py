@@ -658,3 +658,27 @@ def test_dangling_completion_rejects_unsupported_modes():
     assert e.value.status == di.DI_EINVAL
     batch.close()
     g.close()
+
+
+@pytest.mark.parametrize("case", ["ragged", "single", "tiny_mixed"])
+def test_dangling_completion_edge_cases(case):
+    # the uniform add skips the zero padding of the fluid past N (N not a
+    # multiple of 4), a lone dangling node (X = B / (1 - d)), and a graph
+    # where most nodes are dangling
+    if case == "ragged":
+        rp, col = gg.generate(gg.GraphSpec(n=10007, mean_deg=7.0, seed=31))
+        b = gg.uniform_b(10007, D)
+    elif case == "single":
+        rp, col = csr_from_edges(1, [])
+        b = np.array([0.15])
+    else:
+        rp, col = csr_from_edges(7, [(0, 1), (1, 2), (2, 0), (3, 0)])
+        b = np.array([0.01, 0.02, 0.0, 0.05, 0.03, 0.0, 0.04])
+    x = od.d_iteration(rp, col, b, D, tol=1e-15 * b.sum(), dangling=True).H
+    if case == "single":
+        assert x[0] == pytest.approx(0.15 / (1 - D), rel=1e-13)
+    for fp64, rel in ((False, 1e-6), (True, 1e-11)):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=3, dangling=1)
+        assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
+        check_stop_completed(rp, col, b, h, st, tol)
