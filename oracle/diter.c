@@ -43,6 +43,7 @@
 #include <stdint.h>
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 typedef struct {
     int64_t levels;           /* non-empty sweeps performed */
@@ -140,5 +141,155 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
     }
     s.threshold = T;
     if (st) *st = s;
+    return status;
+}
+
+/*
+ * K-PID asynchronous D-iteration (Secs. 2.3-2.6), emulated sequentially.
+ *
+ * The nodes are split into K ranges Omega_k = [bounds[k], bounds[k+1]) (a
+ * uniform or cost-balanced partition, Sec. 2.3), each owned by one PID with
+ * its own threshold T_k.  Readings where the paper is silent (each is listed
+ * in the design notes):
+ *   - the PIDs run in lock-step rounds; in a round every PID makes one cyclic
+ *     threshold sweep over its own nodes (the time-stepped model of Sec. 2.4
+ *     with equal speeds, at the granularity of one sweep);
+ *   - a sweep diffuses a node to its children inside Omega_k only (the
+ *     algorithm (*) of Sec. 2.5); the fluid owed to external children is
+ *     carried implicitly by the increment H - H_old since the PID's last
+ *     transmission;
+ *   - after the sweeps, PID k transmits when s_k > r_k / K (Eq. send), with
+ *     r_k = sum of |F_i| over Omega_k and s_k = sum over the external edges
+ *     j <- i of |p_ji (H_i - H_old_i)|: it adds p_ji (H_i - H_old_i) to F_j
+ *     for every external child j and sets H_old = H on Omega_k.  Every PID
+ *     decides on the state after the sweeps, then all transmissions land;
+ *   - reception (Sec. 2.6): a PID that received fluid rescales its threshold
+ *     by (r_k + received) / r_k, or restarts from max |F_i| over Omega_k when
+ *     it held no fluid (the factor the paper prints is garbled);
+ *   - T_k starts at max |F_i| over Omega_k and a sweep that would find nothing
+ *     is skipped by dividing T_k by alpha first (as in the one-PID oracle); a
+ *     PID without fluid idles;
+ *   - the stop test is the exact residual |B + P H - H|_1 <= tol after each
+ *     round: it includes the fluid still waiting for transmission.
+ * Costs (Sec. 2.4): ops[k] counts PID k's elementary diffusions, one per local
+ * child in its sweeps and one per external edge it transmits.
+ * Returns 0 on convergence, 4 when max_rounds was reached, 1 on invalid
+ * arguments, 2 when a scratch allocation failed.
+ */
+int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *B, double d,
+                double tol, double alpha, int K, const int64_t *bounds, int64_t max_rounds,
+                double *H, double *F, double *H_old, int64_t *ops, int64_t *sends,
+                int64_t *rounds_out, double *resid_out, double *trace, int64_t trace_cap) {
+    if (n < 0 || K < 1 || !(alpha > 1.0) || !(tol >= 0.0) || max_rounds < 0) return 1;
+    if (bounds[0] != 0 || bounds[K] != n) return 1;
+    for (int k = 0; k < K; ++k)
+        if (bounds[k + 1] < bounds[k]) return 1;
+    int32_t *part = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    double *scratch = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *T = (double *)malloc((size_t)K * sizeof(double));
+    double *r = (double *)malloc((size_t)K * sizeof(double));
+    double *s = (double *)malloc((size_t)K * sizeof(double));
+    double *recv = (double *)malloc((size_t)K * sizeof(double));
+    int *send = (int *)malloc((size_t)K * sizeof(int));
+    if (!part || !scratch || !T || !r || !s || !recv || !send) {
+        free(part); free(scratch); free(T); free(r); free(s); free(recv); free(send);
+        return 2;
+    }
+    for (int k = 0; k < K; ++k)
+        for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) part[i] = k;
+    for (int64_t i = 0; i < n; ++i) { F[i] = B[i]; H[i] = 0.0; H_old[i] = 0.0; }
+    for (int k = 0; k < K; ++k) {
+        ops[k] = 0;
+        sends[k] = 0;
+        T[k] = 0.0;
+        for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i)
+            if (fabs(F[i]) > T[k]) T[k] = fabs(F[i]);
+    }
+    int status = 4;
+    int64_t round = 0;
+    double resid = 0.0;
+    for (;;) {
+        resid = oracle_residual(n, row_ptr, col, B, d, H, scratch, 0);
+        if (resid <= tol) { status = 0; break; }
+        if (round >= max_rounds) { status = 4; break; }
+        /* every PID sweeps its own nodes, diffusing to local children only */
+        for (int k = 0; k < K; ++k) {
+            double mx = 0.0;
+            for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i)
+                if (fabs(F[i]) > mx) mx = fabs(F[i]);
+            if (mx == 0.0) continue;                    /* idle */
+            while (T[k] > mx) T[k] /= alpha;
+            for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) {
+                double sent = F[i];
+                if (fabs(sent) < T[k] || sent == 0.0) continue;
+                F[i] = 0.0;
+                H[i] += sent;
+                int64_t deg = row_ptr[i + 1] - row_ptr[i];
+                if (deg == 0) continue;
+                double p = d / (double)deg;
+                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                    if (part[col[e]] != k) continue;    /* external: left in H - H_old */
+                    F[col[e]] += sent * p;
+                    ops[k] += 1;
+                }
+            }
+            T[k] /= alpha;
+        }
+        /* transmissions: decided on the state after the sweeps (Eq. send) */
+        for (int k = 0; k < K; ++k) {
+            r[k] = 0.0;
+            s[k] = 0.0;
+            recv[k] = 0.0;
+            for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) {
+                r[k] += fabs(F[i]);
+                double dh = H[i] - H_old[i];
+                int64_t deg = row_ptr[i + 1] - row_ptr[i];
+                if (dh == 0.0 || deg == 0) continue;
+                double p = d / (double)deg;
+                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                    if (part[col[e]] != k) s[k] += fabs(p * dh);
+            }
+            send[k] = s[k] > 0.0 && s[k] > r[k] / (double)K;
+        }
+        for (int k = 0; k < K; ++k) {
+            if (!send[k]) continue;
+            sends[k] += 1;
+            for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) {
+                double dh = H[i] - H_old[i];
+                int64_t deg = row_ptr[i + 1] - row_ptr[i];
+                H_old[i] = H[i];
+                if (dh == 0.0 || deg == 0) continue;
+                double p = d / (double)deg;
+                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                    int32_t j = col[e];
+                    if (part[j] == k) continue;
+                    F[j] += p * dh;
+                    recv[part[j]] += fabs(p * dh);
+                    ops[k] += 1;
+                }
+            }
+        }
+        /* reception (Sec. 2.6): rescale the threshold of every receiver */
+        for (int k = 0; k < K; ++k) {
+            if (recv[k] == 0.0) continue;
+            if (r[k] > 0.0) {
+                T[k] *= (r[k] + recv[k]) / r[k];
+            } else {
+                T[k] = 0.0;
+                for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i)
+                    if (fabs(F[i]) > T[k]) T[k] = fabs(F[i]);
+            }
+        }
+        if (trace && round < trace_cap)
+            for (int k = 0; k < K; ++k) {
+                double rk = 0.0;
+                for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) rk += fabs(F[i]);
+                trace[round * K + k] = rk;
+            }
+        round += 1;
+    }
+    *rounds_out = round;
+    *resid_out = resid;
+    free(part); free(scratch); free(T); free(r); free(s); free(recv); free(send);
     return status;
 }
