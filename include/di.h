@@ -253,6 +253,29 @@ DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double 
                                      double *F, double *r_l1, void *stream);
 
 /*
+ * K-PID asynchronous D-iteration (Secs. 2.3-2.6) on one GPU: the nodes are
+ * split into K contiguous ranges (kind 0: uniform, w_k = floor(k N / K);
+ * kind 1: cost balanced, each range holding about L / K out-edges, Sec. 2.3).
+ * The PID of range k keeps its own threshold T_k and diffuses its nodes to
+ * their children inside the range only (Sec. 2.5, algorithm (*)); the fluid
+ * owed to other ranges is P (H - H_old) restricted to external children and
+ * is transmitted once its amount s_k exceeds r_k / K (Eq. send); a range that
+ * receives fluid scales T_k by (r_k + received) / r_k (Sec. 2.6).  Every
+ * round, all PIDs make one threshold level in the same launches; the stop is
+ * decided on the exact FP64 residual, which includes the fluid still owed.
+ * B, H (out), F (out, may be NULL) are device vectors of n doubles as in
+ * di_solve.  Supports FP32 fluid, a cold start, the plain selection and zero
+ * dangling columns; opts->alpha, max_levels, recompute_drop and stream apply
+ * (NULL opts = defaults).  pid_ops / pid_sends (host, K entries, may be
+ * NULL) receive each PID's elementary diffusions (local children plus
+ * transmitted external edges) and its number of transmissions.  1 <= K <= 64.
+ * Synchronous; the level loop is host-driven (one synchronisation per round).
+ */
+DI_API di_status di_solve_partitioned(di_graph *g, const double *B, double d, double tol, double *H,
+                                      double *F, const di_opts *opts, int32_t K, int32_t kind,
+                                      int64_t *pid_ops, int64_t *pid_sends, di_stats *stats);
+
+/*
  * Batched solves (many right-hand sides of many graphs in one level loop).
  * Work item t is right-hand side r of graph g, numbered graph-major: the
  * items of graphs[0] first (r = 0 .. nrhs[0]-1), then those of graphs[1] ...

@@ -38,6 +38,7 @@ CU_SOURCES = [
     "batch.cu",
     "warmstart.cu",
     "tune.cu",
+    "partition.cu",
 ]
 
 

@@ -80,6 +80,8 @@ SIGNATURES = {
     "di_frontier": (c_int, [c_vp, c_vp, c_int, c_dbl, c_vp, ctypes.POINTER(c_i64),
                             ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
     "di_residual_noalloc": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(c_dbl), c_vp]),
+    "di_solve_partitioned": (c_int, [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts), c_i32, c_i32,
+                                     c_vp, c_vp, ctypes.POINTER(di_stats)]),
     "di_train_opts_default": (c_int, [ctypes.POINTER(di_train_opts)]),
     "di_model_create": (c_int, [ctypes.c_uint64, ctypes.POINTER(c_vp)]),
     "di_model_destroy": (None, [c_vp]),
@@ -238,6 +240,21 @@ def di_residual_noalloc(graph: Graph, B, d: float, H, F, stream=None) -> float:
     check(lib().di_residual_noalloc(graph.handle, _ptr(B), d, _ptr(H), _ptr(F), ctypes.byref(r),
                                     _stream(stream)))
     return r.value
+
+
+def di_solve_partitioned(graph: Graph, B, d: float, tol: float, H, K: int, kind: int = 0, F=None,
+                         opts: di_opts | None = None, allow=(DI_OK,)):
+    """K-PID asynchronous D-iteration (Secs. 2.3-2.6); kind 0 uniform, 1 cost-balanced
+    ranges.  Returns (status, di_stats, per-PID elementary diffusions, per-PID transmissions)."""
+    import numpy as np
+    st = di_stats()
+    ops = np.zeros(K, dtype=np.int64)
+    sends = np.zeros(K, dtype=np.int64)
+    rc = lib().di_solve_partitioned(graph.handle, _ptr(B), d, tol, _ptr(H), _ptr(F),
+                                    ctypes.byref(opts) if opts is not None else None, K, kind,
+                                    ops.ctypes.data, sends.ctypes.data, ctypes.byref(st))
+    check(rc, allow)
+    return rc, st, ops, sends
 
 
 class Batch:

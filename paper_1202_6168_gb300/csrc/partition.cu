@@ -1,0 +1,661 @@
+// partition.cu - the K-PID asynchronous D-iteration of Secs. 2.3-2.6 on one GPU.
+//
+// The nodes are split into K contiguous ranges Omega_k (uniform, or cost
+// balanced so that every range holds about L / K out-edges, Sec. 2.3).  The
+// PID of range k keeps its own threshold T_k and diffuses its nodes to their
+// children inside Omega_k only (the algorithm (*) of Sec. 2.5); the fluid it
+// owes to other ranges is carried by H - H_old and transmitted, as
+// P (H - H_old) restricted to external children, once the amount s_k exceeds
+// r_k / K (Eq. send).  A range that receives fluid rescales its threshold by
+// (r_k + received) / r_k (Sec. 2.6).  On one GPU every PID runs in the same
+// launches, one round (one threshold level of every range) at a time:
+//   k_pscan  - selection |F_i| >= T_k, per-range |F|_1, max and count; its
+//              last CTA runs the control of every range (threshold, the
+//              transmission decision) and the stop request;
+//   k_ppush  - drain f = atomicExch(F_i, 0), H_i += f, local children only;
+//              the fluid owed to other ranges accumulates into s_k;
+//   k_psend  - transmission of the ranges that decided to send; its last
+//              CTA rescales the thresholds of the receivers;
+//   exact residual (residual.cu) as the stop test and refinement: it
+//              contains the fluid still owed, so H_old is reset with it.
+// The level loop is host-driven (one stream synchronisation per round).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "di_internal.cuh"
+
+namespace di {
+namespace {
+
+constexpr int kMaxParts = 64;
+constexpr int kPThreads = 256;
+
+// Per-range state on the device.  Sums are cleared by the step that consumes them.
+struct PartState {
+    double T[kMaxParts];                 // threshold of the next selection
+    double r[kMaxParts];                 // |F|_1 over the range, from the selection
+    unsigned long long m[kMaxParts];     // max |F| (bits; non-negative doubles order like integers)
+    unsigned long long sel[kMaxParts];   // nodes selected
+    double s[kMaxParts];                 // fluid owed to other ranges since the last transmission
+    double rdec[kMaxParts];              // |F|_1 at the last transmission decision
+    double recv[kMaxParts];              // fluid received in this round's transmissions
+    unsigned long long ops[kMaxParts];   // elementary diffusions of the range's PID
+    unsigned long long sends[kMaxParts]; // transmissions of the range's PID
+    int send[kMaxParts];                 // this round: transmit
+    int any_send;
+    int K;
+    unsigned int scan_blocks, send_blocks, init_blocks;
+};
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b) {
+    return __longlong_as_double(static_cast<long long>(b));
+}
+__device__ __forceinline__ unsigned long long double_to_bits(double v) {
+    return static_cast<unsigned long long>(__double_as_longlong(v));
+}
+
+// Node range of CTA b: [b * span, min(n, (b + 1) * span)), span a multiple of
+// the block size; threads interleave inside it, so a thread meets few range
+// boundaries and flushes its per-range sums rarely.
+__device__ __forceinline__ int64_t cta_span(int64_t n) {
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    return (per + kPThreads - 1) / kPThreads * kPThreads;
+}
+
+// F = B (FP32 fluid), H = H_old = 0, |B|_1, and T_k = max |B_i| over Omega_k.
+__global__ void __launch_bounds__(kPThreads) k_pinit(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                     PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     double *__restrict__ H_old, int64_t n,
+                                                     double *__restrict__ part_sum) {
+    __shared__ unsigned long long s_m[kMaxParts];
+    const int K = ps->K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) s_m[k] = 0ull;
+    __syncthreads();
+    const double *__restrict__ B = desc->B;
+    double *__restrict__ H = desc->H;
+    float *__restrict__ F = static_cast<float *>(desc->F);
+    const int64_t span = cta_span(n), lo = (int64_t)blockIdx.x * span;
+    const int64_t hi = lo + span < n ? lo + span : n;
+    double sum = 0.0, mx = 0.0;
+    int cur = -1;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kPThreads) {
+        const int k = part_of[i];
+        if (k != cur) {
+            if (cur >= 0 && mx > 0.0) atomicMax(&s_m[cur], double_to_bits(mx));
+            cur = k;
+            mx = 0.0;
+        }
+        const double b = B[i];
+        F[i] = static_cast<float>(b);
+        H[i] = 0.0;
+        H_old[i] = 0.0;
+        sum += fabs(b);
+        mx = fmax(mx, fabs(b));
+    }
+    if (cur >= 0 && mx > 0.0) atomicMax(&s_m[cur], double_to_bits(mx));
+    double dummy = 0.0;
+    block_sum_max<kPThreads>(sum, dummy);
+    if (threadIdx.x == 0) part_sum[blockIdx.x] = sum;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (s_m[k]) atomicMax(&ps->m[k], s_m[k]);
+    if (!last_block(&ps->init_blocks)) return;
+    double ts = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) ts += part_sum[i];
+    block_sum_max<kPThreads>(ts, dummy);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        ps->T[k] = bits_to_double(ps->m[k]);   // T_k = max |F_i| over Omega_k (0: the range idles)
+        ps->m[k] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        st->b_l1 = ts;
+        st->f0_l1 = ts;
+        st->r_exact = ts;
+        if (!isfinite(ts)) st->done = 3;
+        else if (ts <= desc->tol) st->done = 1;
+    }
+}
+
+// Selection of every range against its own T_k, in two passes over the CTA's
+// node span (count, one atomic for the CTA's slice of the frontier, write);
+// per-range |F|_1, max and count.  The last CTA runs the control.
+__global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                     PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     int32_t *__restrict__ front, int64_t n) {
+    __shared__ float s_T[kMaxParts];
+    __shared__ double s_r[kMaxParts];
+    __shared__ unsigned long long s_m[kMaxParts], s_sel[kMaxParts];
+    __shared__ int s_warp[kPThreads / 32];
+    __shared__ int s_base;
+    const int K = ps->K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        s_T[k] = __double2float_ru(ps->T[k]);   // |F_i| >= T in FP32: T rounded up to a float
+        s_r[k] = 0.0;
+        s_m[k] = 0ull;
+        s_sel[k] = 0ull;
+    }
+    __syncthreads();
+    const float *__restrict__ F = static_cast<const float *>(desc->F);
+    const int64_t span = cta_span(n), lo = (int64_t)blockIdx.x * span;
+    const int64_t hi = lo + span < n ? lo + span : n;
+    // pass 1: sums and counts
+    double r = 0.0, mx = 0.0;
+    unsigned long long nsel = 0;
+    int cur = -1, mine = 0;
+    auto flush = [&]() {
+        if (cur < 0) return;
+        if (r != 0.0) atomicAdd(&s_r[cur], r);
+        if (mx > 0.0) atomicMax(&s_m[cur], double_to_bits(mx));
+        if (nsel) atomicAdd(&s_sel[cur], nsel);
+        r = 0.0;
+        mx = 0.0;
+        nsel = 0;
+    };
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kPThreads) {
+        const int k = part_of[i];
+        if (k != cur) {
+            flush();
+            cur = k;
+        }
+        const float a = fabsf(F[i]);
+        r += a;
+        mx = fmax(mx, static_cast<double>(a));
+        if (a >= s_T[k] && a > 0.f) {
+            ++nsel;
+            ++mine;
+        }
+    }
+    flush();
+    // exclusive prefix of the per-thread counts, one atomic for the CTA's slice
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kPThreads / 32; ++w) {
+            const int v = s_warp[w];
+            s_warp[w] = run;
+            run += v;
+        }
+        s_base = run ? atomicAdd(&st->nfront, run) : 0;
+    }
+    __syncthreads();
+    // pass 2: the same reads (from L2), write the selected ids
+    int pos = s_base + s_warp[warp] + incl - mine;
+    if (mine)
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kPThreads) {
+            const float a = fabsf(F[i]);
+            if (a >= s_T[part_of[i]] && a > 0.f) front[pos++] = static_cast<int32_t>(i);
+        }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (s_r[k] != 0.0) atomicAdd(&ps->r[k], s_r[k]);
+        if (s_m[k]) atomicMax(&ps->m[k], s_m[k]);
+        if (s_sel[k]) atomicAdd(&ps->sel[k], s_sel[k]);
+    }
+    if (!last_block(&ps->scan_blocks)) return;
+
+    // control of every range (one thread each), then of the solve
+    __shared__ double s_tot[kMaxParts];
+    __shared__ int s_snd[kMaxParts];
+    __shared__ int s_stop;
+    const double alpha = desc->alpha;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double rk = ps->r[k], mk = bits_to_double(ps->m[k]), sk = ps->s[k];
+        double T = ps->T[k];
+        if (ps->sel[k] > 0) {
+            T /= alpha;                                 // the range swept at T: next level T / alpha
+        } else if (mk > 0.0) {                          // empty sweep: first T / alpha^j <= max |F|
+            for (int guard = 0; T > mk && guard < 8192; ++guard) T /= alpha;
+        }
+        ps->T[k] = T;
+        s_snd[k] = sk > 0.0 && sk > rk / (double)K;     // Eq. send
+        ps->rdec[k] = rk;
+        s_tot[k] = rk + sk;
+        ps->r[k] = 0.0;
+        ps->m[k] = 0ull;
+        ps->sel[k] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        int any = 0;
+        for (int k = 0; k < K; ++k) {
+            total += s_tot[k];
+            any |= s_snd[k];
+        }
+        const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
+        const double tol = desc->tol, drop = desc->recompute_drop;
+        int done = 0, rec = 0, stop = 0, push = st->nfront;
+        if (!isfinite(total)) {
+            done = 3;
+        } else if (total * est <= tol) {                // stop request: confirm on the exact residual
+            rec = 1;
+            stop = 1;
+            st->confirming = 1;
+            st->r_confirm = total * est;
+            push = 0;
+            any = 0;
+        } else if (drop > 0.0 && total * est * drop <= st->r_exact) {
+            rec = 1;                                     // refinement of the FP32 fluid
+        }
+        if (push > 0) st->level += 1;
+        st->body_iters += 1;
+        if (!done && st->body_iters >= desc->max_body_iters) done = 2;
+        if (!done && st->level >= desc->max_levels && !rec) done = 2;
+        if (done) {
+            rec = 0;
+            push = 0;
+            any = 0;
+            st->done = done;
+        }
+        st->push_count = push;
+        st->do_recompute = rec;
+        st->nfront = 0;
+        st->tile_ctr = 0;
+        ps->any_send = any;
+        s_stop = stop || done;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) ps->send[k] = s_stop ? 0 : s_snd[k];
+}
+
+__device__ __forceinline__ int32_t push_target(const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node,
+                                               int64_t e) {
+    const int32_t c = pcol[e];
+    return c >= 0 ? c : hot_node[-1 - c];
+}
+
+// Drain of the frontier, one lane per node; a lane's row goes to its local
+// children, and rows longer than 32 edges are walked by the whole warp.
+// The fluid owed to other ranges, |w| per external child, accumulates in s_k.
+__global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                     PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ pcol,
+                                                     const int32_t *__restrict__ hot_node,
+                                                     const float *__restrict__ scale) {
+    const int count = st->push_count;
+    if (count == 0) return;
+    __shared__ double s_s[kMaxParts];
+    __shared__ unsigned long long s_ops[kMaxParts];
+    const int K = ps->K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        s_s[k] = 0.0;
+        s_ops[k] = 0ull;
+    }
+    __syncthreads();
+    float *__restrict__ F = static_cast<float *>(desc->F);
+    double *__restrict__ H = desc->H;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_nodes = 0, my_edges = 0;
+    for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
+        const int64_t idx = base + lane;
+        int32_t b = 0, e = 0;
+        int k = 0;
+        float w = 0.f;
+        if (idx < count) {
+            const int32_t i = front[idx];
+            k = part_of[i];
+            b = rp[i];
+            e = rp[i + 1];
+            const float f = atomicExch(F + i, 0.f);
+            H[i] += static_cast<double>(f);
+            w = f * scale[i];
+            my_nodes += 1;
+        }
+        const int deg = e - b;
+        if (deg <= 32) {
+            unsigned long long loc = 0, ext = 0;
+            for (int32_t q = b; q < e; ++q) {
+                const int32_t j = push_target(pcol, hot_node, q);
+                if (part_of[j] == k) {
+                    red_add(F + j, w);
+                    ++loc;
+                } else {
+                    ++ext;
+                }
+            }
+            if (loc) atomicAdd(&s_ops[k], loc);
+            if (ext) atomicAdd(&s_s[k], fabs(static_cast<double>(w)) * static_cast<double>(ext));
+            my_edges += loc;
+        }
+        unsigned big = __ballot_sync(0xffffffffu, deg > 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
+            const float mw = __shfl_sync(0xffffffffu, w, src);
+            const int mk = __shfl_sync(0xffffffffu, k, src);
+            unsigned long long loc = 0, ext = 0;
+            for (int32_t q = mb + lane; q < me; q += 32) {
+                const int32_t j = push_target(pcol, hot_node, q);
+                if (part_of[j] == mk) {
+                    red_add(F + j, mw);
+                    ++loc;
+                } else {
+                    ++ext;
+                }
+            }
+            loc = warp_sum(loc);
+            ext = warp_sum(ext);
+            if (lane == 0) {
+                if (loc) atomicAdd(&s_ops[mk], loc);
+                if (ext) atomicAdd(&s_s[mk], fabs(static_cast<double>(mw)) * static_cast<double>(ext));
+                my_edges += loc;
+            }
+        }
+    }
+    my_nodes = warp_sum(my_nodes);
+    my_edges = warp_sum(my_edges);
+    if (lane == 0 && my_nodes) {
+        atomicAdd(&st->node_diff, my_nodes);
+        atomicAdd(&st->edge_diff, my_edges);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (s_s[k] != 0.0) atomicAdd(&ps->s[k], s_s[k]);
+        if (s_ops[k]) atomicAdd(&ps->ops[k], s_ops[k]);
+    }
+}
+
+// Transmission of the ranges with send[k]: for every node i of such a range,
+// F_j += (d / outdeg_i)(H_i - H_old_i) for its children j outside the range,
+// and H_old_i = H_i.  The last CTA rescales the receivers' thresholds.
+__global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                                     PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
+                                                     const int32_t *__restrict__ hot_node,
+                                                     const double *__restrict__ scale64, double *__restrict__ H_old,
+                                                     int64_t n) {
+    if (!ps->any_send) return;
+    __shared__ int s_send[kMaxParts];
+    __shared__ double s_recv[kMaxParts];
+    __shared__ unsigned long long s_ops[kMaxParts];
+    const int K = ps->K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        s_send[k] = ps->send[k];
+        s_recv[k] = 0.0;
+        s_ops[k] = 0ull;
+    }
+    __syncthreads();
+    float *__restrict__ F = static_cast<float *>(desc->F);
+    const double *__restrict__ H = desc->H;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_edges = 0;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        int32_t b = 0, e = 0;
+        int k = 0;
+        float w = 0.f;
+        if (i < n) {
+            k = part_of[i];
+            if (s_send[k]) {
+                const double h = H[i], dh = h - H_old[i];
+                H_old[i] = h;
+                if (dh != 0.0) {
+                    w = static_cast<float>(scale64[i] * dh);
+                    b = rp[i];
+                    e = rp[i + 1];
+                }
+            }
+        }
+        const int deg = e - b;
+        if (deg <= 32) {
+            for (int32_t q = b; q < e; ++q) {
+                const int32_t j = push_target(pcol, hot_node, q);
+                const int kj = part_of[j];
+                if (kj == k) continue;
+                red_add(F + j, w);
+                atomicAdd(&s_recv[kj], fabs(static_cast<double>(w)));
+                atomicAdd(&s_ops[k], 1ull);
+                ++my_edges;
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, deg > 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
+            const float mw = __shfl_sync(0xffffffffu, w, src);
+            const int mk = __shfl_sync(0xffffffffu, k, src);
+            for (int32_t q = mb + lane; q < me; q += 32) {
+                const int32_t j = push_target(pcol, hot_node, q);
+                const int kj = part_of[j];
+                if (kj == mk) continue;
+                red_add(F + j, mw);
+                atomicAdd(&s_recv[kj], fabs(static_cast<double>(mw)));
+                atomicAdd(&s_ops[mk], 1ull);
+                ++my_edges;
+            }
+        }
+    }
+    my_edges = warp_sum(my_edges);
+    if (lane == 0 && my_edges) atomicAdd(&st->edge_diff, my_edges);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (s_recv[k] != 0.0) atomicAdd(&ps->recv[k], s_recv[k]);
+        if (s_ops[k]) atomicAdd(&ps->ops[k], s_ops[k]);
+    }
+    if (!last_block(&ps->send_blocks)) return;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (ps->send[k]) {
+            ps->sends[k] += 1;
+            ps->s[k] = 0.0;
+            ps->send[k] = 0;
+        }
+        const double rv = ps->recv[k];
+        if (rv > 0.0) {
+            // Sec. 2.6: scale T_k with the range's residual; a range that held
+            // no fluid restarts from its largest (the next selection lowers a
+            // T above every |F_i| to the first T / alpha^j below the max)
+            const double rd = ps->rdec[k];
+            ps->T[k] = rd > 0.0 ? ps->T[k] * (rd + rv) / rd : DBL_MAX;
+            ps->recv[k] = 0.0;
+        }
+    }
+    if (threadIdx.x == 0) ps->any_send = 0;
+}
+
+// Before an exact residual: it will hold every fluid still owed, so H_old = H
+// and the owed amounts are cleared.
+__global__ void __launch_bounds__(kPThreads) k_phold(const SolveDesc *__restrict__ desc,
+                                                     const SolveState *__restrict__ st, PartState *__restrict__ ps,
+                                                     double *__restrict__ H_old, int64_t n) {
+    if (!st->do_recompute) return;
+    const double *__restrict__ H = desc->H;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) H_old[i] = H[i];
+    if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < ps->K; k += blockDim.x) ps->s[k] = 0.0;
+}
+
+// Range boundaries (host): uniform w_k = floor(k N / K), or the first node at
+// which the out-edge prefix sum reaches k L / K (cost balanced).
+std::vector<int64_t> partition_bounds(const std::vector<int32_t> &rp, int64_t n, int K, int kind) {
+    std::vector<int64_t> b(K + 1, 0);
+    const int64_t L = rp[n];
+    for (int k = 1; k < K; ++k) {
+        if (kind == 0) {
+            b[k] = (int64_t)k * n / K;
+        } else {
+            const double target = (double)k * (double)L / (double)K;
+            int64_t lo = b[k - 1], hi = n;                  // first j >= b[k-1] with rp[j] >= target
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) / 2;
+                if ((double)rp[mid] >= target) hi = mid; else lo = mid + 1;
+            }
+            b[k] = lo;
+        }
+    }
+    b[K] = n;
+    return b;
+}
+
+}  // namespace
+}  // namespace di
+
+using namespace di;
+
+extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, double d, double tol, double *H,
+                                                double *F, const di_opts *opts, int32_t K, int32_t kind,
+                                                int64_t *pid_ops, int64_t *pid_sends, di_stats *stats) {
+    clear_error();
+    if (!g || !B || !H) { set_error("di_solve_partitioned: NULL graph, B or H"); return DI_EINVAL; }
+    di_opts o;
+    if (opts) o = *opts; else di_opts_default(&o);
+    if (!(d > 0.0 && d < 1.0)) { set_error("di_solve_partitioned: d = %g outside (0, 1)", d); return DI_EINVAL; }
+    if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("di_solve_partitioned: tol = %g must be finite and > 0", tol); return DI_EINVAL; }
+    if (!(o.alpha > 1.0) || !std::isfinite(o.alpha)) { set_error("di_solve_partitioned: alpha = %g must be > 1", o.alpha); return DI_EINVAL; }
+    if (K < 1 || K > kMaxParts) { set_error("di_solve_partitioned: K = %d outside [1, %d]", K, kMaxParts); return DI_EINVAL; }
+    if (kind < 0 || kind > 1) { set_error("di_solve_partitioned: kind = %d outside [0, 1]", kind); return DI_EINVAL; }
+    if (o.fluid_fp64 || o.warm_start || o.dangling || o.selection || o.max_levels < 0 ||
+        !(o.recompute_drop == 0.0 || (o.recompute_drop > 1.0 && std::isfinite(o.recompute_drop)))) {
+        set_error("di_solve_partitioned: supports FP32 fluid from a cold start with the plain selection and "
+                  "zero dangling columns; recompute_drop must be 0 or > 1");
+        return DI_EINVAL;
+    }
+    if (g->n > (int64_t)INT32_MAX) { set_error("di_solve_partitioned: too many nodes"); return DI_EINVAL; }
+    cudaStream_t s = as_stream(o.stream);
+    DI_CUDA_TRY(cudaSetDevice(g->device));
+    DI_TRY(ensure_workspace(g));
+    DI_TRY(ensure_scale(g, d, s));
+    g->res_form = 0;
+    DI_TRY(ensure_blocked_order(g, s));
+    Workspace &ws = g->ws;
+    const int64_t n = g->n;
+    if (!ws.F32) {
+        const int64_t npad = (n + 3) / 4 * 4;
+        DI_CUDA_TRY(cudaMalloc(&ws.F32, npad * sizeof(float)));
+        DI_CUDA_TRY(cudaMemsetAsync(ws.F32, 0, npad * sizeof(float), s));
+    }
+
+    // ranges and the node -> range table
+    std::vector<int32_t> rp(n + 1);
+    DI_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    const std::vector<int64_t> bounds = partition_bounds(rp, n, K, kind);
+    std::vector<uint8_t> part(n > 0 ? n : 1, 0);
+    for (int k = 0; k < K; ++k)
+        for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) part[i] = static_cast<uint8_t>(k);
+
+    struct Scratch {
+        uint8_t *part_of = nullptr;
+        double *H_old = nullptr;
+        PartState *ps = nullptr, *ps_h = nullptr;
+        ~Scratch() {
+            if (part_of) cudaFree(part_of);
+            if (H_old) cudaFree(H_old);
+            if (ps) cudaFree(ps);
+            if (ps_h) cudaFreeHost(ps_h);
+        }
+    } sc;
+    DI_CUDA_TRY(cudaMalloc(&sc.part_of, part.size()));
+    DI_CUDA_TRY(cudaMalloc(&sc.H_old, (n > 0 ? n : 1) * sizeof(double)));
+    DI_CUDA_TRY(cudaMalloc(&sc.ps, sizeof(PartState)));
+    DI_CUDA_TRY(cudaMallocHost(&sc.ps_h, sizeof(PartState)));
+    DI_CUDA_TRY(cudaMemcpyAsync(sc.part_of, part.data(), part.size(), cudaMemcpyHostToDevice, s));
+    std::memset(sc.ps_h, 0, sizeof(PartState));
+    sc.ps_h->K = K;
+    DI_CUDA_TRY(cudaMemcpyAsync(sc.ps, sc.ps_h, sizeof(PartState), cudaMemcpyHostToDevice, s));
+
+    // descriptor and state (the previous call on this graph has completed: every solve synchronises)
+    SolveDesc &dh = *ws.desc_h;
+    std::memset(&dh, 0, sizeof(dh));
+    dh.B = B;
+    dh.H = H;
+    dh.F_out = F;
+    dh.F = ws.F32;
+    dh.d = d;
+    dh.tol = tol;
+    dh.alpha = o.alpha;
+    dh.max_levels = o.max_levels;
+    dh.recompute_drop = o.recompute_drop;
+    dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
+    dh.n_nodes = n;
+    DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
+    DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
+    DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
+
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_ppush, kPThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    // k_pinit leaves one partial per CTA in part_sum, which holds as many as
+    // the largest grid of the workspace
+    const int64_t parts = std::max({g->grid_scan, g->grid_select, residual_partials(g), g->grid_push});
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)per_sm * g->num_sms, (n + kPThreads - 1) / kPThreads, parts}));
+    k_pinit<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, sc.H_old, n, ws.part_sum);
+    DI_CUDA_TRY(cudaGetLastError());
+    long long launches = 1;
+    for (;;) {
+        DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ws.st_h->done) break;
+        k_pscan<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, n);
+        k_ppush<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, g->rp, g->pcol, g->hot_node,
+                                           g->s32);
+        k_psend<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, g->rp, g->pcol, g->hot_node, g->s64,
+                                           sc.H_old, n);
+        k_phold<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.H_old, n);
+        launch_residual(g, 0, RES_LEVEL, s);
+        DI_CUDA_TRY(cudaGetLastError());
+        launches += 4 + residual_kernels(g);
+    }
+    SolveState st = *ws.st_h;
+    const bool refresh = st.done != 1 || (F != nullptr && st.recomputes == 0);
+    if (refresh) {
+        launch_residual(g, 0, RES_FINAL, s);
+        DI_CUDA_TRY(cudaGetLastError());
+        launches += residual_kernels(g);
+        DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        st.r_exact = ws.st_h->r_exact;
+    }
+    DI_CUDA_TRY(cudaMemcpyAsync(sc.ps_h, sc.ps, sizeof(PartState), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaEventRecord(ws.ev1, s));
+    DI_CUDA_TRY(cudaEventSynchronize(ws.ev1));
+    float ms = 0.f;
+    DI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
+    for (int k = 0; k < K; ++k) {
+        if (pid_ops) pid_ops[k] = (int64_t)sc.ps_h->ops[k];
+        if (pid_sends) pid_sends[k] = (int64_t)sc.ps_h->sends[k];
+    }
+    di_status rc = DI_OK;
+    if (st.done == 3 || !std::isfinite(st.r_exact)) {
+        rc = DI_ENONFINITE;
+        set_error("di_solve_partitioned: residual is not finite");
+    } else if (st.done != 1) {
+        rc = DI_ENOCONV;
+        set_error("di_solve_partitioned: level cap %d reached with |F|_1 = %g > tol = %g", o.max_levels, st.r_exact, tol);
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->levels = st.level;
+        stats->recomputes = st.recomputes;
+        stats->node_diffusions = (int64_t)st.node_diff;
+        stats->edge_diffusions = (int64_t)st.edge_diff;
+        stats->resid_l1 = st.r_exact;
+        stats->err_bound = st.r_exact / (1.0 - d);
+        stats->b_l1 = st.b_l1;
+        stats->f0_l1 = st.f0_l1;
+        stats->seconds = ms * 1e-3;
+        stats->status = rc;
+        stats->gpu_launches = launches;
+        stats->body_iterations = st.body_iters;
+    }
+    return rc;
+}
