@@ -45,6 +45,8 @@ WORKLOADS = {
     "web-4m": (gg.MID_4M, "web-like N=2^22, m=16, +-256 window, seed 0"),
     "warmstart": (None, "learned warm start: trained on seeded web-like graphs (N log-uniform in [1e5, 1e6], "
                         "m=10, seeds 1000..), evaluated on held-out N=3e6, m=10 graphs (seeds 2000..)"),
+    "kpid-1m": (gg.WEB_1M, "K-PID asynchronous D-iteration (Secs. 2.3-2.6) on the web-like N=1e6, m=10 graph, "
+                           "K = 1, 2, 4, 8, uniform and cost-balanced ranges"),
     "batch-64x4": (None, "64 web-like graphs, N log-uniform in [1e4, 2e6], m ~ U[6, 14], seeds 0..63; "
                          "4 personalised right-hand sides each (B = 0.15 e_s), 256 solves per step"),
 }
@@ -214,6 +216,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     spec, desc = WORKLOADS[args.workload]
+    if args.workload == "kpid-1m":
+        run_reference_kpid(args, desc)
+        return
     if spec is None:
         run_reference_multi(args, desc)
         return
@@ -240,6 +245,36 @@ def run_reference(args, world, rank):
                              "sample": f"{args.steps} full solves of the workload"},
             "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_kpid(args, desc):
+    """Reference arm of the K-PID workload: the oracle's emulation of 8 PIDs
+    (cost-balanced ranges) on a bounded sample, a web-like graph of N = 1e5."""
+    from oracle import kpid as ok
+    sp = gg.GraphSpec(n=100_000, mean_deg=10.0, window=64, seed=0)
+    rp, col = gg.generate(sp)
+    b = gg.uniform_b(sp.n, D)
+    tol = 1e-8 * b.sum()
+    L = int(len(col))
+    costs, secs = [], 0.0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = ok.kpid(rp, col, b, D, tol=tol, bounds=ok.cb_bounds(rp, 8))
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            secs += dt
+            costs.append(float(r.ops.max()) / L)
+    value = statistics.mean(costs)
+    line = {"impl": "reference", "metric": "max_pid_normalised_iterations", "value": value,
+            "unit": "iterations (ops/L)", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": "web-like N=1e5, m=10, K=8 cost-balanced ranges",
+                       "oracle": "sequential emulation of K PIDs, FP64, 1 core"},
+            "cpu_baseline": {"value": value, "unit": "iterations (ops/L)", "cores": 1, "kind": "oracle",
+                             "sample": "K=8 cost-balanced ranges on a web-like N=1e5 graph"},
+            "e2e": {"value": value, "unit": "iterations (ops/L)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -765,10 +800,64 @@ def run_warmstart(args, world, rank, local):
     model.close()
 
 
+def run_kpid(args, world, rank, local):
+    """K-PID asynchronous D-iteration: for every K and partition, the time to
+    tol and each PID's elementary diffusions normalised by L (the paper's
+    normalised iterations, Sec. 2.4), against the one-PID solve."""
+    import torch
+    from paper_1202_6168_gb300 import binding as di
+
+    torch.cuda.set_device(local)
+    spec, desc = WORKLOADS[args.workload]
+    rp, col = gg.generate(spec)
+    n, nnz = spec.n, int(len(col))
+    b = gg.uniform_b(n, D)
+    tol = 1e-8 * b.sum()
+    stream = torch.cuda.current_stream()
+    g = di.Graph.create(rp, col, stream=stream)
+    B = torch.from_numpy(b).cuda()
+    H = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    opts = di.opts_default(stream=stream.cuda_stream)
+    rows = []
+    for K, kind in ((1, 0), (2, 0), (2, 1), (4, 0), (4, 1), (8, 0), (8, 1)):
+        times = []
+        for rep in range(max(args.warmup, 1) + max(args.steps, 1)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st, ops, sends = di.di_solve_partitioned(g, B, D, tol, H, K, kind, None, opts)
+            dt = time.perf_counter() - t0
+            if rep >= max(args.warmup, 1):
+                times.append(dt)
+        rows.append({"K": K, "partition": ["uniform", "cost-balanced"][kind], "ms": 1e3 * statistics.median(times),
+                     "rounds": st.body_iterations, "recomputes": st.recomputes,
+                     "normalised_cost_per_pid": [float(v) / nnz for v in ops],
+                     "max_pid_cost": float(ops.max()) / nnz, "total_cost": float(ops.sum()) / nnz,
+                     "transmissions": [int(v) for v in sends], "resid": st.resid_l1,
+                     "gpu_launches": st.gpu_launches})
+    g.close()
+    one = rows[0]["max_pid_cost"]
+    best = min(rows[1:], key=lambda r: r["max_pid_cost"])
+    line = {"metric": "max_pid_normalised_iterations", "value": best["max_pid_cost"], "unit": "iterations (ops/L)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "nnz": nnz, "tol": "1e-8 |B|_1", "best": {"K": best["K"],
+                       "partition": best["partition"]}, "level_loop": "host-driven, one round per level",
+                       "timed": "wall clock around each di_solve_partitioned (synchronous)",
+                       "l2": "flushed (256 MiB write) before each timed solve"},
+            "one_pid_cost": one, "cost_split": best["max_pid_cost"] / one, "rows": rows,
+            "gpu_launches": best["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
-    if args.workload == "warmstart" and args.impl != "reference":
+    if args.workload == "kpid-1m" and args.impl != "reference":
+        if rank == 0:
+            run_kpid(args, world, rank, local)
+    elif args.workload == "warmstart" and args.impl != "reference":
         if rank == 0:
             run_warmstart(args, world, rank, local)
     elif args.workload == "batch-64x4" and args.impl != "reference":
