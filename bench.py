@@ -843,7 +843,7 @@ def run_kpid(args, world, rank, local):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "n": n, "nnz": nnz, "tol": "1e-8 |B|_1", "best": {"K": best["K"],
-                       "partition": best["partition"]}, "level_loop": "host-driven, one round per level",
+                       "partition": best["partition"]}, "level_loop": "CUDA graph (WHILE/IF nodes), one round per level",
                        "timed": "wall clock around each di_solve_partitioned (synchronous)",
                        "l2": "flushed (256 MiB write) before each timed solve"},
             "one_pid_cost": one, "cost_split": best["max_pid_cost"] / one, "rows": rows,

@@ -269,7 +269,7 @@ DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double 
  * (NULL opts = defaults).  pid_ops / pid_sends (host, K entries, may be
  * NULL) receive each PID's elementary diffusions (local children plus
  * transmitted external edges) and its number of transmissions.  1 <= K <= 64.
- * Synchronous; the level loop is host-driven (one synchronisation per round).
+ * Synchronous; the rounds run on the device in one CUDA graph (WHILE node).
  */
 DI_API di_status di_solve_partitioned(di_graph *g, const double *B, double d, double tol, double *H,
                                       double *F, const di_opts *opts, int32_t K, int32_t kind,

@@ -18,7 +18,9 @@
 //              CTA rescales the thresholds of the receivers;
 //   exact residual (residual.cu) as the stop test and refinement: it
 //              contains the fluid still owed, so H_old is reset with it.
-// The level loop is host-driven (one stream synchronisation per round).
+// The rounds run on the device: a CUDA graph holds a WHILE node around
+// [k_pscan -> k_ppush -> k_psend -> IF(k_phold -> exact residual)], and
+// k_pscan's last CTA sets both conditions.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -124,7 +126,18 @@ __global__ void __launch_bounds__(kPThreads) k_pinit(const SolveDesc *__restrict
 // per-range |F|_1, max and count.  The last CTA runs the control.
 __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                      PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
-                                                     int32_t *__restrict__ front, int64_t n) {
+                                                     int32_t *__restrict__ front, int64_t n,
+                                                     cudaGraphConditionalHandle h_while,
+                                                     cudaGraphConditionalHandle h_rec) {
+    if (st->done) {                                     // converged, capped or not finite: end the loop
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->push_count = 0;
+            ps->any_send = 0;
+            cudaGraphSetConditional(h_rec, 0);
+            cudaGraphSetConditional(h_while, 0);
+        }
+        return;
+    }
     __shared__ float s_T[kMaxParts];
     __shared__ double s_r[kMaxParts];
     __shared__ unsigned long long s_m[kMaxParts], s_sel[kMaxParts];
@@ -263,6 +276,8 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         st->tile_ctr = 0;
         ps->any_send = any;
         s_stop = stop || done;
+        cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
+        if (done) cudaGraphSetConditional(h_while, 0);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) ps->send[k] = s_stop ? 0 : s_snd[k];
@@ -281,16 +296,26 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
                                                      PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
                                                      const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
                                                      const int32_t *__restrict__ pcol,
-                                                     const int32_t *__restrict__ hot_node,
+                                                     const int32_t *__restrict__ hot_node, int n_hot,
                                                      const float *__restrict__ scale) {
     const int count = st->push_count;
     if (count == 0) return;
     __shared__ double s_s[kMaxParts];
     __shared__ unsigned long long s_ops[kMaxParts];
+    // targets of very high in-degree (hot slots, encoded -1 - slot in pcol)
+    // are accumulated per CTA in shared memory and flushed once, as in the
+    // main push: hot-node ranges, then the sums
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_hot = reinterpret_cast<float *>(smem_raw);
+    uint8_t *s_hot_part = reinterpret_cast<uint8_t *>(s_hot + n_hot);
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_s[k] = 0.0;
         s_ops[k] = 0ull;
+    }
+    for (int sl = threadIdx.x; sl < n_hot; sl += blockDim.x) {
+        s_hot[sl] = 0.f;
+        s_hot_part[sl] = part_of[hot_node[sl]];
     }
     __syncthreads();
     float *__restrict__ F = static_cast<float *>(desc->F);
@@ -318,9 +343,16 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
         if (deg <= 32) {
             unsigned long long loc = 0, ext = 0;
             for (int32_t q = b; q < e; ++q) {
-                const int32_t j = push_target(pcol, hot_node, q);
-                if (part_of[j] == k) {
-                    red_add(F + j, w);
+                const int32_t c = pcol[q];
+                if (c < 0) {
+                    if (s_hot_part[-1 - c] == k) {
+                        atomicAdd(&s_hot[-1 - c], w);
+                        ++loc;
+                    } else {
+                        ++ext;
+                    }
+                } else if (part_of[c] == k) {
+                    red_add(F + c, w);
                     ++loc;
                 } else {
                     ++ext;
@@ -339,9 +371,16 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
             const int mk = __shfl_sync(0xffffffffu, k, src);
             unsigned long long loc = 0, ext = 0;
             for (int32_t q = mb + lane; q < me; q += 32) {
-                const int32_t j = push_target(pcol, hot_node, q);
-                if (part_of[j] == mk) {
-                    red_add(F + j, mw);
+                const int32_t c = pcol[q];
+                if (c < 0) {
+                    if (s_hot_part[-1 - c] == mk) {
+                        atomicAdd(&s_hot[-1 - c], mw);
+                        ++loc;
+                    } else {
+                        ++ext;
+                    }
+                } else if (part_of[c] == mk) {
+                    red_add(F + c, mw);
                     ++loc;
                 } else {
                     ++ext;
@@ -363,6 +402,10 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
         atomicAdd(&st->edge_diff, my_edges);
     }
     __syncthreads();
+    for (int sl = threadIdx.x; sl < n_hot; sl += blockDim.x) {
+        const float v = s_hot[sl];
+        if (v != 0.f) red_add(F + hot_node[sl], v);
+    }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         if (s_s[k] != 0.0) atomicAdd(&ps->s[k], s_s[k]);
         if (s_ops[k]) atomicAdd(&ps->ops[k], s_ops[k]);
@@ -590,7 +633,8 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
 
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_ppush, kPThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_ppush, kPThreads,
+                                                      (size_t)g->n_hot * (sizeof(float) + 1)) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     // k_pinit leaves one partial per CTA in part_sum, which holds as many as
@@ -600,21 +644,66 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
         1, std::min<int64_t>({(int64_t)per_sm * g->num_sms, (n + kPThreads - 1) / kPThreads, parts}));
     k_pinit<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, sc.H_old, n, ws.part_sum);
     DI_CUDA_TRY(cudaGetLastError());
-    long long launches = 1;
-    for (;;) {
-        DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-        DI_CUDA_TRY(cudaStreamSynchronize(s));
-        if (ws.st_h->done) break;
-        k_pscan<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, n);
-        k_ppush<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, g->rp, g->pcol, g->hot_node,
-                                           g->s32);
-        k_psend<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, g->rp, g->pcol, g->hot_node, g->s64,
+    DI_CUDA_TRY(cudaGetLastError());
+
+    // the rounds as a CUDA graph: WHILE [scan -> push -> send -> IF(hold -> exact residual)]
+    struct GraphGuard {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cs = nullptr;
+        ~GraphGuard() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } gg;
+    DI_CUDA_TRY(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
+    DI_CUDA_TRY(cudaGraphCreate(&gg.graph, 0));
+    cudaGraphConditionalHandle h_while, h_if;
+    DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_while, gg.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_while;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    DI_CUDA_TRY(cudaGraphAddNode(&wnode, gg.graph, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_if, body, 0, 0));
+    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(gg.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    k_pscan<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, n, h_while, h_if);
+    const size_t hot_smem = (size_t)g->n_hot * (sizeof(float) + 1);
+    k_ppush<<<grid, kPThreads, hot_smem, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, g->rp, g->pcol,
+                                                  g->hot_node, g->n_hot, g->s32);
+    k_psend<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, g->rp, g->pcol, g->hot_node, g->s64,
                                            sc.H_old, n);
-        k_phold<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.H_old, n);
-        launch_residual(g, 0, RES_LEVEL, s);
-        DI_CUDA_TRY(cudaGetLastError());
-        launches += 4 + residual_kernels(g);
-    }
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t capg = nullptr, ended = nullptr;
+    DI_CUDA_TRY(cudaStreamGetCaptureInfo(gg.cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_if;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    DI_CUDA_TRY(cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip));
+    DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(gg.cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    DI_CUDA_TRY(cudaStreamEndCapture(gg.cs, &ended));
+    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(gg.cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+    k_phold<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.H_old, n);
+    launch_residual(g, 0, RES_LEVEL, gg.cs);
+    DI_CUDA_TRY(cudaStreamEndCapture(gg.cs, &ended));
+    DI_CUDA_TRY(cudaGetLastError());
+    DI_CUDA_TRY(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+    DI_CUDA_TRY(cudaGraphLaunch(gg.exec, s));
+    DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaStreamSynchronize(s));
+    // k_pinit; the three kernels of every round, and of the round that ends
+    // the loop; the IF body's when a recompute ran
+    long long launches = 1 + 3LL * (ws.st_h->body_iters + 1) + (1LL + residual_kernels(g)) * ws.st_h->recomputes;
     SolveState st = *ws.st_h;
     const bool refresh = st.done != 1 || (F != nullptr && st.recomputes == 0);
     if (refresh) {
