@@ -597,6 +597,23 @@ def check_stop_completed(rp, col, b, h, st, tol):
     return f_cpu
 
 
+def assert_completed_residual_close(f_gpu, f_cpu, rp, col, b, h):
+    """Elementwise agreement of two FP64 evaluations of F = B + P_c H - H with
+    the completed P_c: the recursive-summation bound of each in-row sum, as in
+    assert_residual_close, with P_c |H| in the scale, plus the rounding of the
+    one sum over the dangling nodes that every row shares (n_dangling eps
+    sum_dangling |H_j| on each side, times d / N)."""
+    eps = np.finfo(np.float64).eps
+    n = len(b)
+    dang = np.diff(rp) == 0
+    indeg = np.bincount(col, minlength=n)
+    shared = D / n * np.abs(h[dang]).sum()
+    scale = np.abs(b) + od.p_times(rp, col, D, np.abs(h)) + shared + np.abs(h)
+    bound = 2 * (indeg + 2) * eps * scale + 2 * dang.sum() * eps * shared
+    err = np.abs(f_gpu - f_cpu)
+    assert np.all(err <= bound + 1e-300), f"max excess {np.max(err - bound):.3e}"
+
+
 @pytest.mark.parametrize("prop", [3, 4])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
@@ -606,7 +623,7 @@ def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
     h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, dangling=1)
     assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
     f_cpu = check_stop_completed(rp, col, b, h, st, tol)
-    np.testing.assert_allclose(f, f_cpu, atol=1e-15 + 1e-9 * tol)
+    assert_completed_residual_close(f, f_cpu, rp, col, b, h)
     # the completed columns are stochastic: 1'H is within the error bound of 1'X = 1
     assert abs(h.sum() - 1.0) <= st.resid_l1 / (1 - D) * 1.001 + 1e-12
 
@@ -638,7 +655,7 @@ def test_dangling_completion_on_two_source_blocks(web5m):
     h, st, f, _ = solve(rp, col, b, tol, propagation=4, dangling=1)
     assert st.recomputes >= 1
     f_cpu = check_stop_completed(rp, col, b, h, st, tol)
-    np.testing.assert_allclose(f, f_cpu, atol=1e-15 + 1e-9 * tol)
+    assert_completed_residual_close(f, f_cpu, rp, col, b, h)
     assert abs(h.sum() - 1.0) <= st.resid_l1 / (1 - D) * 1.001 + 1e-9
 
 
