@@ -300,15 +300,20 @@ def run_reference_multi(args, desc):
                 secs += time.perf_counter() - t0
                 edges += r.edge_diffusions
                 done += 1
-    value = edges / secs
-    print(json.dumps({"impl": "reference", "metric": "edge_diffusions_per_s", "value": value,
-                      "unit": "edge_diffusions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+    if args.workload == "batch-64x4":
+        # the native line's metric: edge diffusions per second
+        metric, unit, value, hib = "edge_diffusions_per_s", "edge_diffusions/s", edges / secs, True
+    else:
+        # the native line's metric: time to tol of one held-out graph (the zero start)
+        metric, unit, value, hib = "time_to_tol_ms", "ms", 1e3 * secs / max(done, 1), False
+    print(json.dumps({"impl": "reference", "metric": metric, "value": value,
+                      "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": hib, "scaling": "weak",
                       "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": desc, "oracle": "sequential cyclic-threshold D-iteration, FP64, 1 core"},
-                      "cpu_baseline": {"value": value, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+                      "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                                        "sample": f"{done} solves: {sample}"},
-                      "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
+                      "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 

@@ -31,3 +31,10 @@ def test_reference_arm_prints_one_contract_line(workload):
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_warm_start_reference_uses_the_native_metric():
+    # the native warm-start line reports time to tol (lower is better); its
+    # reference arm must report the same metric and unit
+    d = reference_line("warmstart")
+    assert d["metric"] == "time_to_tol_ms" and d["unit"] == "ms" and d["higher_is_better"] is False
