@@ -179,7 +179,7 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
 int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *B, double d,
                 double tol, double alpha, int K, const int64_t *bounds, int64_t max_rounds,
                 double *H, double *F, double *H_old, int64_t *ops, int64_t *sends,
-                int64_t *rounds_out, double *resid_out, double *trace, int64_t trace_cap) {
+                int64_t *rounds_out, double *resid_out, double *trace, int64_t trace_cap, double *T_out) {
     if (n < 0 || K < 1 || !(alpha > 1.0) || !(tol >= 0.0) || max_rounds < 0) return 1;
     if (bounds[0] != 0 || bounds[K] != n) return 1;
     for (int k = 0; k < K; ++k)
@@ -290,6 +290,8 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
     }
     *rounds_out = round;
     *resid_out = resid;
+    if (T_out)
+        for (int k = 0; k < K; ++k) T_out[k] = T[k];
     free(part); free(scratch); free(T); free(r); free(s); free(recv); free(send);
     return status;
 }

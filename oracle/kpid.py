@@ -54,6 +54,7 @@ class KpidResult:
     sends: np.ndarray        # transmissions per PID
     resid_l1: float          # exact |B + P H - H|_1 at return
     trace: np.ndarray | None  # rounds x K: r_k after every round
+    T: np.ndarray            # every PID's threshold at return
 
 
 def _lib():
@@ -62,7 +63,7 @@ def _lib():
         vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         lib.oracle_kpid.restype = ci
         lib.oracle_kpid.argtypes = [i64, vp, vp, vp, dbl, dbl, dbl, ci, vp, i64, vp, vp, vp, vp, vp,
-                                    ctypes.POINTER(i64), ctypes.POINTER(dbl), vp, i64]
+                                    ctypes.POINTER(i64), ctypes.POINTER(dbl), vp, i64, vp]
         lib._kpid_ready = True
     return lib
 
@@ -82,13 +83,14 @@ def kpid(row_ptr, col, B, d: float = 0.85, tol: float = 1e-14, alpha: float = 1.
     rounds = ctypes.c_int64(0)
     resid = ctypes.c_double(0.0)
     tr = np.zeros((max_rounds if trace else 1, K))
+    T = np.zeros(K)
     status = _lib().oracle_kpid(n, rp.ctypes.data, cl.ctypes.data, B.ctypes.data, d, tol, alpha, K,
                                 bnd.ctypes.data, max_rounds, H.ctypes.data, F.ctypes.data, Ho.ctypes.data,
                                 ops.ctypes.data, sends.ctypes.data, ctypes.byref(rounds), ctypes.byref(resid),
-                                tr.ctypes.data if trace else None, max_rounds if trace else 0)
+                                tr.ctypes.data if trace else None, max_rounds if trace else 0, T.ctypes.data)
     if status == 1:
         raise ValueError("oracle rejected its arguments")
     if status == 2:
         raise MemoryError("oracle scratch allocation failed")
     return KpidResult(H=H, F=F, H_old=Ho, status=status, rounds=rounds.value, ops=ops, sends=sends,
-                      resid_l1=resid.value, trace=tr[:rounds.value].copy() if trace else None)
+                      resid_l1=resid.value, trace=tr[:rounds.value].copy() if trace else None, T=T)

@@ -129,3 +129,39 @@ def test_each_pid_costs_about_one_kth(K, bound):
         assert r.status == 0
         assert r.ops.max() <= bound * one.ops[0]
         assert np.abs(r.H - one.H).sum() <= 2 * tol / (1 - D)
+
+
+def test_hand_trace_idle_send_and_restart():
+    # 0 <-> 1, each node its own range, B = (1, 0).  Round 1: PID 0 diffuses
+    # node 0 (its child is external, so nothing moves locally), owes 0.85 and
+    # sends it (s_0 = 0.85 > r_0 / 2 = 0); PID 1 idles, receives 0.85 with no
+    # fluid of its own and restarts from T_1 = max |F| = 0.85.  Round 2 mirrors
+    # it: PID 1 diffuses node 1 and sends 0.85^2 back; PID 0 restarts at 0.7225.
+    rp, col = csr_from_edges(2, [(0, 1), (1, 0)])
+    b = np.array([1.0, 0.0])
+    r1 = ok.kpid(rp, col, b, D, tol=0.0, K=2, max_rounds=1)
+    np.testing.assert_array_equal(r1.H, [1.0, 0.0])
+    np.testing.assert_allclose(r1.F, [0.0, 0.85], rtol=1e-15)
+    np.testing.assert_array_equal(r1.H_old, [1.0, 0.0])
+    np.testing.assert_allclose(r1.T, [1.0 / 1.5, 0.85], rtol=1e-15)
+    assert list(r1.ops) == [1, 0] and list(r1.sends) == [1, 0]
+    r2 = ok.kpid(rp, col, b, D, tol=0.0, K=2, max_rounds=2)
+    np.testing.assert_allclose(r2.H, [1.0, 0.85], rtol=1e-15)
+    np.testing.assert_allclose(r2.F, [0.85 ** 2, 0.0], rtol=1e-15)
+    np.testing.assert_allclose(r2.T, [0.85 ** 2, 0.85 / 1.5], rtol=1e-15)
+    assert list(r2.ops) == [1, 1] and list(r2.sends) == [1, 1]
+
+
+def test_hand_trace_rescale_on_reception():
+    # ranges {0} and {1, 2}; edges 0 -> 2 (external), 1 -> 2 and 2 -> 1 (local);
+    # B = (1, 0.4, 0).  Round 1: PID 0 diffuses node 0 and sends 0.85 to node 2;
+    # PID 1 starts at T_1 = 0.4, diffuses node 1 (0.34 reaches node 2 locally,
+    # below T_1), ends the sweep at T_1 = 0.4 / 1.5 holding r_1 = 0.34, then
+    # receives 0.85: T_1 <- T_1 (r_1 + 0.85) / r_1 (Sec. 2.6 reading).
+    rp, col = csr_from_edges(3, [(0, 2), (1, 2), (2, 1)])
+    b = np.array([1.0, 0.4, 0.0])
+    r = ok.kpid(rp, col, b, D, tol=0.0, bounds=np.array([0, 1, 3]), max_rounds=1)
+    np.testing.assert_allclose(r.H, [1.0, 0.4, 0.0], rtol=1e-15)
+    np.testing.assert_allclose(r.F, [0.0, 0.0, 0.4 * 0.85 + 0.85], rtol=1e-15)
+    np.testing.assert_allclose(r.T, [1.0 / 1.5, (0.4 / 1.5) * (0.34 + 0.85) / 0.34], rtol=1e-14)
+    assert list(r.ops) == [1, 1] and list(r.sends) == [1, 0]
