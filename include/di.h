@@ -260,7 +260,8 @@ DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double 
  * their children inside the range only (Sec. 2.5, algorithm (*)); the fluid
  * owed to other ranges is P (H - H_old) restricted to external children and
  * is transmitted once its amount s_k exceeds r_k / K (Eq. send); a range that
- * receives fluid scales T_k by (r_k + received) / r_k (Sec. 2.6).  Every
+ * receives fluid scales T_k by (r_k + received) / r_k, or sets T_k to the
+ * received amount when it held no fluid (Sec. 2.6).  Every
  * round, all PIDs make one threshold level in the same launches; the stop is
  * decided on the exact FP64 residual, which includes the fluid still owed.
  * B, H (out), F (out, may be NULL) are device vectors of n doubles as in

@@ -164,8 +164,10 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
  *     for every external child j and sets H_old = H on Omega_k.  Every PID
  *     decides on the state after the sweeps, then all transmissions land;
  *   - reception (Sec. 2.6): a PID that received fluid rescales its threshold
- *     by (r_k + received) / r_k, or restarts from max |F_i| over Omega_k when
- *     it held no fluid (the factor the paper prints is garbled);
+ *     by (r_k + received) / r_k when r_k > 0 (the printed factor
+ *     min((r_k + received) / r_k, received) is garbled; its first term is
+ *     taken), and sets T_k = received when r_k = 0, as the paper states; the
+ *     empty-sweep rule below then lowers a T_k above every |F_i| of the range;
  *   - T_k starts at max |F_i| over Omega_k and a sweep that would find nothing
  *     is skipped by dividing T_k by alpha first (as in the one-PID oracle); a
  *     PID without fluid idles;
@@ -272,13 +274,8 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
         /* reception (Sec. 2.6): rescale the threshold of every receiver */
         for (int k = 0; k < K; ++k) {
             if (recv[k] == 0.0) continue;
-            if (r[k] > 0.0) {
-                T[k] *= (r[k] + recv[k]) / r[k];
-            } else {
-                T[k] = 0.0;
-                for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i)
-                    if (fabs(F[i]) > T[k]) T[k] = fabs(F[i]);
-            }
+            if (r[k] > 0.0) T[k] *= (r[k] + recv[k]) / r[k];
+            else T[k] = recv[k];
         }
         if (trace && round < trace_cap)
             for (int k = 0; k < K; ++k) {

@@ -266,8 +266,10 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
                 it.confirming = 1;
                 it.r_confirm = ts * est;
             } else if (nsel == 0) {
-                if (tm > 0.0)                  // empty level: first T / alpha^k <= max |F|
+                if (tm > 0.0) {                  // empty level: first T / alpha^k <= max |F|
                     for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+                    if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
+                }
             } else {
                 push = 1;
                 it.level += 1;

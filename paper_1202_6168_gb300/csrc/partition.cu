@@ -7,7 +7,8 @@
 // owes to other ranges is carried by H - H_old and transmitted, as
 // P (H - H_old) restricted to external children, once the amount s_k exceeds
 // r_k / K (Eq. send).  A range that receives fluid rescales its threshold by
-// (r_k + received) / r_k (Sec. 2.6).  On one GPU every PID runs in the same
+// (r_k + received) / r_k, or sets it to the received amount when it held no
+// fluid (Sec. 2.6).  On one GPU every PID runs in the same
 // launches, one round (one threshold level of every range) at a time:
 //   k_pscan  - selection |F_i| >= T_k, per-range |F|_1, max and count; its
 //              last CTA runs the control of every range (threshold, the
@@ -22,7 +23,6 @@
 // [k_pscan -> k_ppush -> k_psend -> IF(k_phold -> exact residual)], and
 // k_pscan's last CTA sets both conditions.
 #include <algorithm>
-#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
             T /= alpha;                                 // the range swept at T: next level T / alpha
         } else if (mk > 0.0) {                          // empty sweep: first T / alpha^j <= max |F|
             for (int guard = 0; T > mk && guard < 8192; ++guard) T /= alpha;
+            if (T > mk) T = mk;                         // alpha so close to 1 that the guard ran out
         }
         ps->T[k] = T;
         s_snd[k] = sk > 0.0 && sk > rk / (double)K;     // Eq. send
@@ -501,11 +502,12 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
         }
         const double rv = ps->recv[k];
         if (rv > 0.0) {
-            // Sec. 2.6: scale T_k with the range's residual; a range that held
-            // no fluid restarts from its largest (the next selection lowers a
-            // T above every |F_i| to the first T / alpha^j below the max)
+            // Sec. 2.6: scale T_k by (r_k + received) / r_k; a range that held
+            // no fluid takes T_k = received (the next selection's empty-sweep
+            // rule lowers a T above every |F_i| to the first T / alpha^j below
+            // the max)
             const double rd = ps->rdec[k];
-            ps->T[k] = rd > 0.0 ? ps->T[k] * (rd + rv) / rd : DBL_MAX;
+            ps->T[k] = rd > 0.0 ? ps->T[k] * (rd + rv) / rd : rv;
             ps->recv[k] = 0.0;
         }
     }

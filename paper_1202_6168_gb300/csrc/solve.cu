@@ -391,8 +391,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
         st->confirming = 1;
         st->r_confirm = ts * est;
     } else if (nf == 0) {
-        if (tm > 0.0)                       // empty level: next T is the first T / alpha^k <= max |F|
+        if (tm > 0.0) {                       // empty level: next T is the first T / alpha^k <= max |F|
             for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+            if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
+        }
     } else {
         push = nf;
         level += 1;
@@ -750,6 +752,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
             if (refine_due(desc, st, since, ts * est)) rec = 1;
         } else if (tm > 0.0) {
             for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+            if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
         }
         if (ts * est <= tol) {            // the fluid read before the pushes already meets tol
             rec = 1;
@@ -925,6 +928,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_select(
             // empty level: next T is the first T / alpha^k <= max |F| (tm > 0, so
             // at most ~3600 steps from any double down to the smallest denormal)
             for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+            if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
         }
         if (ts * est <= tol) {
             rec = 1;                      // stop request: confirm on the exact residual

@@ -135,8 +135,9 @@ def test_hand_trace_idle_send_and_restart():
     # 0 <-> 1, each node its own range, B = (1, 0).  Round 1: PID 0 diffuses
     # node 0 (its child is external, so nothing moves locally), owes 0.85 and
     # sends it (s_0 = 0.85 > r_0 / 2 = 0); PID 1 idles, receives 0.85 with no
-    # fluid of its own and restarts from T_1 = max |F| = 0.85.  Round 2 mirrors
-    # it: PID 1 diffuses node 1 and sends 0.85^2 back; PID 0 restarts at 0.7225.
+    # fluid of its own and takes T_1 = received = 0.85 (Sec. 2.6).  Round 2
+    # mirrors it: PID 1 diffuses node 1 and sends 0.85^2 back; PID 0 takes
+    # T_0 = 0.7225.
     rp, col = csr_from_edges(2, [(0, 1), (1, 0)])
     b = np.array([1.0, 0.0])
     r1 = ok.kpid(rp, col, b, D, tol=0.0, K=2, max_rounds=1)
@@ -165,3 +166,26 @@ def test_hand_trace_rescale_on_reception():
     np.testing.assert_allclose(r.F, [0.0, 0.0, 0.4 * 0.85 + 0.85], rtol=1e-15)
     np.testing.assert_allclose(r.T, [1.0 / 1.5, (0.4 / 1.5) * (0.34 + 0.85) / 0.34], rtol=1e-14)
     assert list(r.ops) == [1, 1] and list(r.sends) == [1, 0]
+
+
+def test_hand_trace_empty_receiver_takes_the_received_amount():
+    # ranges {0} and {1, 2}; edges 0 -> 1 and 0 -> 2 (both external); B = (1, 0, 0).
+    # Round 1: PID 0 diffuses node 0 and owes 0.425 to each of nodes 1 and 2
+    # (s_0 = 0.85 > r_0 / 2 = 0: it sends); PID 1 holds no fluid (r_1 = 0), so
+    # on reception T_1 is set to received = 0.85 (Sec. 2.6), not to the largest
+    # fluid of its range (0.425).  Round 2: PID 1 lowers T_1 past its empty
+    # sweeps, 0.85 -> 0.85/1.5 -> 0.85/1.5^2 <= 0.425, diffuses both nodes (no
+    # children) and ends at T_1 = 0.85 / 1.5^3.
+    rp, col = csr_from_edges(3, [(0, 1), (0, 2)])
+    b = np.array([1.0, 0.0, 0.0])
+    bounds = np.array([0, 1, 3])
+    r1 = ok.kpid(rp, col, b, D, tol=0.0, bounds=bounds, max_rounds=1)
+    np.testing.assert_array_equal(r1.H, [1.0, 0.0, 0.0])
+    np.testing.assert_allclose(r1.F, [0.0, 0.425, 0.425], rtol=1e-15)
+    np.testing.assert_allclose(r1.T, [1.0 / 1.5, 0.85], rtol=1e-15)
+    assert list(r1.ops) == [2, 0] and list(r1.sends) == [1, 0]
+    r2 = ok.kpid(rp, col, b, D, tol=0.0, bounds=bounds, max_rounds=2)
+    np.testing.assert_allclose(r2.H, [1.0, 0.425, 0.425], rtol=1e-15)
+    np.testing.assert_array_equal(r2.F, [0.0, 0.0, 0.0])
+    np.testing.assert_allclose(r2.T, [1.0 / 1.5, 0.85 / 1.5 ** 3], rtol=1e-15)
+    assert list(r2.ops) == [2, 0] and list(r2.sends) == [1, 0]
