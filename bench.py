@@ -75,8 +75,11 @@ def parse():
     p.add_argument("--no-l2-window", action="store_true", help="no L2 access-policy windows")
     p.add_argument("--propagation", type=int, default=None,
                    help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push, "
-                        "4 asynchronous push with warp-level tiles, 5 fused select + push")
+                        "4 asynchronous push with warp-level tiles, 5 fused select + push, "
+                        "6 node-ordered chunks with on-chip window and hot slots")
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
+    p.add_argument("--resweeps", type=int, default=None,
+                   help="propagations 3-6: re-selections at the same threshold before T <- T/alpha")
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
     p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
@@ -394,6 +397,8 @@ def run_native(args, world, rank, local):
         opts.propagation = args.propagation
     if args.push_ratio is not None:
         opts.push_ratio = args.push_ratio
+    if args.resweeps is not None:
+        opts.resweeps = args.resweeps
     if args.exact_residual is not None:
         opts.exact_residual = args.exact_residual
     if args.weighted:
@@ -451,7 +456,7 @@ def run_native(args, world, rank, local):
                                recompute_drop=opts.recompute_drop,
                                l2_window=opts.l2_window, propagation=opts.propagation,
                                push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
-                               selection=opts.selection, dangling=opts.dangling)
+                               selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps)
         te = tn = 0
         tpush = trec = tsel = 0.0
         npush = 0
@@ -533,8 +538,10 @@ def run_native(args, world, rank, local):
                            "propagation": ["auto: binned gather / push", "auto: flat gather / push",
                                            "push only", "asynchronous push",
                                            "asynchronous push, warp-level tiles",
-                                           "fused select + push, one launch per level"][opts.propagation],
-                           "push_ratio": opts.push_ratio,
+                                           "fused select + push, one launch per level",
+                                           "node-ordered chunks, on-chip window and hot slots, one launch "
+                                           "per level"][opts.propagation],
+                           "push_ratio": opts.push_ratio, "resweeps": opts.resweeps,
                            "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
                            "selection": ["|F_i| >= T", "|F_i| / ((in_i+1)(out_i+1)) >= T"][opts.selection],

@@ -90,7 +90,13 @@ typedef struct {
                               asynchronous push with warp-level tiles (each warp drains 32
                               frontier nodes at a time; no block-wide barrier); 5: the
                               level in one launch - each CTA selects nodes in its chunks
-                              of F and pushes them at once, with no frontier list */
+                              of F and pushes them at once, with no frontier list;
+                              6: the level in one launch over contiguous node chunks in node
+                              order (the cyclic sweep of Sec. 2.4 at GPU width): targets
+                              within a window around the chunk and targets of very high
+                              in-degree are added in shared memory and flushed with
+                              coalesced reductions, fluid sent to a later chunk is diffused
+                              in the same level; rows are pushed edge-parallel per warp */
     int push_ratio;        /* auto: a level is dense (gather) when its active edges times
                               push_ratio reach the edge count; default 8 */
     int exact_residual;    /* form of the exact FP64 residual B + P H - H: 1 gather over the
@@ -109,7 +115,7 @@ typedef struct {
                               stochastic.  The fluid a dangling node drains is spread
                               over all nodes as one uniform add in the next frontier
                               selection; the exact residual adds d/N sum_dangling H_j.
-                              Needs propagation 3 or 4 and exact_residual 0 or 2 */
+                              Needs propagation 3, 4 or 6 and exact_residual 0 or 2 */
     double recompute_drop; /* FP32 fluid: exact FP64 residual whenever the running |F|_1
                               has fallen by this factor since the last exact value, so
                               that the FP32 rounding of the pushes stays a fraction of
@@ -120,6 +126,11 @@ typedef struct {
                               kernel of this library waits on another CTA (cross-CTA
                               decisions use a last-block counter), so it is unused */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
+    int resweeps;          /* propagations 3-6: after a level's pass, select again at the
+                              same T up to this many times (nodes whose fluid crossed T
+                              while the level pushed - what the paper's sequential sweep
+                              meets later in the same sweep) before T <- T / alpha; a pass
+                              that selects nothing ends the level.  0 .. 8; default 0 */
 } di_opts;
 
 /* Statistics of one solve. */
@@ -145,6 +156,9 @@ typedef struct {
     int32_t reserved;
     double select_seconds;     /* timing mode, propagation 3/4: the frontier-selection part of
                                   level_seconds */
+    int64_t red_ops;           /* propagation 6: global L2 reduction sectors its level kernel
+                                  issued (a scattered red counts one, a coalesced flush one per
+                                  sector it touches); 0 for the other propagations */
 } di_stats;
 
 /* Library version string. */
@@ -156,7 +170,8 @@ DI_API const char *di_last_error(void);
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 0, recompute_drop 1024,
  * max_levels 100000, cold start (fallback on when warm), L2 window on,
  * timing off, propagation 3, push_ratio 8, exact_residual 0, selection 0,
- * dangling 0, spin_limit 2^26, stream NULL.  Returns DI_EINVAL if o is NULL. */
+ * dangling 0, spin_limit 2^26, stream NULL, resweeps 0.  Returns DI_EINVAL if
+ * o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
 /*
@@ -403,6 +418,29 @@ DI_API di_status di_warmstart_infer(di_model *m, di_graph *g, const double *B, d
 /* Model file: header, step, state, Adam moments (little-endian floats). */
 DI_API di_status di_warmstart_save(const di_model *m, const char *path);
 DI_API di_status di_warmstart_load(const char *path, di_model **out);
+
+/*
+ * Ceiling of the scattered memory operations of the push and the exact
+ * residual.  A threshold level (Sec. 2.4) adds p_ki F_i into the fluid of
+ * every child k (Eq. defF): one red.global.add per elementary diffusion at an
+ * irregular target of the fluid vector, which the library keeps in L2; the
+ * exact residual gathers one word per in-edge.  Their ceiling is the rate at
+ * which the GPU processes such single-word operations, not the HBM copy
+ * bandwidth.  This call measures it: ops operations by every thread of a
+ * full-occupancy grid over a zeroed device array of `slots` words (a power of
+ * two in [2^10, 2^30]; 2^24 floats is the fluid of a 2^24-node graph), after
+ * one warm-up launch; *ops_per_s (host) receives the best rate of three
+ * launches and *seconds (host, may be NULL) that launch's time.
+ *   mode 0: red.global.add.f32 at pseudo-random slots with the L2 evict-last
+ *           hint of the push;  1: the same in FP64;  2: 4-byte loads at
+ *           pseudo-random slots (gathers);  3: red.global.add.f32 at
+ *           consecutive slots per warp (coalesced, for contrast).
+ * The array is allocated and freed by the call (this is a measurement, not a
+ * solver step).  Synchronous on stream.  DI_EINVAL on a bad mode, size or
+ * count; DI_ENOMEM / DI_ECUDA on CUDA failures.
+ */
+DI_API di_status di_probe_l2(int mode, int64_t slots, int64_t ops, double *ops_per_s, double *seconds,
+                             void *stream);
 
 /*
  * Autotuning of the push shape.  The paper's cost model counts elementary

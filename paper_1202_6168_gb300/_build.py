@@ -39,6 +39,7 @@ CU_SOURCES = [
     "warmstart.cu",
     "tune.cu",
     "partition.cu",
+    "probe.cu",
 ]
 
 

@@ -26,7 +26,7 @@ class di_opts(ctypes.Structure):
                 ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
                 ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int), ("exact_residual", c_int), ("selection", c_int),
                 ("dangling", c_int), ("recompute_drop", c_dbl), ("spin_limit", ctypes.c_longlong),
-                ("stream", c_vp)]
+                ("stream", c_vp), ("resweeps", c_int)]
 
 
 class di_train_opts(ctypes.Structure):
@@ -49,7 +49,8 @@ class di_stats(ctypes.Structure):
                 ("b_l1", c_dbl), ("f0_l1", c_dbl), ("seconds", c_dbl), ("warm_used", c_i32),
                 ("status", c_i32), ("gpu_launches", c_i64), ("level_seconds", c_dbl),
                 ("recompute_seconds", c_dbl), ("level_launches", c_i32), ("recompute_launches", c_i32),
-                ("body_iterations", c_i32), ("reserved", c_i32), ("select_seconds", c_dbl)]
+                ("body_iterations", c_i32), ("reserved", c_i32), ("select_seconds", c_dbl),
+                ("red_ops", c_i64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -110,6 +111,7 @@ SIGNATURES = {
     "di_batch_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "di_solve_batched": (c_int, [c_vp, c_vp, c_dbl, c_vp, c_vp, ctypes.POINTER(di_opts),
                                  ctypes.POINTER(di_stats), ctypes.POINTER(di_stats)]),
+    "di_probe_l2": (c_int, [c_int, c_i64, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp]),
 }
 
 
@@ -452,3 +454,15 @@ def di_frontier(graph: Graph, F, fluid_fp64: bool, T: float, out_list, stream=No
 
 def version() -> str:
     return lib().di_version().decode()
+
+
+PROBE_MODES = {"red_f32": 0, "red_f64": 1, "gather_f32": 2, "red_f32_coalesced": 3}
+
+
+def probe_l2(mode: str, slots: int, ops: int, stream=None) -> tuple[float, float]:
+    """(operations per second, seconds of the best launch) of one scattered
+    operation kind over a device array of `slots` words (di_probe_l2)."""
+    rate, secs = c_dbl(), c_dbl()
+    check(lib().di_probe_l2(PROBE_MODES[mode], slots, ops, ctypes.byref(rate), ctypes.byref(secs),
+                            _stream(stream)))
+    return rate.value, secs.value

@@ -44,5 +44,6 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->dangling = 0;
     o->spin_limit = 1LL << 26;
     o->stream = nullptr;
+    o->resweeps = 0;
     return DI_OK;
 }

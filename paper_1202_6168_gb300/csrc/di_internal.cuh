@@ -45,6 +45,8 @@ constexpr int kResFine = 256;       // segment length of the exact residual's lo
 constexpr int kMaxHot = 2048;       // privatised hot targets (shared-memory slots)
 constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
 constexpr int kSrcBlockShift = 22;  // exact residual: sources in blocks of 2^22 nodes (32 MB of FP64 gathers)
+constexpr int kWinBins = 4;         // tiled level kernel: window radii 32 .. 256 (powers of two)
+constexpr int kMaxWinR = 32 << (kWinBins - 1);
 
 // ------------------------------------------------------------------ solver state
 
@@ -69,6 +71,7 @@ struct SolveDesc {
     int warp_max;         // ... up to this to one warp, longer ones to the CTA
     const void *iw;       // weighted selection: 1 / ((in + 1)(out + 1)) per node (FT), else NULL
     int dangling;         // 1: columns of dangling nodes completed by d/N (uniform)
+    int resweeps;         // propagations 3-6: extra selections at the same T before T <- T / alpha
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -106,6 +109,10 @@ struct SolveState {
     int pad;
     double dang_acc;            // fluid drained from dangling nodes since the last selection
     double dang_h;              // exact residual: sum of H over the dangling nodes
+    double dang_next;           // tiled level: dangling fluid drained in this level (for the next)
+    int phase;                  // selections made at the current T (0 = the level's first)
+    int pad2;
+    unsigned long long red_ops; // tiled level: global reduction sectors issued (scattered reds count one each)
 };
 
 enum ResMode : int {
@@ -192,6 +199,10 @@ struct di_graph {
     double scale_d = -1.0;
     float *s32 = nullptr;
     double *s64 = nullptr;
+    // tiled level kernel: radius of the shared-memory fluid window (-1 = not yet chosen),
+    // nodes per chunk and grid (per fluid precision)
+    int win_R = -1;
+    int tiled_chunk[2] = {0, 0}, grid_tiled[2] = {0, 0};
     // weighted selection (Sec. 2.4 score): 1 / ((in + 1)(out + 1)), built on first use
     float *iw32 = nullptr;
     double *iw64 = nullptr;
@@ -272,6 +283,61 @@ __device__ __forceinline__ void push_range(const int32_t *__restrict__ pcol, int
     }
 }
 
+// Threshold in the fluid's precision: a float threshold is rounded up, so
+// |F_i| >= T in FP32 never selects a node the FP64 comparison would not.
+__device__ __forceinline__ float thr_cast(double T, float) { return __double2float_ru(T); }
+__device__ __forceinline__ double thr_cast(double T, double) { return T; }
+
+// Exact recomputation as iterative refinement (FP32 fluid only): every
+// recompute_every levels, and whenever the running |F|_1 estimate r has
+// fallen by the factor recompute_drop since the last exact residual.  The
+// FP32 pushes round each target to 2^-24 of its value, so the drift they add
+// between two recomputations stays a small multiple of 2^-24 * recompute_drop
+// of the current residual.
+__device__ __forceinline__ bool refine_due(const SolveDesc *__restrict__ desc, const SolveState *__restrict__ st,
+                                           int since, double r) {
+    if (desc->fluid_fp64) return false;
+    const int R = desc->recompute_every;
+    const double drop = desc->recompute_drop;
+    return (R > 0 && since >= R) || (drop > 0.0 && r * drop <= st->r_exact);
+}
+
+// Threshold schedule after one selection pass (Sec. 2.4): a level starts at
+// T; after its pass the level is re-selected at the same T up to `resweeps`
+// times (nodes that crossed T while the level pushed - the fluid a
+// sequential sweep would have met later in the same sweep), then T <- T /
+// alpha.  A pass that selects nothing ends the level; an empty first pass
+// lowers T to the first T / alpha^k <= the largest fluid tm (an empty sweep
+// changes nothing).  level counts threshold levels that diffused, since the
+// levels since the last exact recomputation.
+__device__ __forceinline__ void lower_threshold(double &T, double alpha, double tm) {
+    if (tm > 0.0) {
+        for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
+        if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
+    }
+}
+__device__ __forceinline__ void threshold_step(int resweeps, bool pushed, double alpha, double tm, double &T,
+                                               int &phase, int &level, int &since) {
+    if (pushed) {
+        if (phase == 0) {
+            level += 1;
+            since += 1;
+        }
+        if (phase < resweeps) {
+            phase += 1;
+        } else {
+            phase = 0;
+            T /= alpha;
+        }
+    } else {
+        if (phase > 0) {
+            phase = 0;
+            T /= alpha;
+        }
+        lower_threshold(T, alpha, tm);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -328,6 +394,8 @@ di_status ensure_scale(di_graph *g, double d, cudaStream_t s);
 di_status ensure_blocked_order(di_graph *g, cudaStream_t s);
 // graph.cu: the selection weights 1 / ((in + 1)(out + 1)) (lazy)
 di_status ensure_selection_weights(di_graph *g, cudaStream_t s);
+// graph.cu: the window radius of the tiled level kernel (lazy)
+di_status ensure_window(di_graph *g, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
 int push_grid(const di_graph *g);

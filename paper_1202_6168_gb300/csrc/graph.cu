@@ -241,6 +241,33 @@ __global__ void k_outdeg(const int32_t *__restrict__ rp, int64_t n, int32_t *__r
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) deg[i] = rp[i + 1] - rp[i];
 }
 
+// Locality of the edges for the window of the tiled level kernel: counts of
+// the edges j -> k with |k - j| <= 32 << b for b = 0 .. kWinBins - 1 (hot
+// targets decoded through hot_node).  One thread per row, per-CTA counters.
+__global__ void k_win_hist(const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
+                           const int32_t *__restrict__ hot_node, int64_t n, unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long s_c[kWinBins];
+    for (int b = threadIdx.x; b < kWinBins; b += blockDim.x) s_c[b] = 0ull;
+    __syncthreads();
+    unsigned long long c[kWinBins] = {};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        for (int32_t e = rp[j]; e < rp[j + 1]; ++e) {
+            const int32_t code = pcol[e];
+            const int64_t k = code >= 0 ? code : hot_node[-1 - code];
+            const int64_t dist = k > j ? k - j : j - k;
+#pragma unroll
+            for (int b = 0; b < kWinBins; ++b) c[b] += dist <= (int64_t(32) << b) ? 1ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kWinBins; ++b)
+        if (c[b]) atomicAdd(&s_c[b], c[b]);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kWinBins; b += blockDim.x)
+        if (s_c[b]) atomicAdd(&out[b], s_c[b]);
+}
+
 // d / outdeg (0 for a dangling node) in FP64 and its FP32 rounding.
 __global__ void k_scale(const int32_t *__restrict__ rp, int64_t n, double d, double *__restrict__ s64,
                         float *__restrict__ s32) {
@@ -482,6 +509,36 @@ PullPlan pull_plan_of(const di_graph *g) {
     p.seg_row = g->pl_seg_row;
     p.seg_beg = g->pl_seg_beg;
     return p;
+}
+
+// Radius R of the fluid window of the tiled level kernel: the smallest
+// 32 << b whose edges |k - j| <= R are at least 90% of those within
+// kMaxWinR; 0 (no window) when fewer than 2% of the edges are that local.
+// Lazy, once.
+di_status ensure_window(di_graph *g, cudaStream_t s) {
+    if (g->win_R >= 0) return DI_OK;
+    unsigned long long *cnt = nullptr;
+    DI_CUDA_TRY(cudaMalloc(&cnt, kWinBins * sizeof(unsigned long long)));
+    unsigned long long h[kWinBins] = {};
+    cudaError_t e = cudaMemsetAsync(cnt, 0, kWinBins * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && g->nnz > 0) {
+        k_win_hist<<<grid_for(g->n, kThreads, g->num_sms * 8), kThreads, 0, s>>>(g->rp, g->pcol, g->hot_node, g->n,
+                                                                                cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cnt);
+    DI_CUDA_TRY(e);
+    const unsigned long long all = h[kWinBins - 1];
+    int R = 0;
+    if (g->nnz > 0 && (double)all >= 0.02 * (double)g->nnz) {
+        int b = 0;
+        while (b < kWinBins - 1 && (double)h[b] < 0.9 * (double)all) ++b;
+        R = 32 << b;
+    }
+    g->win_R = R;
+    return DI_OK;
 }
 
 di_status ensure_scale(di_graph *g, double d, cudaStream_t s) {

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "di_internal.cuh"
+#include "level_tiled.cuh"
 #include "pull.cuh"
 
 namespace di {
@@ -33,8 +34,6 @@ struct Acc<float> { using T = float; };
 template <>
 struct Acc<double> { using T = double; };
 
-__device__ __forceinline__ float thr_cast(double T, float) { return __double2float_ru(T); }
-__device__ __forceinline__ double thr_cast(double T, double) { return T; }
 
 template <typename FT>
 struct Vec4;   // 4 consecutive fluid values per load
@@ -108,19 +107,6 @@ __global__ void __launch_bounds__(kScanThreads) k_init(const SolveDesc *__restri
     }
 }
 
-// Exact recomputation as iterative refinement (FP32 fluid only): every
-// recompute_every levels, and whenever the running |F|_1 estimate r has
-// fallen by the factor recompute_drop since the last exact residual.  The
-// FP32 pushes round each target to 2^-24 of its value, so the drift they add
-// between two recomputations stays a small multiple of 2^-24 * recompute_drop
-// of the current residual.
-__device__ __forceinline__ bool refine_due(const SolveDesc *__restrict__ desc, const SolveState *__restrict__ st,
-                                           int since, double r) {
-    if (desc->fluid_fp64) return false;
-    const int R = desc->recompute_every;
-    const double drop = desc->recompute_drop;
-    return (R > 0 && since >= R) || (drop > 0.0 && r * drop <= st->r_exact);
-}
 
 // |B|_1 only (warm start)
 __global__ void __launch_bounds__(kScanThreads) k_bnorm(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
@@ -379,7 +365,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     // control (all loads first: one round trip)
     const int nf = st->nfront;
     double T = st->T;
-    int level = st->level, since = st->since_recompute, iters = st->body_iters;
+    int level = st->level, since = st->since_recompute, iters = st->body_iters, phase = st->phase;
     const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
     const int max_iters = desc->max_body_iters;
@@ -390,17 +376,14 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
         rec = 1;                            // stop request: confirm on the exact residual, no push
         st->confirming = 1;
         st->r_confirm = ts * est;
-    } else if (nf == 0) {
-        if (tm > 0.0) {                       // empty level: next T is the first T / alpha^k <= max |F|
-            for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
-            if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
-        }
     } else {
+        // push the frontier (if any); the next selection is at the same T
+        // (a resweep) or at T / alpha, or, after an empty first pass, at the
+        // first T / alpha^k <= max |F|
         push = nf;
-        level += 1;
-        since += 1;
-        T = T / alpha;
-        if (refine_due(desc, st, since, ts * est)) rec = 1;
+        const int level0 = level;
+        threshold_step(desc->resweeps, nf > 0, alpha, tm, T, phase, level, since);
+        if (level != level0 && refine_due(desc, st, since, ts * est)) rec = 1;
     }
     iters += 1;
     if (!done && iters >= max_iters) done = 2;
@@ -415,6 +398,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     st->level = level;
     st->since_recompute = since;
     st->body_iters = iters;
+    st->phase = phase;
     st->do_recompute = rec;
     if (done) st->done = done;
     if (ctl == 1) {
@@ -737,7 +721,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     // control step after the level's pushes
     const unsigned long long lnodes = st->lvl_nodes;
     double T = st->T;
-    int level = st->level, since = st->since_recompute, iters = st->body_iters;
+    int level = st->level, since = st->since_recompute, iters = st->body_iters, phase = st->phase;
     const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
     const int max_iters = desc->max_body_iters;
@@ -745,15 +729,9 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     if (!isfinite(ts)) {
         done = 3;
     } else {
-        if (lnodes > 0) {
-            level += 1;
-            since += 1;
-            T = T / alpha;
-            if (refine_due(desc, st, since, ts * est)) rec = 1;
-        } else if (tm > 0.0) {
-            for (int guard = 0; T > tm && guard < 8192; ++guard) T /= alpha;
-            if (T > tm) T = tm;   // alpha so close to 1 that the guard ran out
-        }
+        const int level0 = level;
+        threshold_step(desc->resweeps, lnodes > 0, alpha, tm, T, phase, level, since);
+        if (level != level0 && refine_due(desc, st, since, ts * est)) rec = 1;
         if (ts * est <= tol) {            // the fluid read before the pushes already meets tol
             rec = 1;
             st->confirming = 1;
@@ -769,6 +747,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     st->level = level;
     st->since_recompute = since;
     st->body_iters = iters;
+    st->phase = phase;
     st->lvl_nodes = 0;
     st->do_recompute = rec;
     if (done) st->done = done;
@@ -1221,6 +1200,48 @@ void launch_fused(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
               (int64_t)g->n, ws.part_sum, ws.part_max, hw, hr, ctl);
 }
 
+// Chunk size and grid of the tiled level kernel for this graph and fluid
+// precision (after ensure_window): the largest C in {256, ..., 32} that still
+// gives every warp of the occupancy-limited grid four chunks or more.
+template <typename FT>
+di_status prepare_tiled(di_graph *g) {
+    const int fp64 = sizeof(FT) == 8;
+    if (g->tiled_chunk[fp64]) return DI_OK;
+    const int R = g->win_R;
+    // the attribute is per function, shared by every graph: the largest layout
+    DI_CUDA_TRY(cudaFuncSetAttribute(k_level_tiled<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tiled_smem<FT>(kMaxHot, 256, kMaxWinR)));
+    auto grid_for_chunk = [&](int C, int *grid) -> di_status {
+        const size_t smem = tiled_smem<FT>(g->n_hot, C, R);
+        int per_sm = 0;
+        DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_tiled<FT>, kPushThreads, smem));
+        *grid = std::max(1, per_sm) * g->num_sms;
+        return DI_OK;
+    };
+    int C = 256, grid = 0;
+    DI_TRY(grid_for_chunk(C, &grid));
+    while (C > 32 && g->n / C < 4LL * kTiledWarps * grid) C /= 2;
+    DI_TRY(grid_for_chunk(C, &grid));
+    const int64_t chunks = (g->n + C - 1) / C;
+    g->tiled_chunk[fp64] = C;
+    g->grid_tiled[fp64] = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (chunks + kTiledWarps - 1) / kTiledWarps));
+    return DI_OK;
+}
+
+template <typename FT>
+void launch_tiled(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
+                  int l2) {
+    Workspace &ws = g->ws;
+    const int fp64 = sizeof(FT) == 8;
+    const cudaAccessPolicyWindow *win = l2_window(g, 0, fp64, l2);
+    const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
+    const int C = g->tiled_chunk[fp64], R = g->win_R;
+    launch_ex(k_level_tiled<FT>, g->grid_tiled[fp64], kPushThreads, tiled_smem<FT>(g->n_hot, C, R), s, win,
+              (const SolveDesc *)ws.desc, ws.st, (const int32_t *)g->rp, (const int32_t *)g->pcol,
+              (const int32_t *)g->hot_node, g->n_hot, scale, (int64_t)g->n, C, R, ws.part_sum, ws.part_max, hw, hr,
+              ctl);
+}
+
 template <typename FT>
 void launch_select(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hp,
                    cudaGraphConditionalHandle hr, int ctl, int) {
@@ -1300,7 +1321,11 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraph_t capg = nullptr;
     cudaGraph_t ended = nullptr;
     DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (prop == 5) {
+    if (prop == 6) {
+        // body: k_level_tiled -> IF(exact residual)
+        if (fp64) launch_tiled<double>(g, cs, sg.h_while, sg.h_if, 1, win);
+        else launch_tiled<float>(g, cs, sg.h_while, sg.h_if, 1, win);
+    } else if (prop == 5) {
         // body: k_level_fused -> IF(exact residual)
         if (fp64) launch_fused<double>(g, cs, sg.h_while, sg.h_if, 1, win);
         else launch_fused<float>(g, cs, sg.h_while, sg.h_if, 1, win);
@@ -1378,12 +1403,14 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
         set_error("di_solve: recompute_drop = %g must be 0 or a finite factor > 1", o->recompute_drop);
         return DI_EINVAL;
     }
-    if (o->propagation < 0 || o->propagation > 5) { set_error("di_solve: propagation = %d outside [0, 5]", o->propagation); return DI_EINVAL; }
+    if (o->propagation < 0 || o->propagation > 6) { set_error("di_solve: propagation = %d outside [0, 6]", o->propagation); return DI_EINVAL; }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
+    if (o->resweeps < 0 || o->resweeps > 8) { set_error("di_solve: resweeps = %d outside [0, 8]", o->resweeps); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
     if (o->dangling < 0 || o->dangling > 1) { set_error("di_solve: dangling = %d outside [0, 1]", o->dangling); return DI_EINVAL; }
-    if (o->dangling == 1 && ((o->propagation != 3 && o->propagation != 4) || o->exact_residual == 1)) {
-        set_error("di_solve: the 1/N dangling completion needs propagation 3 or 4 and exact_residual 0 or 2 "
+    if (o->dangling == 1 && ((o->propagation != 3 && o->propagation != 4 && o->propagation != 6) ||
+                             o->exact_residual == 1)) {
+        set_error("di_solve: the 1/N dangling completion needs propagation 3, 4 or 6 and exact_residual 0 or 2 "
                   "(got %d, %d)", o->propagation, o->exact_residual);
         return DI_EINVAL;
     }
@@ -1431,7 +1458,8 @@ di_status ensure_workspace(di_graph *g) {
     g->grid_res = residual_grid(g->num_sms);
     // one partial per CTA of every kernel that reduces across CTAs (the fused
     // level kernel runs on the push grid)
-    const int parts = std::max({g->grid_scan, g->grid_select, residual_partials(g), g->grid_push});
+    // (the tiled kernel's grid is at most the occupancy of 256-thread CTAs, below 2048 per SM)
+    const int parts = std::max({g->grid_scan, g->grid_select, residual_partials(g), g->grid_push, 8 * g->num_sms});
     const PullPlan pl = pull_plan_of(g);
     const int64_t nseg5 = pl.task_off[5] - pl.task_off[4];
     DI_CUDA_TRY(dmalloc(&ws.front, n));
@@ -1485,6 +1513,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     if (o.selection == 1) DI_TRY(ensure_selection_weights(g, s));
     g->res_form = o.exact_residual;
     if (g->res_form != 1) DI_TRY(ensure_blocked_order(g, s));
+    if (o.propagation == 6) {
+        DI_TRY(ensure_window(g, s));
+        DI_TRY(fp64 ? prepare_tiled<double>(g) : prepare_tiled<float>(g));
+    }
     if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
 
     // descriptor (the previous call has completed: every solve synchronises)
@@ -1509,6 +1541,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.warp_max = g->tune.warp_max_deg;
     dh.iw = o.selection == 1 ? (fp64 ? (const void *)g->iw64 : (const void *)g->iw32) : nullptr;
     dh.dangling = o.dangling;
+    dh.resweeps = o.propagation >= 3 ? o.resweeps : 0;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
@@ -1560,7 +1593,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
                 DI_CUDA_TRY(cudaEventRecord(e[3], s));
-                if (o.propagation == 5) {
+                if (o.propagation == 6) {
+                    if (fp64) launch_tiled<double>(g, s, 0, 0, 2, win);
+                    else launch_tiled<float>(g, s, 0, 0, 2, win);
+                } else if (o.propagation == 5) {
                     if (fp64) launch_fused<double>(g, s, 0, 0, 2, win);
                     else launch_fused<float>(g, s, 0, 0, 2, win);
                 } else if (o.propagation >= 3) {
@@ -1578,7 +1614,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                 DI_CUDA_TRY(cudaEventRecord(e[1], s));
                 launch_residual(g, fp64, RES_LEVEL, s);
                 DI_CUDA_TRY(cudaEventRecord(e[2], s));
-                host_launches += (o.propagation == 5 ? 1 : o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
+                host_launches += (o.propagation >= 5 ? 1 : o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
             }
             DI_CUDA_TRY(cudaGetLastError());
             DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -1641,7 +1677,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         } else {
             // per live level: select + one propagation kernel; the level that
             // finds the loop finished; the exact residuals
-            launches += (o.propagation == 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
+            launches += (o.propagation >= 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
         }
         if (refresh) launches += rk;        // final residual refresh
         stats->gpu_launches = launches;
@@ -1651,6 +1687,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         stats->recompute_launches = st.recomputes;
         stats->body_iterations = st.body_iters;
         stats->select_seconds = t_sel;
+        stats->red_ops = (int64_t)st.red_ops;
     }
     return rc;
 }

@@ -54,6 +54,7 @@ def test_version_and_defaults(lib):
     assert o.warm_fallback == 1 and o.max_levels == 100000
     # the fields after the double keep their place in the C layout
     assert o.propagation == 3 and o.push_ratio == 8 and o.selection == 0 and o.spin_limit == 1 << 26
+    assert o.resweeps == 0   # the last field, after the stream pointer
 
 
 def test_invalid_arguments_are_rejected_before_gpu_work(lib):

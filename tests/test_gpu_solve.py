@@ -348,7 +348,7 @@ def test_device_resident_csr_input(web10k):
 
 # ---------------------------------------------------------------- every propagation mode
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_parity_every_propagation_mode(web10k, prop, fp64):
     rp, col, b, x = web10k
@@ -359,7 +359,32 @@ def test_parity_every_propagation_mode(web10k, prop, fp64):
         check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6])
+@pytest.mark.parametrize("resweeps", [0, 2])
+def test_parity_every_resweep_count(web10k, prop, resweeps):
+    # re-selections at the same threshold change the order of the diffusions,
+    # not the limit (Sec. 2: any order that keeps diffusing every node)
+    rp, col, b, x = web10k
+    for fp64, rel in ((False, 1e-6), (True, 1e-11)):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, resweeps=resweeps)
+        assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
+        check_stop(rp, col, b, h, st, tol)
+        assert st.body_iterations >= st.levels
+
+
+def test_resweeps_out_of_range_are_rejected(web10k):
+    rp, col, b, _ = web10k
+    g = di.Graph.create(rp, col)
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    for bad in (-1, 9):
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(resweeps=bad))
+        assert e.value.status == di.DI_EINVAL
+    g.close()
+
+
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6])
 def test_personalised_sparse_levels_every_mode(prop):
     # a personalised right-hand side keeps the early frontiers tiny (scatter levels)
     rp, col = gg.generate(gg.GraphSpec(n=30000, mean_deg=9, seed=8))
@@ -371,7 +396,7 @@ def test_personalised_sparse_levels_every_mode(prop):
     check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [1, 3, 5])
+@pytest.mark.parametrize("prop", [1, 3, 5, 6])
 def test_timing_mode_matches(web10k, prop):
     rp, col, b, x = web10k
     tol = 1e-8 * b.sum()
@@ -485,7 +510,7 @@ def test_solve_on_two_source_blocks_meets_the_stop(web5m):
 
 # ---------------------------------------------------------------- push shapes and the autotuner
 
-@pytest.mark.parametrize("prop", [3, 4, 5])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6])
 @pytest.mark.parametrize("shape", [(1, 1, 0), (4, 64, 1), (32, 32, 0), (1024, 1 << 30, 2)])
 def test_parity_every_push_shape(web10k, prop, shape):
     rp, col, b, x = web10k
@@ -561,7 +586,7 @@ def test_weighted_selection_needs_a_selection_kernel(web10k):
     rp, col, b, _ = web10k
     g = di.Graph.create(rp, col)
     H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
-    for prop in (0, 1, 2, 5):
+    for prop in (0, 1, 2, 5, 6):
         with pytest.raises(di.DiError) as e:
             di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(propagation=prop, selection=1))
         assert e.value.status == di.DI_EINVAL
@@ -614,7 +639,7 @@ def assert_completed_residual_close(f_gpu, f_cpu, rp, col, b, h):
     assert np.all(err <= bound + 1e-300), f"max excess {np.max(err - bound):.3e}"
 
 
-@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("prop", [3, 4, 6])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
     rp, col, b, x = web10k_completed
@@ -633,9 +658,10 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     # a personalised right-hand side (sparse early levels)
     bp = gg.personalised_b(len(b), 1234)
     xp = od.d_iteration(rp, col, bp, D, tol=1e-14 * bp.sum(), dangling=True).H
-    h, st, _, _ = solve(rp, col, bp, 1e-8 * bp.sum(), propagation=4, dangling=1)
-    assert np.abs(h - xp).sum() <= 1e-6 * np.abs(xp).sum()
-    check_stop_completed(rp, col, bp, h, st, 1e-8 * bp.sum())
+    for prop in (4, 6):
+        h, st, _, _ = solve(rp, col, bp, 1e-8 * bp.sum(), propagation=prop, dangling=1)
+        assert np.abs(h - xp).sum() <= 1e-6 * np.abs(xp).sum()
+        check_stop_completed(rp, col, bp, h, st, 1e-8 * bp.sum())
     # a warm start: F0 = B + P H0 - H0 with the completed P (small enough that
     # the start is kept: |F0|_1 <= |B|_1)
     rng = np.random.default_rng(44)
@@ -648,11 +674,12 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     check_stop_completed(rp, col, b, h, st, 1e-8 * b.sum())
 
 
-def test_dangling_completion_on_two_source_blocks(web5m):
+@pytest.mark.parametrize("prop", [4, 6])
+def test_dangling_completion_on_two_source_blocks(web5m, prop):
     # more than 2^22 nodes: the dangling sum of the exact residual spans both blocks
     rp, col, b = web5m
     tol = 1e-8 * b.sum()
-    h, st, f, _ = solve(rp, col, b, tol, propagation=4, dangling=1)
+    h, st, f, _ = solve(rp, col, b, tol, propagation=prop, dangling=1)
     assert st.recomputes >= 1
     f_cpu = check_stop_completed(rp, col, b, h, st, tol)
     assert_completed_residual_close(f, f_cpu, rp, col, b, h)
@@ -696,6 +723,62 @@ def test_dangling_completion_edge_cases(case):
         assert x[0] == pytest.approx(0.15 / (1 - D), rel=1e-13)
     for fp64, rel in ((False, 1e-6), (True, 1e-11)):
         tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
-        h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=3, dangling=1)
-        assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
-        check_stop_completed(rp, col, b, h, st, tol)
+        for prop in (3, 6):
+            h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, dangling=1)
+            assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
+            check_stop_completed(rp, col, b, h, st, tol)
+
+
+# ---------------------------------------------------------------- propagation 6: on-chip window and hot slots
+
+def ring_graph(n, reach):
+    """Every node j points to j+1 .. j+reach (mod n): all edges local."""
+    edges = [(j, (j + k) % n) for j in range(n) for k in range(1, reach + 1)]
+    return csr_from_edges(n, edges)
+
+
+@pytest.mark.parametrize("case", ["ring", "random", "ragged", "tiny", "hub_and_ring"])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_tiled_level_cases(case, fp64):
+    # ring: every target lies in the shared-memory window (wrap-around edges
+    # at both ends of the node range go to global memory); random: no
+    # locality, the window radius is 0; ragged: N not a multiple of the chunk;
+    # tiny: N below one chunk; hub_and_ring: a target of very high in-degree
+    # (a hot slot) that is also inside the window of its sources
+    rng = np.random.default_rng({"ring": 1, "random": 2, "ragged": 3, "tiny": 4, "hub_and_ring": 5}[case])
+    if case == "ring":
+        rp, col = ring_graph(5000, 6)
+    elif case == "random":
+        rp, col = random_graph(6000, rng)
+    elif case == "ragged":
+        rp, col = gg.generate(gg.GraphSpec(n=20011, mean_deg=9.0, seed=17))
+    elif case == "tiny":
+        rp, col = random_graph(37, rng)
+    else:
+        n = 4000
+        edges = [(j, (j + 1) % n) for j in range(n)] + [(j, 2000) for j in range(n) if j != 2000]
+        rp, col = csr_from_edges(n, edges)
+    b = rng.random(len(rp) - 1)
+    x = oracle_x(rp, col, b)
+    tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=6)
+    assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+    f_cpu = check_stop(rp, col, b, h, st, tol)
+    assert_residual_close(f, f_cpu, rp, col, b, h)
+    assert st.red_ops >= 0
+
+
+def test_tiled_level_issues_fewer_reductions_than_edges():
+    # on a graph whose edges all stay within the window, the level kernel's
+    # global reductions are the coalesced flushes only (one per sector of 8
+    # FP32 words) - far fewer than the elementary diffusions it performs
+    rp, col = ring_graph(200_000, 8)
+    b = gg.uniform_b(200_000, D)
+    tol = 1e-8 * b.sum()
+    h, st, _, _ = solve(rp, col, b, tol, propagation=6, want_f=False)
+    x = oracle_x(rp, col, b)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    assert 0 < st.red_ops < st.edge_diffusions / 4, (st.red_ops, st.edge_diffusions)
+    # the other propagations do not count
+    _, st3, _, _ = solve(rp, col, b, tol, propagation=3, want_f=False)
+    assert st3.red_ops == 0
