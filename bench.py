@@ -76,7 +76,7 @@ def parse():
     p.add_argument("--propagation", type=int, default=None,
                    help="0 auto/binned gather, 1 auto/flat gather, 2 push only, 3 asynchronous push, "
                         "4 asynchronous push with warp-level tiles, 5 fused select + push, "
-                        "6 node-ordered chunks with on-chip window and hot slots")
+                        "6 node-ordered chunks with on-chip window and hot slots, 7 persistent level loop")
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
     p.add_argument("--resweeps", type=int, default=None,
                    help="propagations 3-6: re-selections at the same threshold before T <- T/alpha")
@@ -457,7 +457,7 @@ def run_native(args, world, rank, local):
                                l2_window=opts.l2_window, propagation=opts.propagation,
                                push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
                                selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps)
-        te = tn = 0
+        te = tn = tred = 0
         tpush = trec = tsel = 0.0
         npush = 0
         reps = min(3, max(args.steps, 1))
@@ -470,6 +470,7 @@ def run_native(args, world, rank, local):
             trec += ts.recompute_seconds
             tsel += ts.select_seconds
             npush += ts.level_launches
+            tred += ts.red_ops
         alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
         achieved = alg_bytes / tpush / 1e9
         peak, peak_src = measured_hbm_peak()
@@ -485,6 +486,14 @@ def run_native(args, world, rank, local):
                               "seconds": {"level": tpush, "of_which_selection": tsel,
                                           "recompute_and_empty_launches": trec},
                               "measured_by": "CUDA events around every level kernel of host-driven solves"}
+        if tred > 0:
+            # L2 reduction sectors the level kernel issued against the measured ceiling of
+            # scattered red.global.add.f32 (a 2^24-word array, the fluid of a 2^24-node graph)
+            red_peak, _ = di.probe_l2("red_f32", 1 << 24, 1 << 28, stream)
+            extras["l2_red"] = {"achieved": tred / tpush, "peak": red_peak, "unit": "red sectors/s",
+                                "frac": tred / tpush / red_peak, "red_sectors_per_edge": tred / max(te, 1),
+                                "peak_source": "di_probe_l2 red_f32 over 2^24 words, this run",
+                                "kernel": "level kernels (selection + push), host-driven timing"}
         # end to end through the host-buffer entry point: H2D of B, D2H of H
         Bh = torch.from_numpy(b).pin_memory()
         Hh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -540,7 +549,8 @@ def run_native(args, world, rank, local):
                                            "asynchronous push, warp-level tiles",
                                            "fused select + push, one launch per level",
                                            "node-ordered chunks, on-chip window and hot slots, one launch "
-                                           "per level"][opts.propagation],
+                                           "per level",
+                                           "asynchronous push, persistent cooperative level loop"][opts.propagation],
                            "push_ratio": opts.push_ratio, "resweeps": opts.resweeps,
                            "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],

@@ -59,12 +59,16 @@ typedef struct di_graph di_graph;
  * warp_max_deg edges by a warp, a longer one by the whole CTA (the
  * warp-tile push, propagation 4, sends every row above thread_max_deg to a
  * warp); the push runs push_ctas_per_sm CTAs per SM (0 = the occupancy
- * maximum).  Defaults: 16, 512, 0. */
+ * maximum; it also caps the persistent loop's grid, propagation 7).
+ * push_window = 1 gives the frontier push of propagations 3 and 7 a
+ * shared-memory copy of the fluid around each tile of 256 frontier nodes
+ * (targets within the graph's locality radius of the tile are added there and
+ * flushed with coalesced reductions).  Defaults: 16, 512, 0, 0. */
 typedef struct {
     int32_t thread_max_deg;    /* 1 .. 1024 */
     int32_t warp_max_deg;      /* thread_max_deg .. 2^30 */
     int32_t push_ctas_per_sm;  /* 0 .. 64 */
-    int32_t reserved;
+    int32_t push_window;       /* 0 or 1 */
 } di_tune;
 
 /* Solver options.  Fill with di_opts_default() and change what you need. */
@@ -96,7 +100,12 @@ typedef struct {
                               within a window around the chunk and targets of very high
                               in-degree are added in shared memory and flushed with
                               coalesced reductions, fluid sent to a later chunk is diffused
-                              in the same level; rows are pushed edge-parallel per warp */
+                              in the same level; rows are pushed edge-parallel per warp;
+                              7: the levels of mode 3 in one persistent cooperative launch
+                              per segment between exact residuals - selection and push
+                              phases separated by bounded grid barriers (see spin_limit),
+                              whose last CTA runs the control; the phases are timed on the
+                              device (di_stats.level_seconds / select_seconds) */
     int push_ratio;        /* auto: a level is dense (gather) when its active edges times
                               push_ratio reach the edge count; default 8 */
     int exact_residual;    /* form of the exact FP64 residual B + P H - H: 1 gather over the
@@ -108,25 +117,27 @@ typedef struct {
                               |F_i| / ((#in_i + 1)(#out_i + 1)) >= T that Sec. 2.4 names as
                               the ideal diffusion order (T_0 and the empty-level rule then
                               use the largest score; the stop rule keeps |F|_1).
-                              Needs propagation 3 or 4 */
+                              Needs propagation 3, 4 or 7 */
     int dangling;          /* columns of nodes without out-edges: 0 (default) zero, so
                               sum X < 1; 1 the uniform 1/N completion of Sec. 2.2
                               (p_kj = d/N for every k), which makes the columns of Q
                               stochastic.  The fluid a dangling node drains is spread
                               over all nodes as one uniform add in the next frontier
                               selection; the exact residual adds d/N sum_dangling H_j.
-                              Needs propagation 3, 4 or 6 and exact_residual 0 or 2 */
+                              Needs propagation 3, 4, 6 or 7 and exact_residual 0 or 2 */
     double recompute_drop; /* FP32 fluid: exact FP64 residual whenever the running |F|_1
                               has fallen by this factor since the last exact value, so
                               that the FP32 rounding of the pushes stays a fraction of
                               about 2^-24 * recompute_drop of the residual; 0 = no drop
                               rule, else > 1; default 1024.  Either rule, and every stop
                               request, triggers an exact recomputation */
-    long long spin_limit;  /* iteration limit of a bounded device wait.  Reserved: no
-                              kernel of this library waits on another CTA (cross-CTA
-                              decisions use a last-block counter), so it is unused */
+    long long spin_limit;  /* bound of a device wait, in microseconds: the grid barriers of
+                              the persistent level loop (propagation 7) give up after it and
+                              the solve returns DI_ETIMEOUT (no GPU fault; the context stays
+                              usable).  No other kernel waits on another CTA.  0 .. 2^40;
+                              default 2^20 (about 1 s) */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
-    int resweeps;          /* propagations 3-6: after a level's pass, select again at the
+    int resweeps;          /* propagations 3-7: after a level's pass, select again at the
                               same T up to this many times (nodes whose fluid crossed T
                               while the level pushed - what the paper's sequential sweep
                               meets later in the same sweep) before T <- T / alpha; a pass
@@ -148,17 +159,20 @@ typedef struct {
     int32_t status;            /* the di_status the call returned */
     int64_t gpu_launches;      /* kernels this call launched */
     /* CUDA-event times, filled only when opts.timing = 1 */
-    double level_seconds;      /* level kernels (frontier selection fused with the push) */
+    double level_seconds;      /* level kernels (frontier selection fused with the push);
+                                  propagation 7: its selection and push phases, timed on the
+                                  device in either loop mode */
     double recompute_seconds;  /* exact-residual kernels (timing mode launches them each level) */
-    int32_t level_launches;    /* level kernels that did work */
+    int32_t level_launches;    /* level kernels that did work (propagation 7: selection passes) */
     int32_t recompute_launches;/* exact residual recomputations */
     int32_t body_iterations;   /* iterations of the device-side level loop */
     int32_t reserved;
-    double select_seconds;     /* timing mode, propagation 3/4: the frontier-selection part of
-                                  level_seconds */
-    int64_t red_ops;           /* propagation 6: global L2 reduction sectors its level kernel
-                                  issued (a scattered red counts one, a coalesced flush one per
-                                  sector it touches); 0 for the other propagations */
+    double select_seconds;     /* timing mode, propagation 3/4 (propagation 7: always): the
+                                  frontier-selection part of level_seconds */
+    int64_t red_ops;           /* propagations 3, 6, 7: global L2 reduction sectors the push
+                                  issued (a scattered red counts one, a coalesced flush of the
+                                  shared-memory fluid window one per sector it touches); 0 for
+                                  the other propagations */
 } di_stats;
 
 /* Library version string. */
@@ -170,7 +184,7 @@ DI_API const char *di_last_error(void);
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 0, recompute_drop 1024,
  * max_levels 100000, cold start (fallback on when warm), L2 window on,
  * timing off, propagation 3, push_ratio 8, exact_residual 0, selection 0,
- * dangling 0, spin_limit 2^26, stream NULL, resweeps 0.  Returns DI_EINVAL if
+ * dangling 0, spin_limit 2^20, stream NULL, resweeps 0.  Returns DI_EINVAL if
  * o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
@@ -449,7 +463,8 @@ DI_API di_status di_probe_l2(int mode, int64_t slots, int64_t ops, double *ops_p
  * depends on the graph's degree mix.  di_autotune / di_batch_autotune time
  * complete solves of the caller's problem (plain D-iteration, the same
  * options) for candidate shapes - thread_max_deg in {4, 8, 16, 32}, with the
- * occupancy-maximum push grid and with half of it - keep the fastest, store
+ * occupancy-maximum push grid and with half of it, and (di_autotune with
+ * propagation 3 or 7) the default shape with the fluid window - keep the fastest, store
  * it in the graph or batch (used by every later solve) and return it.
  * cache_path (may be NULL) names a text file of JSON lines keyed by the
  * problem's size bucket (log2 of nodes and edges, items, fluid precision,

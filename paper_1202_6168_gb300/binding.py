@@ -36,11 +36,11 @@ class di_train_opts(ctypes.Structure):
 
 class di_tune(ctypes.Structure):
     _fields_ = [("thread_max_deg", c_i32), ("warp_max_deg", c_i32), ("push_ctas_per_sm", c_i32),
-                ("reserved", c_i32)]
+                ("push_window", c_i32)]
 
     def as_dict(self) -> dict:
         return {"thread_max_deg": self.thread_max_deg, "warp_max_deg": self.warp_max_deg,
-                "push_ctas_per_sm": self.push_ctas_per_sm}
+                "push_ctas_per_sm": self.push_ctas_per_sm, "push_window": self.push_window}
 
 
 class di_stats(ctypes.Structure):

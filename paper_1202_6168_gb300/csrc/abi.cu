@@ -42,7 +42,7 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->exact_residual = 0;
     o->selection = 0;
     o->dangling = 0;
-    o->spin_limit = 1LL << 26;
+    o->spin_limit = 1LL << 20;
     o->stream = nullptr;
     o->resweeps = 0;
     return DI_OK;

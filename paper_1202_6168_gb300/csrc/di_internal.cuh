@@ -47,6 +47,7 @@ constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
 constexpr int kSrcBlockShift = 22;  // exact residual: sources in blocks of 2^22 nodes (32 MB of FP64 gathers)
 constexpr int kWinBins = 4;         // tiled level kernel: window radii 32 .. 256 (powers of two)
 constexpr int kMaxWinR = 32 << (kWinBins - 1);
+constexpr int kPushWin = 1024;      // frontier push: nodes of a tile's fluid window beyond its radius
 
 // ------------------------------------------------------------------ solver state
 
@@ -71,7 +72,8 @@ struct SolveDesc {
     int warp_max;         // ... up to this to one warp, longer ones to the CTA
     const void *iw;       // weighted selection: 1 / ((in + 1)(out + 1)) per node (FT), else NULL
     int dangling;         // 1: columns of dangling nodes completed by d/N (uniform)
-    int resweeps;         // propagations 3-6: extra selections at the same T before T <- T / alpha
+    int resweeps;         // propagations 3-7: extra selections at the same T before T <- T / alpha
+    int win_R;            // frontier push (propagations 3, 7): radius of the shared-memory fluid window, 0 = none
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -111,7 +113,12 @@ struct SolveState {
     double dang_h;              // exact residual: sum of H over the dangling nodes
     double dang_next;           // tiled level: dangling fluid drained in this level (for the next)
     int phase;                  // selections made at the current T (0 = the level's first)
-    int pad2;
+    int timed_out;              // persistent loop: a grid barrier gave up (DI_ETIMEOUT)
+    unsigned int bar_count;     // persistent loop: CTAs arrived at the current grid barrier
+    unsigned int bar_gen;       // persistent loop: barrier generation (released when it changes)
+    unsigned long long t_mark;  // persistent loop: %globaltimer at the last phase boundary (ns)
+    unsigned long long t_scan_ns, t_push_ns;   // persistent loop: time in selection / push phases
+    unsigned long long passes;  // persistent loop: selection passes made
     unsigned long long red_ops; // tiled level: global reduction sectors issued (scattered reds count one each)
 };
 
@@ -131,6 +138,8 @@ struct SolverGraph {
     int prop = 0;         // built with this propagation option
     int res_form = 0;     // built with this exact-residual form
     int grid_push = 0;    // built with this push grid
+    unsigned long long timeout_ns = 0;   // built with this grid-barrier bound (persistent loop)
+    int grid_coop = 0;                   // built with this persistent grid
 };
 
 struct Workspace {
@@ -203,6 +212,10 @@ struct di_graph {
     // nodes per chunk and grid (per fluid precision)
     int win_R = -1;
     int tiled_chunk[2] = {0, 0}, grid_tiled[2] = {0, 0};
+    // persistent level loop: cooperative grid (per fluid precision) and grid-barrier bound
+    int grid_coop[2] = {0, 0};
+    unsigned long long coop_timeout_ns = 0;
+    int push_R = 0;               // frontier push: window radius in use (0 = none)
     // weighted selection (Sec. 2.4 score): 1 / ((in + 1)(out + 1)), built on first use
     float *iw32 = nullptr;
     double *iw64 = nullptr;
@@ -299,7 +312,7 @@ __device__ __forceinline__ bool refine_due(const SolveDesc *__restrict__ desc, c
     if (desc->fluid_fp64) return false;
     const int R = desc->recompute_every;
     const double drop = desc->recompute_drop;
-    return (R > 0 && since >= R) || (drop > 0.0 && r * drop <= st->r_exact);
+    return (R > 0 && since >= R) || (drop > 0.0 && r * drop <= __ldcg(&st->r_exact));
 }
 
 // Threshold schedule after one selection pass (Sec. 2.4): a level starts at
@@ -367,6 +380,35 @@ __device__ __forceinline__ void block_sum_max(double &s, double &m) {
         m = warp_max(m);
     }
     __syncthreads();
+}
+
+// Adds this CTA's per-thread counts to up to four device counters with one
+// global atomic per counter and CTA (the same-address atomics of every warp
+// would serialise at one L2 slice).  Every thread of the CTA must call it.
+__device__ __forceinline__ void cta_add_counts(unsigned long long *c0, unsigned long long v0, unsigned long long *c1,
+                                               unsigned long long v1, unsigned long long *c2 = nullptr,
+                                               unsigned long long v2 = 0, unsigned long long *c3 = nullptr,
+                                               unsigned long long v3 = 0) {
+    __shared__ unsigned long long s_c[4];
+    if (threadIdx.x < 4) s_c[threadIdx.x] = 0ull;
+    __syncthreads();
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    v3 = warp_sum(v3);
+    if ((threadIdx.x & 31) == 0) {
+        if (v0) atomicAdd(&s_c[0], v0);
+        if (v1) atomicAdd(&s_c[1], v1);
+        if (v2) atomicAdd(&s_c[2], v2);
+        if (v3) atomicAdd(&s_c[3], v3);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_c[0] && c0) atomicAdd(c0, s_c[0]);
+        if (s_c[1] && c1) atomicAdd(c1, s_c[1]);
+        if (s_c[2] && c2) atomicAdd(c2, s_c[2]);
+        if (s_c[3] && c3) atomicAdd(c3, s_c[3]);
+    }
 }
 
 // Marks this block done; returns true in every thread of the last block to

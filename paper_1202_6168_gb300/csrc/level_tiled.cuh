@@ -214,16 +214,9 @@ __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 4 : 6) k_level
             ++my_reds;
         }
     }
-    my_edges = warp_sum(my_edges);
-    my_nodes = warp_sum(my_nodes);
-    my_reds = warp_sum(my_reds);
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->lvl_nodes, my_nodes, &st->red_ops,
+                   my_reds);
     my_dang = warp_sum(my_dang);
-    if (lane == 0 && (my_nodes || my_reds)) {
-        atomicAdd(&st->node_diff, my_nodes);
-        atomicAdd(&st->edge_diff, my_edges);
-        atomicAdd(&st->lvl_nodes, my_nodes);
-        atomicAdd(&st->red_ops, my_reds);
-    }
     if (lane == 0 && my_dang != 0.0) atomicAdd(&s_dang, my_dang);
     double s = static_cast<double>(acc);
     double m = static_cast<double>(mx);

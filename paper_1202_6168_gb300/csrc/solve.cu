@@ -51,6 +51,10 @@ struct Vec4<float> {
         const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
+    __device__ __forceinline__ void load_cg(const float *p) {
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
 };
 template <>
 struct Vec4<double> {
@@ -68,7 +72,28 @@ struct Vec4<double> {
                       b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
+    __device__ __forceinline__ void load_cg(const double *p) {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)),
+                      b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
 };
+
+// Loads of data that other SMs write while a persistent kernel runs: kCG
+// selects ld.global.cg (L2 only), since an SM's L1 is not kept coherent with
+// other SMs' writes and is only clean at a kernel launch; a kernel launched
+// per phase keeps the cheaper streaming loads.
+template <bool kCG, typename T>
+__device__ __forceinline__ T ld_mut(const T *p) { return kCG ? __ldcg(p) : __ldcs(p); }
+
+// Dynamic shared memory of the frontier push (propagations 3 and 7): the hot
+// slots (padded to 4 words), then the fluid window of kPushWin + 2R words
+// (none when R = 0).
+__host__ __device__ inline int push_hot_pad(int n_hot) { return (n_hot + 3) & ~3; }
+template <typename FT>
+__host__ __device__ inline size_t push_smem(int n_hot, int R) {
+    return (size_t)(push_hot_pad(n_hot) + (R > 0 ? kPushWin + 2 * R : 0)) * sizeof(FT);
+}
 
 // ------------------------------------------------------------------ init (cold start)
 
@@ -205,34 +230,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const SolveDesc *__restri
 // Its last CTA decides the level: push the frontier (T <- T / alpha), lower T
 // to the largest fluid after an empty scan, or request an exact residual to
 // confirm a stop (no push).  ctl: 1 in a CUDA graph, 2 host-driven.
-template <typename FT>
-__global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
-    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front, int64_t n,
-    double *__restrict__ part_sum, double *__restrict__ part_max, cudaGraphConditionalHandle h_while,
-    cudaGraphConditionalHandle h_rec, int ctl) {
-    {
-        const int done0 = st->done;
-        const int stop = done0 ? done0 : (st->level >= desc->max_levels ? 2 : 0);
-        if (stop) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                st->done = stop;
-                st->push_count = 0;
-                if (ctl == 1) {
-                    cudaGraphSetConditional(h_rec, 0);
-                    cudaGraphSetConditional(h_while, 0);
-                }
-            }
-            return;
-        }
-    }
+// Selection pass of one level (every CTA over its chunks): the frontier
+// slice of the CTA and its partial |F|_1 and max in part_sum / part_max.
+template <typename FT, bool kCG = false>
+__device__ __forceinline__ void scan_select(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                            int32_t *__restrict__ front, int64_t n, double *__restrict__ part_sum,
+                                            double *__restrict__ part_max) {
     using AT = typename Acc<FT>::T;
     // not __restrict__: with the dangling completion pass 1 writes F and pass 2 reads it back
     FT *F = static_cast<FT *>(desc->F);
-    const FT Tc = thr_cast(st->T, FT(0));
+    const FT Tc = thr_cast(__ldcg(&st->T), FT(0));
     // 1/N completion (Sec. 2.2): the fluid that dangling nodes drained since the
     // last selection reaches every node as d / N of it; added here, before the
     // test, and stored (the last CTA clears the accumulator)
-    const FT u = desc->dangling ? static_cast<FT>(desc->d * st->dang_acc / (double)n) : FT(0);
+    const FT u = desc->dangling ? static_cast<FT>(desc->d * __ldcg(&st->dang_acc) / (double)n) : FT(0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // vector layout of a 2048-node chunk: item k (0, 1), thread t, nodes
     // c0 + 1024 k + 4 t + j (j = 0..3), which is node order; the fluid vector
@@ -267,7 +278,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 #pragma unroll
         for (int k = 0; k < kVItems; ++k) {
             const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
-            if (i0 < n) f[k].load(F + i0);
+            if (i0 < n) {
+                if (kCG) f[k].load_cg(F + i0);
+                else f[k].load(F + i0);
+            }
             else f[k].v[0] = f[k].v[1] = f[k].v[2] = f[k].v[3] = FT(0);
         }
         if (u != FT(0)) {
@@ -315,7 +329,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
             for (int k = 0; k < kVItems; ++k) {
                 const int64_t i0 = c0 + (int64_t)k * 4 * kScanThreads + 4 * threadIdx.x;
                 Vec4<FT> f, w;
-                if (i0 < n) f.load(F + i0);
+                if (i0 < n) {
+                    if (kCG) f.load_cg(F + i0);
+                    else f.load(F + i0);
+                }
                 else f.v[0] = f.v[1] = f.v[2] = f.v[3] = FT(0);
                 load_w(w, i0);
                 msk[k] = sel_mask(f, w, i0);
@@ -356,17 +373,32 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     double m = static_cast<double>(mx);
     block_sum_max<kScanThreads>(s, m);
     if (threadIdx.x == 0) { part_sum[blockIdx.x] = s; part_max[blockIdx.x] = m; }
-    if (!last_block(&st->scan_blocks)) return;
+}
+
+// Control step of a level after its selection pass, run by one CTA that sees
+// every partial: the push (or not) and the next threshold, a stop request or
+// an exact recomputation.  ctl: 1 sets the graph's conditionals, otherwise
+// none are set.
+__device__ __noinline__ void scan_control(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                          const double *__restrict__ part_sum, const double *__restrict__ part_max,
+                                          int nparts, cudaGraphConditionalHandle h_while,
+                                          cudaGraphConditionalHandle h_rec, int ctl) {
     double ts = 0.0, tm = 0.0;
-    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) { ts += part_sum[i]; tm = fmax(tm, part_max[i]); }
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        ts += __ldcg(part_sum + i);
+        tm = fmax(tm, __ldcg(part_max + i));
+    }
     block_sum_max<kScanThreads>(ts, tm);
     if (threadIdx.x != 0) return;
 
-    // control (all loads first: one round trip)
-    const int nf = st->nfront;
-    double T = st->T;
-    int level = st->level, since = st->since_recompute, iters = st->body_iters, phase = st->phase;
-    const double est = st->est_scale > 1.0 ? st->est_scale : 1.0;
+    // control (all loads first, one round trip; read past L1, which a
+    // persistent kernel may hold stale)
+    const int nf = __ldcg(&st->nfront);
+    double T = __ldcg(&st->T);
+    int level = __ldcg(&st->level), since = __ldcg(&st->since_recompute), iters = __ldcg(&st->body_iters),
+        phase = __ldcg(&st->phase);
+    const double est_raw = __ldcg(&st->est_scale);
+    const double est = est_raw > 1.0 ? est_raw : 1.0;
     const double tol = desc->tol, alpha = desc->alpha;
     const int max_iters = desc->max_body_iters;
     int done = 0, rec = 0, push = 0;
@@ -407,6 +439,36 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     }
 }
 
+// A stop found at the start of a level (converged, capped or not finite):
+// no selection; in a graph the loop ends.
+__device__ __forceinline__ bool level_stopped(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                              cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_rec,
+                                              int ctl) {
+    const int done0 = st->done;
+    const int stop = done0 ? done0 : (st->level >= desc->max_levels ? 2 : 0);
+    if (!stop) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = stop;
+        st->push_count = 0;
+        if (ctl == 1) {
+            cudaGraphSetConditional(h_rec, 0);
+            cudaGraphSetConditional(h_while, 0);
+        }
+    }
+    return true;
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front, int64_t n,
+    double *__restrict__ part_sum, double *__restrict__ part_max, cudaGraphConditionalHandle h_while,
+    cudaGraphConditionalHandle h_rec, int ctl) {
+    if (level_stopped(desc, st, h_while, h_rec, ctl)) return;
+    scan_select<FT>(desc, st, front, n, part_sum, part_max);
+    if (!last_block(&st->scan_blocks)) return;
+    scan_control(desc, st, part_sum, part_max, gridDim.x, h_while, h_rec, ctl);
+}
+
 // Push of the asynchronous design, for every frontier node i: f =
 // atomicExch(F_i, 0) (fluid that arrives after the exchange waits for a
 // later level), H_i += f in FP64, and F_k += (d / outdeg_i) f for every
@@ -414,18 +476,20 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 // nodes; a row is pushed by its thread (outdeg <= 16), by a warp (<= 512)
 // or by the whole CTA.  Targets of very high in-degree are accumulated in
 // shared memory per CTA and flushed once.
-template <typename FT>
-__global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 6 : 8)
-    k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
-                                                       const int32_t *__restrict__ front,
-                                                       const int32_t *__restrict__ rp,
-                                                       const int32_t *__restrict__ pcol,
-                                                       const int32_t *__restrict__ hot_node, int n_hot,
-                                                       const FT *__restrict__ scale) {
-    const int count = st->push_count;
+template <typename FT, bool kCG = false>
+__device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
+                                              const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
+                                              const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node,
+                                              int n_hot, const FT *__restrict__ scale) {
+    const int count = __ldcg(&st->push_count);
     if (count == 0) return;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     FT *s_hot = reinterpret_cast<FT *>(smem_raw);
+    // fluid window of the tile: targets in [lo - R, lo - R + span) with lo the
+    // tile's first frontier node (span = kPushWin + 2R, 0 when R = 0)
+    const int R = desc->win_R;
+    const unsigned span = R > 0 ? (unsigned)(kPushWin + 2 * R) : 0u;
+    FT *s_win = s_hot + push_hot_pad(n_hot);
     __shared__ unsigned s_tile;
     __shared__ int s_qn;
     __shared__ int32_t s_qb[kPushThreads], s_qe[kPushThreads];
@@ -434,18 +498,30 @@ __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 6 : 8)
 
     FT *__restrict__ F = static_cast<FT *>(desc->F);
     double *__restrict__ H = desc->H;
+    const int64_t n = desc->n_nodes;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_dang = 0.0;   // ordered before any add by the loop's first barrier
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
+    for (unsigned q = threadIdx.x; q < span; q += kPushThreads) s_win[q] = FT(0);
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max, warp_max = desc->warp_max;
+    unsigned long long my_edges = 0, my_nodes = 0, my_reds = 0;
+    int64_t wlo = 0;
 
     auto push1 = [&](int32_t c, FT w) {
-        if (c >= 0) red_add_keep(F + c, w, keep);
-        else atomicAdd(&s_hot[-1 - c], w);
+        if (c < 0) {
+            atomicAdd(&s_hot[-1 - c], w);
+            return;
+        }
+        const uint64_t o = (uint64_t)((int64_t)c - wlo);
+        if (o < span) {
+            atomicAdd(&s_win[o], w);
+        } else {
+            red_add_keep(F + c, w, keep);
+            ++my_reds;
+        }
     };
 
-    unsigned long long my_edges = 0, my_nodes = 0;
     // tiles are claimed two at a time (one atomic on the shared counter per
     // 512 frontier entries) and pushed one after the other
     unsigned pair = 0;
@@ -461,16 +537,19 @@ __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 6 : 8)
         const int64_t first = (int64_t)(pair + sub) * kPushThreads;
         ++sub;
         if (first >= count) break;
+        // the frontier of a CTA's scan slice is in node order, so in a dense
+        // level the tile's nodes (and most of their near targets) fall in the window
+        if (span) wlo = (int64_t)ld_mut<kCG>(front + first) - R;
         const int64_t idx = first + threadIdx.x;
         int32_t b = 0, e = 0;
         FT w = FT(0);
         if (idx < count) {
-            const int32_t i = __ldcs(front + idx);
+            const int32_t i = ld_mut<kCG>(front + idx);
             b = __ldcs(rp + i);
             e = __ldcs(rp + i + 1);
             const FT f = atomic_exch_keep(F + i, FT(0), keep);
             const double fd = static_cast<double>(f);
-            __stcs(H + i, __ldcs(H + i) + fd);   // i appears once per frontier
+            __stcs(H + i, ld_mut<kCG>(H + i) + fd);   // i appears once per frontier
             if (e == b && desc->dangling) atomicAdd(&s_dang, fd);   // 1/N completion
             w = f * __ldcs(scale + i);
             my_nodes += 1;
@@ -505,19 +584,160 @@ __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 6 : 8)
             push_range<2>(pcol, (int64_t)hb + threadIdx.x, he, kPushThreads, pw);
         }
         __syncthreads();
+        // flush the window and clear it: consecutive threads, consecutive nodes
+        // (coalesced reductions, eight FP32 or four FP64 words per sector)
+        for (unsigned q = threadIdx.x; q < span; q += kPushThreads) {
+            const FT v = s_win[q];
+            s_win[q] = FT(0);
+            const int64_t node = wlo + q;
+            const bool go = v != FT(0) && node >= 0 && node < n;
+            const unsigned m = __ballot_sync(0xffffffffu, go);
+            if (lane == 0) {
+                constexpr int per = 32 / (int)sizeof(FT);
+                for (int g = 0; g < 32; g += per) my_reds += ((m >> g) & ((1u << per) - 1u)) ? 1u : 0u;
+            }
+            if (go) red_add_keep(F + node, v, keep);
+        }
     }
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
         const FT v = s_hot[sl];
-        if (v != FT(0)) red_add_keep(F + hot_node[sl], v, keep);
+        if (v != FT(0)) {
+            red_add_keep(F + hot_node[sl], v, keep);
+            ++my_reds;
+        }
     }
-    my_edges = warp_sum(my_edges);
-    my_nodes = warp_sum(my_nodes);
-    if (lane == 0 && my_nodes) {
-        atomicAdd(&st->node_diff, my_nodes);
-        atomicAdd(&st->edge_diff, my_edges);
-    }
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->red_ops, my_reds);
     if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_acc, s_dang);
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(kPushThreads, 6)
+    k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ front,
+                 const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
+                 const int32_t *__restrict__ hot_node, int n_hot, const FT *__restrict__ scale) {
+    push_frontier<FT>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
+}
+
+// ------------------------------------------------------------------ persistent level loop (propagation 7)
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of a cooperative launch (every CTA resident).  The last CTA to
+// arrive runs control() with all its threads (it sees every write made
+// before the barrier), then releases the others by advancing the generation.
+// The wait is bounded: after timeout_ns of %globaltimer a waiting CTA records
+// the timeout and every CTA leaves the loop at its next check (no spin is
+// unbounded, so a lost CTA cannot hang the device).  Returns false on a
+// timeout.
+template <typename Control>
+__device__ __forceinline__ bool grid_barrier(SolveState *st, unsigned long long timeout_ns, Control control) {
+    __shared__ unsigned s_gen;
+    __shared__ int s_last, s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_gen = ld_acquire_gpu(&st->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+        s_last = arrived == gridDim.x;
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0) st->bar_count = 0;
+        control();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(&st->bar_gen, s_gen + 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        const unsigned long long t0 = global_ns();
+        // bounded twice: by the timer and by the number of polls (each sleeps >= ~32 ns)
+        const unsigned long long max_polls = (timeout_ns >> 5) + 1024ull;
+        unsigned long long polls = 0;
+        while (ld_acquire_gpu(&st->bar_gen) == s_gen) {
+            if (global_ns() - t0 > timeout_ns || ++polls > max_polls) {
+                atomicExch(&st->timed_out, 1);
+                s_ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    // one decision per CTA (another CTA may set the flag at any time); the
+    // CTA's later reads of shared state go to L2 (.cg), ordered after thread
+    // 0's acquire by the block barrier
+    if (threadIdx.x == 0 && __ldcg(&st->timed_out)) s_ok = 0;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The level loop of propagation 3 in one cooperative launch: every pass is a
+// selection phase (frontier compaction, |F|_1 and max) and, when the control
+// pushes, a push phase of the asynchronous design, separated by grid
+// barriers whose last CTA runs the control.  The kernel returns when the
+// control asks for an exact FP64 residual (a stop to confirm or a
+// refinement) or the solve ended; a CUDA graph runs the residual in an IF
+// node and relaunches it in its WHILE node.  The controller also adds the
+// wall time of each phase (%globaltimer) to the solve state.
+template <typename FT>
+__global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 4 : 6) k_levels_coop(
+    const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front,
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node, int n_hot,
+    const FT *__restrict__ scale, int64_t n, double *__restrict__ part_sum, double *__restrict__ part_max,
+    unsigned long long timeout_ns, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_rec, int ctl) {
+    if (level_stopped(desc, st, h_while, h_rec, ctl)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_mark = global_ns();
+    bool ok = true;
+    for (;;) {
+        scan_select<FT, true>(desc, st, front, n, part_sum, part_max);
+        ok = grid_barrier(st, timeout_ns, [&] {
+            scan_control(desc, st, part_sum, part_max, gridDim.x, h_while, h_rec, 0);
+            if (threadIdx.x == 0) {
+                const unsigned long long t = global_ns();
+                st->t_scan_ns = __ldcg(&st->t_scan_ns) + (t - __ldcg(&st->t_mark));
+                st->t_mark = t;
+                st->passes = __ldcg(&st->passes) + 1;
+            }
+        });
+        if (!ok) break;
+        if (__ldcg(&st->push_count) > 0) {
+            push_frontier<FT, true>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
+            ok = grid_barrier(st, timeout_ns, [&] {
+                if (threadIdx.x == 0) {
+                    const unsigned long long t = global_ns();
+                    st->t_push_ns = __ldcg(&st->t_push_ns) + (t - __ldcg(&st->t_mark));
+                    st->t_mark = t;
+                }
+            });
+            if (!ok) break;
+        }
+        if (__ldcg(&st->done) || __ldcg(&st->do_recompute)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!ok || __ldcg(&st->timed_out)) {
+            st->done = 4;          // a grid barrier gave up (here or in another CTA): DI_ETIMEOUT
+            st->do_recompute = 0;
+        }
+        if (ctl == 1) {
+            cudaGraphSetConditional(h_rec, __ldcg(&st->do_recompute) ? 1u : 0u);
+            if (__ldcg(&st->done)) cudaGraphSetConditional(h_while, 0);
+        }
+    }
 }
 
 // Push of the asynchronous design, warp-level form: every warp claims
@@ -601,12 +821,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
         const FT v = s_hot[sl];
         if (v != FT(0)) red_add_keep(F + hot_node[sl], v, keep);
     }
-    my_edges = warp_sum(my_edges);
-    my_nodes = warp_sum(my_nodes);
-    if (lane == 0 && my_nodes) {
-        atomicAdd(&st->node_diff, my_nodes);
-        atomicAdd(&st->edge_diff, my_edges);
-    }
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges);
     if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_acc, s_dang);
 }
 
@@ -701,13 +916,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
         const FT hv = s_hot[sl];
         if (hv != FT(0)) red_add_keep(F + hot_node[sl], hv, keep);
     }
-    my_edges = warp_sum(my_edges);
-    my_nodes = warp_sum(my_nodes);
-    if (lane == 0 && my_nodes) {
-        atomicAdd(&st->node_diff, my_nodes);
-        atomicAdd(&st->edge_diff, my_edges);
-        atomicAdd(&st->lvl_nodes, my_nodes);
-    }
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->lvl_nodes, my_nodes);
     double s = static_cast<double>(acc);
     double m = static_cast<double>(mx);
     block_sum_max<kPushThreads>(s, m);
@@ -865,14 +1074,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_select(
         }
         w[i] = wvi;
     }
-    my_edges = warp_sum(my_edges);
-    my_nodes = warp_sum(my_nodes);
-    if ((threadIdx.x & 31) == 0 && my_nodes) {
-        atomicAdd(&st->node_diff, my_nodes);
-        atomicAdd(&st->edge_diff, my_edges);
-        atomicAdd(&st->lvl_nodes, my_nodes);
-        atomicAdd(&st->lvl_edges, my_edges);
-    }
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->lvl_nodes, my_nodes, &st->lvl_edges,
+                   my_edges);
     double s = static_cast<double>(acc);
     double m = static_cast<double>(mx);
     block_sum_max<kLevelThreads>(s, m);
@@ -1183,7 +1386,7 @@ void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
     else
-        launch_ex(k_push_async<FT>, push_grid(g), kPushThreads, g->n_hot * sizeof(FT), s, win,
+        launch_ex(k_push_async<FT>, push_grid(g), kPushThreads, push_smem<FT>(g->n_hot, g->push_R), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
 }
@@ -1242,6 +1445,51 @@ void launch_tiled(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
               ctl);
 }
 
+// Grid of the persistent level loop: every CTA must be resident at once (a
+// cooperative launch), so the occupancy maximum of the kernel with its hot
+// slots, on every SM.
+template <typename FT>
+di_status prepare_coop(di_graph *g) {
+    const int fp64 = sizeof(FT) == 8;
+    int per_sm = 0;
+    DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_coop<FT>, kPushThreads,
+                                                              push_smem<FT>(g->n_hot, g->push_R)));
+    if (per_sm < 1) { set_error("persistent level loop: the kernel does not fit on an SM"); return DI_ECUDA; }
+    // the push shape's CTAs per SM (di_tune) caps the grid, as for the push kernels
+    if (g->tune.push_ctas_per_sm > 0) per_sm = std::min(per_sm, g->tune.push_ctas_per_sm);
+    g->grid_coop[fp64] = per_sm * g->num_sms;
+    return DI_OK;
+}
+
+template <typename FT>
+void launch_coop(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl,
+                 int l2, unsigned long long timeout_ns) {
+    Workspace &ws = g->ws;
+    const int fp64 = sizeof(FT) == 8;
+    const cudaAccessPolicyWindow *win = l2_window(g, 0, fp64, l2);
+    const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(g->s32) : reinterpret_cast<const FT *>(g->s64);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g->grid_coop[fp64]);
+    cfg.blockDim = dim3(kPushThreads);
+    cfg.dynamicSmemBytes = push_smem<FT>(g->n_hot, g->push_R);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+    if (win) {
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na].val.accessPolicyWindow = *win;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    cudaLaunchKernelEx(&cfg, k_levels_coop<FT>, (const SolveDesc *)ws.desc, ws.st, ws.front, (const int32_t *)g->rp,
+                       (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale, (int64_t)g->n,
+                       ws.part_sum, ws.part_max, timeout_ns, hw, hr, ctl);
+}
+
 template <typename FT>
 void launch_select(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hp,
                    cudaGraphConditionalHandle hr, int ctl, int) {
@@ -1283,7 +1531,8 @@ void launch_pushw(di_graph *g, cudaStream_t s, int l2) {
 
 di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     SolverGraph &sg = g->sg[fp64];
-    if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form && sg.grid_push == push_grid(g))
+    if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form && sg.grid_push == push_grid(g) &&
+        sg.timeout_ns == g->coop_timeout_ns && sg.grid_coop == g->grid_coop[fp64])
         return DI_OK;
     if (sg.built) {   // rebuilt with the other window setting
         cudaGraphExecDestroy(sg.exec);
@@ -1321,7 +1570,11 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraph_t capg = nullptr;
     cudaGraph_t ended = nullptr;
     DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (prop == 6) {
+    if (prop == 7) {
+        // body: k_levels_coop (passes until a residual is due) -> IF(exact residual)
+        if (fp64) launch_coop<double>(g, cs, sg.h_while, sg.h_if, 1, win, g->coop_timeout_ns);
+        else launch_coop<float>(g, cs, sg.h_while, sg.h_if, 1, win, g->coop_timeout_ns);
+    } else if (prop == 6) {
         // body: k_level_tiled -> IF(exact residual)
         if (fp64) launch_tiled<double>(g, cs, sg.h_while, sg.h_if, 1, win);
         else launch_tiled<float>(g, cs, sg.h_while, sg.h_if, 1, win);
@@ -1378,6 +1631,8 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     sg.prop = prop;
     sg.res_form = g->res_form;
     sg.grid_push = push_grid(g);
+    sg.timeout_ns = g->coop_timeout_ns;
+    sg.grid_coop = g->grid_coop[fp64];
     return DI_OK;
 }
 
@@ -1403,19 +1658,22 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
         set_error("di_solve: recompute_drop = %g must be 0 or a finite factor > 1", o->recompute_drop);
         return DI_EINVAL;
     }
-    if (o->propagation < 0 || o->propagation > 6) { set_error("di_solve: propagation = %d outside [0, 6]", o->propagation); return DI_EINVAL; }
+    if (o->propagation < 0 || o->propagation > 7) { set_error("di_solve: propagation = %d outside [0, 7]", o->propagation); return DI_EINVAL; }
+    if (o->spin_limit < 0 || o->spin_limit > (1LL << 40)) {
+        set_error("di_solve: spin_limit = %lld outside [0, 2^40] us", o->spin_limit);
+        return DI_EINVAL;
+    }
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     if (o->resweeps < 0 || o->resweeps > 8) { set_error("di_solve: resweeps = %d outside [0, 8]", o->resweeps); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
     if (o->dangling < 0 || o->dangling > 1) { set_error("di_solve: dangling = %d outside [0, 1]", o->dangling); return DI_EINVAL; }
-    if (o->dangling == 1 && ((o->propagation != 3 && o->propagation != 4 && o->propagation != 6) ||
-                             o->exact_residual == 1)) {
-        set_error("di_solve: the 1/N dangling completion needs propagation 3, 4 or 6 and exact_residual 0 or 2 "
+    if (o->dangling == 1 && ((o->propagation < 3 || o->propagation == 5) || o->exact_residual == 1)) {
+        set_error("di_solve: the 1/N dangling completion needs propagation 3, 4, 6 or 7 and exact_residual 0 or 2 "
                   "(got %d, %d)", o->propagation, o->exact_residual);
         return DI_EINVAL;
     }
-    if (o->selection == 1 && o->propagation != 3 && o->propagation != 4) {
-        set_error("di_solve: the weighted selection needs propagation 3 or 4 (got %d)", o->propagation);
+    if (o->selection == 1 && o->propagation != 3 && o->propagation != 4 && o->propagation != 7) {
+        set_error("di_solve: the weighted selection needs propagation 3, 4 or 7 (got %d)", o->propagation);
         return DI_EINVAL;
     }
     return DI_OK;
@@ -1448,8 +1706,8 @@ di_status ensure_workspace(di_graph *g) {
                                         g->num_sms);
         const int64_t chunks = (n + kChunkNodes - 1) / kChunkNodes;
         g->grid_pushw = (int)std::max<int64_t>(1, std::min<int64_t>(push, (chunks + 7) / 8));
-        g->grid_push = occupancy_grid((const void *)k_push_async<double>, kPushThreads, kMaxHot * sizeof(double),
-                                      g->num_sms);
+        g->grid_push = occupancy_grid((const void *)k_push_async<double>, kPushThreads,
+                                      push_smem<double>(kMaxHot, kMaxWinR), g->num_sms);
         const int flat = occupancy_grid((const void *)k_pull_flat<double>, kLevelThreads, 0, g->num_sms);
         const int64_t fchunks = (g->nnz + kFlatEdges - 1) / kFlatEdges;
         g->grid_flat =
@@ -1517,6 +1775,15 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         DI_TRY(ensure_window(g, s));
         DI_TRY(fp64 ? prepare_tiled<double>(g) : prepare_tiled<float>(g));
     }
+    if (o.propagation == 3 || o.propagation == 7) {
+        // the frontier push's fluid window (its radius follows the graph's locality)
+        DI_TRY(ensure_window(g, s));
+        g->push_R = g->tune.push_window ? g->win_R : 0;
+    }
+    if (o.propagation == 7) {
+        DI_TRY(fp64 ? prepare_coop<double>(g) : prepare_coop<float>(g));
+        g->coop_timeout_ns = (unsigned long long)o.spin_limit * 1000ull;
+    }
     if (!o.timing) DI_TRY(build_level_graph(g, fp64, o.l2_window, o.propagation));
 
     // descriptor (the previous call has completed: every solve synchronises)
@@ -1542,6 +1809,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.iw = o.selection == 1 ? (fp64 ? (const void *)g->iw64 : (const void *)g->iw32) : nullptr;
     dh.dangling = o.dangling;
     dh.resweeps = o.propagation >= 3 ? o.resweeps : 0;
+    dh.win_R = (o.propagation == 3 || o.propagation == 7) ? g->push_R : 0;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
@@ -1593,7 +1861,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
                 DI_CUDA_TRY(cudaEventRecord(e[3], s));
-                if (o.propagation == 6) {
+                if (o.propagation == 7) {
+                    if (fp64) launch_coop<double>(g, s, 0, 0, 2, win, g->coop_timeout_ns);
+                    else launch_coop<float>(g, s, 0, 0, 2, win, g->coop_timeout_ns);
+                } else if (o.propagation == 6) {
                     if (fp64) launch_tiled<double>(g, s, 0, 0, 2, win);
                     else launch_tiled<float>(g, s, 0, 0, 2, win);
                 } else if (o.propagation == 5) {
@@ -1651,7 +1922,11 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     DI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
 
     di_status rc = DI_OK;
-    if (st.done == 3 || !std::isfinite(st.r_exact)) {
+    if (st.done == 4) {
+        rc = DI_ETIMEOUT;
+        set_error("di_solve: a grid barrier of the persistent level loop waited longer than %lld us",
+                  (long long)o.spin_limit);
+    } else if (st.done == 3 || !std::isfinite(st.r_exact)) {
         rc = DI_ENONFINITE;
         set_error("di_solve: residual is not finite (non-finite B or H0?)");
     } else if (st.done != 1) {
@@ -1677,7 +1952,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         } else {
             // per live level: select + one propagation kernel; the level that
             // finds the loop finished; the exact residuals
-            launches += (o.propagation >= 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
+            if (o.propagation == 7)   // one persistent launch per segment between exact residuals, plus the last
+                launches += (long long)st.recomputes + 1 + 1 + (long long)rk * st.recomputes;
+            else
+                launches += (o.propagation >= 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
         }
         if (refresh) launches += rk;        // final residual refresh
         stats->gpu_launches = launches;
@@ -1688,6 +1966,13 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         stats->body_iterations = st.body_iters;
         stats->select_seconds = t_sel;
         stats->red_ops = (int64_t)st.red_ops;
+        if (o.propagation == 7) {
+            // the persistent loop times its own phases on the device (%globaltimer), in
+            // either loop mode: selection phases and push phases of every pass
+            stats->level_seconds = (double)(st.t_scan_ns + st.t_push_ns) * 1e-9;
+            stats->select_seconds = (double)st.t_scan_ns * 1e-9;
+            stats->level_launches = (int32_t)st.passes;
+        }
     }
     return rc;
 }

@@ -19,9 +19,11 @@ namespace di {
 di_status check_tune(const di_tune *t, const char *who) {
     if (!t) { set_error("%s: NULL tune", who); return DI_EINVAL; }
     if (t->thread_max_deg < 1 || t->thread_max_deg > 1024 || t->warp_max_deg < t->thread_max_deg ||
-        t->warp_max_deg > (1 << 30) || t->push_ctas_per_sm < 0 || t->push_ctas_per_sm > 64) {
-        set_error("%s: bad shape (thread_max_deg %d in 1..1024, warp_max_deg %d >= it, push_ctas_per_sm %d in 0..64)",
-                  who, t->thread_max_deg, t->warp_max_deg, t->push_ctas_per_sm);
+        t->warp_max_deg > (1 << 30) || t->push_ctas_per_sm < 0 || t->push_ctas_per_sm > 64 ||
+        t->push_window < 0 || t->push_window > 1) {
+        set_error("%s: bad shape (thread_max_deg %d in 1..1024, warp_max_deg %d >= it, push_ctas_per_sm %d in 0..64, "
+                  "push_window %d in 0..1)",
+                  who, t->thread_max_deg, t->warp_max_deg, t->push_ctas_per_sm, t->push_window);
         return DI_EINVAL;
     }
     return DI_OK;
@@ -59,10 +61,12 @@ bool tune_cache_lookup(const char *path, const char *key, di_tune *out) {
         const char *p1 = std::strstr(line, "\"thread_max_deg\":");
         const char *p2 = std::strstr(line, "\"warp_max_deg\":");
         const char *p3 = std::strstr(line, "\"push_ctas_per_sm\":");
+        const char *p4 = std::strstr(line, "\"push_window\":");
         if (!p1 || !p2 || !p3) continue;
         t.thread_max_deg = (int32_t)std::strtol(p1 + 17, nullptr, 10);
         t.warp_max_deg = (int32_t)std::strtol(p2 + 15, nullptr, 10);
         t.push_ctas_per_sm = (int32_t)std::strtol(p3 + 19, nullptr, 10);
+        t.push_window = p4 ? (int32_t)std::strtol(p4 + 14, nullptr, 10) : 0;
         if (check_tune(&t, "tune cache") != DI_OK) { clear_error(); continue; }
         *out = t;
         found = true;
@@ -76,8 +80,8 @@ void tune_cache_store(const char *path, const char *key, const di_tune &t, doubl
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f, "{\"key\": \"%s\", \"thread_max_deg\": %d, \"warp_max_deg\": %d, \"push_ctas_per_sm\": %d, "
-                    "\"seconds\": %.6e}\n",
-                 key, t.thread_max_deg, t.warp_max_deg, t.push_ctas_per_sm, seconds);
+                    "\"push_window\": %d, \"seconds\": %.6e}\n",
+                 key, t.thread_max_deg, t.warp_max_deg, t.push_ctas_per_sm, t.push_window, seconds);
     std::fclose(f);
 }
 
@@ -132,8 +136,10 @@ extern "C" DI_API di_status di_autotune(di_graph *g, const double *B, double d, 
         ~FreeH() { cudaFree(p); }
     } fh{H};
     const int occ_per_sm = std::max(1, g->grid_push / std::max(1, g->num_sms));
-    di_tune cand[16];
-    const int nc = tune_candidates(cand, 16);
+    di_tune cand[17];
+    int nc = tune_candidates(cand, 16);
+    // the frontier push of propagations 3 and 7 may keep a fluid window per tile
+    if (o.propagation == 3 || o.propagation == 7) cand[nc++] = di_tune{kThreadMaxDeg, kWarpMaxDeg, 0, 1};
     di_tune win = g->tune;
     double win_s = 1e300;
     for (int c = 0; c < nc; ++c) {

@@ -53,7 +53,7 @@ def test_version_and_defaults(lib):
     assert o.alpha == 1.5 and o.fluid_fp64 == 0 and o.recompute_every == 0 and o.recompute_drop == 1024.0
     assert o.warm_fallback == 1 and o.max_levels == 100000
     # the fields after the double keep their place in the C layout
-    assert o.propagation == 3 and o.push_ratio == 8 and o.selection == 0 and o.spin_limit == 1 << 26
+    assert o.propagation == 3 and o.push_ratio == 8 and o.selection == 0 and o.spin_limit == 1 << 20
     assert o.resweeps == 0   # the last field, after the stream pointer
 
 

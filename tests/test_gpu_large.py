@@ -48,7 +48,7 @@ def check(rp, col, b, x, h, st, tol):
     return err
 
 
-@pytest.mark.parametrize("prop", [3, 4, 5, 6])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("every", [8, 0])
 def test_three_source_blocks_match_the_oracle(web8m, prop, every):
     rp, col, b, x, g = web8m

@@ -29,8 +29,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def solve(rp, col, b, tol, fp64=False, h0=None, want_f=True, allow=(di.DI_OK,), **opt):
+def solve(rp, col, b, tol, fp64=False, h0=None, want_f=True, allow=(di.DI_OK,), window=False, **opt):
     g = di.Graph.create(rp, col)
+    if window:   # the frontier push's shared-memory fluid window (propagations 3, 7)
+        t = di.tune_default()
+        t.push_window = 1
+        di.set_tune(g, t)
     B = dev(b)
     H = dev(h0) if h0 is not None else torch.zeros(len(b), dtype=torch.float64, device="cuda")
     F = torch.zeros_like(H) if want_f else None
@@ -348,7 +352,7 @@ def test_device_resident_csr_input(web10k):
 
 # ---------------------------------------------------------------- every propagation mode
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_parity_every_propagation_mode(web10k, prop, fp64):
     rp, col, b, x = web10k
@@ -359,8 +363,8 @@ def test_parity_every_propagation_mode(web10k, prop, fp64):
         check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [3, 4, 5, 6])
-@pytest.mark.parametrize("resweeps", [0, 2])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6, 7])
+@pytest.mark.parametrize("resweeps", [0, 1, 2])
 def test_parity_every_resweep_count(web10k, prop, resweeps):
     # re-selections at the same threshold change the order of the diffusions,
     # not the limit (Sec. 2: any order that keeps diffusing every node)
@@ -384,7 +388,7 @@ def test_resweeps_out_of_range_are_rejected(web10k):
     g.close()
 
 
-@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_personalised_sparse_levels_every_mode(prop):
     # a personalised right-hand side keeps the early frontiers tiny (scatter levels)
     rp, col = gg.generate(gg.GraphSpec(n=30000, mean_deg=9, seed=8))
@@ -396,7 +400,7 @@ def test_personalised_sparse_levels_every_mode(prop):
     check_stop(rp, col, b, h, st, tol)
 
 
-@pytest.mark.parametrize("prop", [1, 3, 5, 6])
+@pytest.mark.parametrize("prop", [1, 3, 5, 6, 7])
 def test_timing_mode_matches(web10k, prop):
     rp, col, b, x = web10k
     tol = 1e-8 * b.sum()
@@ -510,7 +514,7 @@ def test_solve_on_two_source_blocks_meets_the_stop(web5m):
 
 # ---------------------------------------------------------------- push shapes and the autotuner
 
-@pytest.mark.parametrize("prop", [3, 4, 5, 6])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("shape", [(1, 1, 0), (4, 64, 1), (32, 32, 0), (1024, 1 << 30, 2)])
 def test_parity_every_push_shape(web10k, prop, shape):
     rp, col, b, x = web10k
@@ -555,7 +559,7 @@ def test_autotune_keeps_a_shape_and_caches_it(web10k, tmp_path):
 
 # ---------------------------------------------------------------- weighted selection (Sec. 2.4 score)
 
-@pytest.mark.parametrize("prop", [3, 4])
+@pytest.mark.parametrize("prop", [3, 4, 7])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_weighted_selection_parity(web10k, prop, fp64):
     rp, col, b, x = web10k
@@ -639,7 +643,7 @@ def assert_completed_residual_close(f_gpu, f_cpu, rp, col, b, h):
     assert np.all(err <= bound + 1e-300), f"max excess {np.max(err - bound):.3e}"
 
 
-@pytest.mark.parametrize("prop", [3, 4, 6])
+@pytest.mark.parametrize("prop", [3, 4, 6, 7])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
     rp, col, b, x = web10k_completed
@@ -658,7 +662,7 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     # a personalised right-hand side (sparse early levels)
     bp = gg.personalised_b(len(b), 1234)
     xp = od.d_iteration(rp, col, bp, D, tol=1e-14 * bp.sum(), dangling=True).H
-    for prop in (4, 6):
+    for prop in (4, 6, 7):
         h, st, _, _ = solve(rp, col, bp, 1e-8 * bp.sum(), propagation=prop, dangling=1)
         assert np.abs(h - xp).sum() <= 1e-6 * np.abs(xp).sum()
         check_stop_completed(rp, col, bp, h, st, 1e-8 * bp.sum())
@@ -674,7 +678,7 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     check_stop_completed(rp, col, b, h, st, 1e-8 * b.sum())
 
 
-@pytest.mark.parametrize("prop", [4, 6])
+@pytest.mark.parametrize("prop", [4, 6, 7])
 def test_dangling_completion_on_two_source_blocks(web5m, prop):
     # more than 2^22 nodes: the dangling sum of the exact residual spans both blocks
     rp, col, b = web5m
@@ -723,7 +727,7 @@ def test_dangling_completion_edge_cases(case):
         assert x[0] == pytest.approx(0.15 / (1 - D), rel=1e-13)
     for fp64, rel in ((False, 1e-6), (True, 1e-11)):
         tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
-        for prop in (3, 6):
+        for prop in (3, 6, 7):
             h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, dangling=1)
             assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
             check_stop_completed(rp, col, b, h, st, tol)
@@ -737,9 +741,10 @@ def ring_graph(n, reach):
     return csr_from_edges(n, edges)
 
 
+@pytest.mark.parametrize("prop", [3, 6, 7])
 @pytest.mark.parametrize("case", ["ring", "random", "ragged", "tiny", "hub_and_ring"])
 @pytest.mark.parametrize("fp64", [False, True])
-def test_tiled_level_cases(case, fp64):
+def test_fluid_window_cases(prop, case, fp64):
     # ring: every target lies in the shared-memory window (wrap-around edges
     # at both ends of the node range go to global memory); random: no
     # locality, the window radius is 0; ragged: N not a multiple of the chunk;
@@ -761,24 +766,62 @@ def test_tiled_level_cases(case, fp64):
     b = rng.random(len(rp) - 1)
     x = oracle_x(rp, col, b)
     tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
-    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=6)
+    h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, window=True)
     assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
     f_cpu = check_stop(rp, col, b, h, st, tol)
     assert_residual_close(f, f_cpu, rp, col, b, h)
     assert st.red_ops >= 0
 
 
-def test_tiled_level_issues_fewer_reductions_than_edges():
-    # on a graph whose edges all stay within the window, the level kernel's
-    # global reductions are the coalesced flushes only (one per sector of 8
-    # FP32 words) - far fewer than the elementary diffusions it performs
+def test_fluid_window_issues_fewer_reductions_than_edges():
+    # on a graph whose edges all stay within the window, the push's global
+    # reductions are mostly the coalesced flushes (one per sector of 8 FP32
+    # words) - far fewer than the elementary diffusions it performs
     rp, col = ring_graph(200_000, 8)
     b = gg.uniform_b(200_000, D)
     tol = 1e-8 * b.sum()
-    h, st, _, _ = solve(rp, col, b, tol, propagation=6, want_f=False)
     x = oracle_x(rp, col, b)
-    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
-    assert 0 < st.red_ops < st.edge_diffusions / 4, (st.red_ops, st.edge_diffusions)
-    # the other propagations do not count
+    for prop in (3, 6, 7):
+        h, st, _, _ = solve(rp, col, b, tol, propagation=prop, want_f=False, window=True)
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+        assert 0 < st.red_ops < st.edge_diffusions / 4, (prop, st.red_ops, st.edge_diffusions)
+    # without the window every edge is one scattered reduction (the ring has no hot targets)
     _, st3, _, _ = solve(rp, col, b, tol, propagation=3, want_f=False)
-    assert st3.red_ops == 0
+    assert st3.red_ops == st3.edge_diffusions
+    # the warp-tile push does not count
+    _, st4, _, _ = solve(rp, col, b, tol, propagation=4, want_f=False)
+    assert st4.red_ops == 0
+
+
+# ---------------------------------------------------------------- propagation 7: persistent level loop
+
+def test_persistent_loop_times_its_phases(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    for timing in (0, 1):
+        h, st, _, _ = solve(rp, col, b, tol, propagation=7, resweeps=1, timing=timing)
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+        check_stop(rp, col, b, h, st, tol)
+        # device-timed phases: every selection pass is counted, the push phases
+        # take part of the level time, and the whole loop fits in the solve
+        assert st.level_launches == st.body_iterations
+        assert 0 < st.select_seconds < st.level_seconds <= st.seconds
+
+
+def test_persistent_loop_barrier_timeout_returns_an_error(web10k):
+    # a zero bound on the grid barriers' wait: the waiting CTAs give up, the
+    # solve returns DI_ETIMEOUT (no fault, no hang) and the context stays usable
+    rp, col, b, x = web10k
+    g = di.Graph.create(rp, col)
+    B = dev(b)
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    rc, st = di.di_solve(g, B, D, 1e-8 * b.sum(), H, None, di.opts_default(propagation=7, spin_limit=0),
+                         allow=(di.DI_ETIMEOUT,))
+    assert rc == di.DI_ETIMEOUT and "grid barrier" in di.last_error()
+    rc, st = di.di_solve(g, B, D, 1e-8 * b.sum(), H, None, di.opts_default(propagation=7))
+    assert rc == di.DI_OK
+    assert np.abs(H.cpu().numpy() - x).sum() <= 1e-6 * np.abs(x).sum()
+    with pytest.raises(di.DiError) as e:
+        di.di_solve(g, B, D, 1e-8, H, None, di.opts_default(propagation=7, spin_limit=-1))
+    assert e.value.status == di.DI_EINVAL
+    g.close()
