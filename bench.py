@@ -4,13 +4,18 @@
 One step = one complete solve of X = P X + B (PageRank form, d = 0.85) by the
 threshold-frontier D-iteration, from F = B to the exact FP64 stop
 |B + P H - H|_1 <= 1e-8 |B|_1, on a seeded synthetic web-like graph.
-Metric: edge diffusions per second (the paper's elementary cost unit,
-Sec. 2.4) and time to tolerance.
+Metric: solves per second to that tolerance (the reciprocal of the time to
+tolerance, summed over replicas); the line also carries the time to
+tolerance, edge diffusions per second (the paper's elementary cost unit,
+Sec. 2.4) and the normalised iterations (edge diffusions / L).  The default
+run adds the N = 2^24 stress workload (stress_16m) and the learned warm start
+as specified (warmstart_cfg5: 200 training graphs, 32 held-out N = 3e6
+graphs), each checked against the CPU oracle.
 
 Default workload: N = 1,000,000 nodes, mean out-degree 10 (non-dangling),
 10% dangling, +-64 locality window, FP32 fluid with FP64 history, exact
-FP64 residual every 8 levels.  Inputs are resident in HBM for the device
-timing; L2 is flushed (256 MiB write) before every timed step.
+FP64 residual when |F|_1 fell 1024-fold.  Inputs are resident in HBM for the
+device timing; L2 is flushed (256 MiB write) before every timed step.
 
 Arms:
   --impl native     (default) the CUDA library through its C ABI;
@@ -53,7 +58,7 @@ WORKLOADS = {
 # algorithmic bytes of the level kernel: per edge diffusion, per node
 # diffusion, and per node scanned (the fluid read of the selection)
 EDGE_BYTES = {"f32": 12, "f64": 20}   # 4 B column index + target fluid read + write
-NODE_BYTES = {"f32": 36, "f64": 48}   # row_ptr pair, fluid exchange, FP64 history RMW, scale
+NODE_BYTES = {"f32": 40, "f64": 48}   # row_ptr pair, fluid exchange, FP64 history RMW, frontier write + read
 SCAN_BYTES = {"f32": 4, "f64": 8}     # fluid read of every node, every level
 
 
@@ -91,6 +96,8 @@ def parse():
     p.add_argument("--ws-eval", type=int, default=32, help="warm start: held-out evaluation graphs")
     p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
     p.add_argument("--ws-lr", type=float, default=1e-3, help="warm start: Adam learning rate")
+    p.add_argument("--no-stress", action="store_true", help="skip the N=2^24 stress sub-object")
+    p.add_argument("--no-cfg5", action="store_true", help="skip the learned warm-start study sub-object")
     p.add_argument("--host-loop", action="store_true",
                    help="host-driven levels with per-kernel events (profilers cannot see kernels in "
                         "graphs with conditional nodes)")
@@ -209,10 +216,11 @@ def cpu_baseline(rp, col, b, tol, dangling=False):
     t0 = time.perf_counter()
     r = od.d_iteration(rp, col, b, D, tol=tol, dangling=dangling)
     dt = time.perf_counter() - t0
-    return {"value": r.edge_diffusions / dt, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"one full sequential FP64 solve of the same graph to the same tol "
                       f"({r.levels} levels, {r.edge_diffusions} edge diffusions, {dt:.2f} s)",
-            "seconds": dt}
+            "seconds": dt, "edge_diffusions_per_s": r.edge_diffusions / dt,
+            "normalised_iterations": r.edge_diffusions / len(col)}
 
 
 def run_reference(args, world, rank):
@@ -237,16 +245,18 @@ def run_reference(args, world, rank):
         r = od.d_iteration(rp, col, b, D, tol=tol)
         secs += time.perf_counter() - t0
         edges += r.edge_diffusions
-    value = edges / secs
-    line = {"impl": "reference", "metric": "edge_diffusions_per_s", "value": value,
-            "unit": "edge_diffusions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+    value = args.steps / secs
+    line = {"impl": "reference", "metric": "solves_per_s_to_tol", "value": value,
+            "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "n": spec.n, "nnz": int(len(col)), "tol": tol,
                        "oracle": "sequential cyclic-threshold D-iteration, FP64, 1 core"},
-            "cpu_baseline": {"value": value, "unit": "edge_diffusions/s", "cores": 1, "kind": "oracle",
+            "time_to_tol_ms": 1e3 * secs / args.steps, "edge_diffusions_per_s": edges / secs,
+            "normalised_iterations": edges / args.steps / len(col),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full solves of the workload"},
-            "e2e": {"value": value, "unit": "edge_diffusions/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -320,51 +330,220 @@ def run_reference_multi(args, desc):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
-def warm_start_leg(args, g, B, tol, stream, flush, n_train=24, epochs=8):
-    """Time to tolerance of this workload's graph from the learned warm start
-    (features, network, F0 and solve, all timed) against the zero start.  The
-    network is trained first on n_train other seeded graphs (N log-uniform in
-    [1e5, 1e6], m = 10) with targets from the plain solver."""
+def phase_roofline(di, g, B, H, tol, opts, prec, n, flush, stream, workload, reps=3):
+    """Roofline of the level kernels of propagation 3 (selection, then the
+    asynchronous push), with every phase timed on the device: the persistent
+    level loop (propagation 7) runs the same selection and push code and
+    reads %globaltimer at its grid barriers, so the times are those of the
+    phases inside a running solve, with no host launch in between.  Each
+    phase's time includes its closing grid barrier, which makes the
+    fractions conservative.  Algorithmic bytes: 4 B (FP64: 8 B) of fluid per
+    node and selection pass; 12 B (20 B) per edge diffusion and 40 B (48 B)
+    per node diffusion for the push."""
+    popt = di.opts_copy(opts, propagation=7, timing=0)
+    sel_s = push_s = 0.0
+    passes = nodes = edges = reds = 0
+    for _ in range(reps):
+        flush.zero_()
+        _, st = di.di_solve(g, B, D, tol, H, None, popt)
+        sel_s += st.select_seconds
+        push_s += st.level_seconds - st.select_seconds
+        passes += st.level_launches
+        nodes += st.node_diffusions
+        edges += st.edge_diffusions
+        reds += st.red_ops
+    peak, peak_src = measured_hbm_peak()
+    sel_b = SCAN_BYTES[prec] * n * passes
+    push_b = EDGE_BYTES[prec] * edges + NODE_BYTES[prec] * nodes
+    achieved = (sel_b + push_b) / (sel_s + push_s) / 1e9
+    traffic = level_traffic(workload, prec, 3) if not (opts.selection or opts.dangling) and opts.resweeps == 0 \
+        else None
+    out = {"bound": "hbm", "kernel": "selection + asynchronous push of a level (propagation 3's code)",
+           "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": f"{peak_src} (hbm_gbs)", "traffic": traffic,
+           "alg_bytes_per_launch": (sel_b + push_b) / max(passes, 1),
+           "avg_launch_us": 1e6 * (sel_s + push_s) / max(passes, 1),
+           "phases": {"select": {"seconds": sel_s, "alg_bytes": sel_b, "achieved": sel_b / sel_s / 1e9,
+                                 "frac": sel_b / sel_s / 1e9 / peak},
+                      "push": {"seconds": push_s, "alg_bytes": push_b, "achieved": push_b / push_s / 1e9,
+                               "frac": push_b / push_s / 1e9 / peak}},
+           "passes": passes, "solves": reps,
+           "measured_by": "device %globaltimer at the grid barriers of the persistent level loop "
+                          "(propagation 7: the same selection and push code, one launch per segment)"}
+    if reds:
+        red_peak, _ = di.probe_l2("red_f32" if prec == "f32" else "red_f64", 1 << 24, 1 << 28, stream)
+        out_red = {"achieved": reds / push_s, "peak": red_peak, "unit": "red sectors/s",
+                   "frac": reds / push_s / red_peak, "red_sectors_per_edge": reds / max(edges, 1),
+                   "peak_source": "di_probe_l2 scattered red over 2^24 words, this run",
+                   "kernel": "push phase"}
+        return out, out_red
+    return out, None
+
+
+def stress_leg(args, di, stream, flush):
+    """The N = 2^24, m = 16, +-256 window workload: FP32 fluid, FP64 history, an
+    exact FP64 residual every 8 levels (the workload's schedule), one
+    re-selection per level (the fastest measured setting); time to
+    tolerance, the phase roofline, and the error of H against the oracle's X
+    (the oracle solved to 1e-10 |B|_1, so its own error is <= 6.7e-10 |X|_1)."""
     import torch
-    from paper_1202_6168_gb300 import binding as di
+    from oracle import diter as od
+    sp = gg.STRESS_16M
+    t0 = time.perf_counter()
+    rp, col = gg.generate(sp)
+    gen_s = time.perf_counter() - t0
+    n, nnz = sp.n, int(len(col))
+    b = gg.uniform_b(n, D)
+    tol = 1e-8 * b.sum()
+    g = di.Graph.create(rp, col, stream=stream)
+    B = torch.from_numpy(b).cuda()
+    H = torch.zeros(n, dtype=torch.float64, device="cuda")
+    opts = di.opts_default(stream=stream.cuda_stream, recompute_every=8, recompute_drop=0.0, resweeps=1)
+    di.di_solve(g, B, D, tol, H, None, opts)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times, st = [], None
+    for _ in range(3):
+        flush.zero_()
+        ev[0].record(stream)
+        _, st = di.di_solve(g, B, D, tol, H, None, opts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    ms = statistics.median(times)
+    roof, red = phase_roofline(di, g, B, H, tol, opts, "f32", n, flush, stream, "stress-16m")
+    h = H.cpu().numpy()
+    g.close()
+    del B, H
+    t0 = time.perf_counter()
+    x = od.d_iteration(rp, col, b, D, tol=1e-10 * b.sum()).H
+    oracle_s = time.perf_counter() - t0
+    _, r_cpu = od.residual(rp, col, b, D, h)
+    out = {"workload": WORKLOADS["stress-16m"][1], "n": n, "nnz": nnz, "time_to_tol_ms": ms,
+           "solves_per_s": 1e3 / ms, "edge_diffusions_per_s": st.edge_diffusions / (ms * 1e-3),
+           "normalised_iterations": st.edge_diffusions / nnz, "levels": st.levels,
+           "passes": st.body_iterations, "recomputes": st.recomputes,
+           "options": {"propagation": "asynchronous push (3)", "resweeps": 1, "recompute_every": 8,
+                       "fluid": "f32", "history": "f64"},
+           "roofline": roof,
+           "check": {"rel_l1_err_vs_oracle_x": float(np.abs(h - x).sum() / np.abs(x).sum()),
+                     "resid_l1_oracle_fp64": r_cpu, "tol": tol, "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
+                     "oracle_tol": "1e-10 |B|_1", "oracle_seconds": oracle_s},
+           "setup_seconds": {"generate": gen_s}}
+    if red:
+        out["l2_red"] = red
+    return out
+
+
+def warmstart_study(args, di, stream, flush, n_train, n_eval, epochs, lr, reps=2, warmup=1):
+    """The learned warm start as the workload specifies it: train on n_train
+    seeded graphs (N log-uniform in [1e5, 1e6], m = 10) with targets from the
+    plain solver, then time to |F|_1 <= 1e-8 |B|_1 on n_eval held-out N = 3e6
+    graphs - warm (features + network + F0 + solve, all timed) against the
+    zero start on the same GPU - with the fallback count."""
+    import torch
+    t_gen = time.perf_counter()
     graphs, Bs, Xs = [], [], []
+    train_nodes = 0
     for sp in gg.warmstart_specs("train", n_train):
         rp, col = gg.generate(sp)
-        gt = di.Graph.create(rp, col, stream=stream)
+        g = di.Graph.create(rp, col, stream=stream)
         b = torch.full((sp.n,), (1.0 - D) / sp.n, dtype=torch.float64, device="cuda")
         h = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
-        di.di_solve(gt, b, D, 1e-8 * (1.0 - D), h, None, di.opts_default(stream=stream.cuda_stream))
-        graphs.append(gt)
+        di.di_solve(g, b, D, 1e-8 * (1.0 - D), h, None, di.opts_default(stream=stream.cuda_stream))
+        graphs.append(g)
         Bs.append(b)
         Xs.append(h)
+        train_nodes += sp.n
+    t_gen = time.perf_counter() - t_gen
     model = di.Model.create(7)
-    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=epochs, batch=65536, lr=1e-3,
+    t0 = time.perf_counter()
+    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=epochs, batch=65536, lr=lr,
                                                              stream=stream.cuda_stream))
-    for gt in graphs:
-        gt.close()
-    H = torch.zeros_like(B)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for g in graphs:
+        g.close()
+    del Bs, Xs
+    rows = []
+    opts_c = di.opts_default(stream=stream.cuda_stream)
+    opts_w = di.opts_default(stream=stream.cuda_stream, warm_start=1)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    res = {}
-    for label in ("cold", "warm"):
-        o = di.opts_default(stream=stream.cuda_stream, warm_start=1 if label == "warm" else 0)
-        times = []
-        for rep in range(3 + max(args.steps, 1)):
-            flush.zero_()
-            ev[0].record(stream)
-            if label == "warm":
-                model.infer(g, B, H, stream)
-            _, st = di.di_solve(g, B, D, tol, H, None, o)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            if rep >= 3:
-                times.append(ev[0].elapsed_time(ev[1]))
-        res[label] = {"ms": statistics.median(times), "edge_diffusions": st.edge_diffusions, "levels": st.levels,
-                      "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1}
+    infer_parts = None
+    for sp in gg.warmstart_specs("eval", n_eval):
+        rp, col = gg.generate(sp)
+        g = di.Graph.create(rp, col, stream=stream)
+        n = sp.n
+        b = torch.full((n,), (1.0 - D) / n, dtype=torch.float64, device="cuda")
+        tol = 1e-8 * (1.0 - D)
+        H = torch.zeros(n, dtype=torch.float64, device="cuda")
+        res = {}
+        for label in ("cold", "warm"):
+            times = []
+            for rep in range(warmup + reps):
+                flush.zero_()
+                ev[0].record(stream)
+                if label == "warm":
+                    model.infer(g, b, H, stream)
+                    _, st = di.di_solve(g, b, D, tol, H, None, opts_w)
+                else:
+                    _, st = di.di_solve(g, b, D, tol, H, None, opts_c)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                if rep >= warmup:
+                    times.append(ev[0].elapsed_time(ev[1]))
+            res[label] = {"ms": statistics.median(times), "edges": st.edge_diffusions, "levels": st.levels,
+                          "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1, "resid": st.resid_l1}
+        if infer_parts is None:
+            # the inference parts alone on the first held-out graph: features and the network
+            feat = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+            yv = torch.empty(n, dtype=torch.float32, device="cuda")
+            t_feat, t_fwd = [], []
+            for rep in range(5):
+                flush.zero_()
+                ev[0].record(stream)
+                model.features(g, b, feat, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_feat.append(ev[0].elapsed_time(ev[1]))
+                flush.zero_()
+                ev[0].record(stream)
+                model.forward(feat, n, yv, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_fwd.append(ev[0].elapsed_time(ev[1]))
+            fwd_s = statistics.median(t_fwd[1:]) * 1e-3
+            peak, peak_src = measured_hbm_peak()
+            infer_parts = {"features_ms": statistics.median(t_feat[1:]), "network_ms": fwd_s * 1e3,
+                           "network_roofline": {"bound": "hbm", "kernel": "k_mlp_fwd (BF16 mma.sync)",
+                                                "achieved": (36 + 4) * n / fwd_s / 1e9, "peak": peak,
+                                                "unit": "GB/s", "frac": (36 + 4) * n / fwd_s / 1e9 / peak,
+                                                "peak_source": f"{peak_src} (hbm_gbs)",
+                                                "tflops": 2 * (16 * 64 + 64 * 64 + 64) * n / fwd_s / 1e12,
+                                                "bytes_per_node": "36 B features in, 4 B prediction out"}}
+            del feat, yv
+        rows.append(res)
+        g.close()
+        del H, b
+    cold = [r["cold"]["ms"] for r in rows]
+    warm = [r["warm"]["ms"] for r in rows]
+    ratios = [c / w for c, w in zip(cold, warm)]
     model.close()
-    res["speedup"] = res["cold"]["ms"] / res["warm"]["ms"]
-    res["train"] = {"graphs": n_train, "epochs": epochs, "loss_last_epoch": loss}
-    res["timed"] = "warm: features + network + F0 + solve; cold: solve; L2 flushed before each"
-    return res
+    return {"workload": WORKLOADS["warmstart"][1], "train_graphs": n_train, "train_nodes": train_nodes,
+            "eval_graphs": n_eval, "epochs": epochs, "lr": lr, "tol": "1e-8 |B|_1",
+            "timed": "warm: features + network + F0 + solve; cold: solve; L2 flushed before each",
+            "cold_ms": statistics.mean(cold), "warm_ms": statistics.mean(warm),
+            "speedup": statistics.mean(cold) / statistics.mean(warm),
+            "speedup_per_graph": {"mean": statistics.mean(ratios), "min": min(ratios), "max": max(ratios),
+                                  "stdev": statistics.pstdev(ratios)},
+            "fallbacks": sum(1 - r["warm"]["warm_used"] for r in rows),
+            "f0_over_b_mean": statistics.mean(r["warm"]["f0_over_b"] for r in rows),
+            "edges_cold": statistics.mean(r["cold"]["edges"] for r in rows),
+            "edges_warm": statistics.mean(r["warm"]["edges"] for r in rows),
+            "levels_cold": statistics.mean(r["cold"]["levels"] for r in rows),
+            "levels_warm": statistics.mean(r["warm"]["levels"] for r in rows),
+            "inference": infer_parts,
+            "train": {"loss_last_epoch": loss, "seconds": t_train, "generate_and_solve_s": t_gen},
+            "per_graph": rows}
 
 
 def run_native(args, world, rank, local):
@@ -445,55 +624,47 @@ def run_native(args, world, rank, local):
     last = st
 
     secs_max, edges_all = aggregate_over_ranks(secs, edges, world, "cuda")
-    value = edges_all / secs_max
+    solves_all = world * args.steps   # every rank makes args.steps solves
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        # roofline of the dominant kernel (the push), from CUDA events around
-        # every push launch of instrumented solves (host-driven levels)
-        topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
-                               alpha=opts.alpha, recompute_every=opts.recompute_every,
-                               recompute_drop=opts.recompute_drop,
-                               l2_window=opts.l2_window, propagation=opts.propagation,
-                               push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
-                               selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps)
-        te = tn = tred = 0
-        tpush = trec = tsel = 0.0
-        npush = 0
-        reps = min(3, max(args.steps, 1))
-        for _ in range(reps):
-            flush.zero_()
-            _, ts = di.di_solve(g, B, D, tol, H, None, topt)
-            te += ts.edge_diffusions
-            tn += ts.node_diffusions
-            tpush += ts.level_seconds
-            trec += ts.recompute_seconds
-            tsel += ts.select_seconds
-            npush += ts.level_launches
-            tred += ts.red_ops
-        alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
-        achieved = alg_bytes / tpush / 1e9
-        peak, peak_src = measured_hbm_peak()
-        # the recorded captures ran with the default selection and zero dangling columns
-        traffic = (level_traffic(args.workload, prec, opts.propagation)
-                   if not (opts.selection or opts.dangling) else None)
-        extras["roofline"] = {"bound": "hbm", "kernel": f"k_level<{'double' if args.fp64 else 'float'}> (scan + push)",
-                              "achieved": achieved, "peak": peak, "unit": "GB/s",
-                              "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
-                              "traffic": traffic,
-                              "alg_bytes_per_launch": alg_bytes / max(npush, 1),
-                              "avg_launch_us": 1e6 * tpush / max(npush, 1),
-                              "seconds": {"level": tpush, "of_which_selection": tsel,
-                                          "recompute_and_empty_launches": trec},
-                              "measured_by": "CUDA events around every level kernel of host-driven solves"}
-        if tred > 0:
-            # L2 reduction sectors the level kernel issued against the measured ceiling of
-            # scattered red.global.add.f32 (a 2^24-word array, the fluid of a 2^24-node graph)
-            red_peak, _ = di.probe_l2("red_f32", 1 << 24, 1 << 28, stream)
-            extras["l2_red"] = {"achieved": tred / tpush, "peak": red_peak, "unit": "red sectors/s",
-                                "frac": tred / tpush / red_peak, "red_sectors_per_edge": tred / max(te, 1),
-                                "peak_source": "di_probe_l2 red_f32 over 2^24 words, this run",
-                                "kernel": "level kernels (selection + push), host-driven timing"}
+        if opts.propagation in (3, 7) and not args.fp64:
+            # the dominant kernels (selection + push), phases timed on the device
+            extras["roofline"], red = phase_roofline(di, g, B, H, tol, opts, prec, n, flush, stream, args.workload)
+            if red:
+                extras["l2_red"] = red
+        else:
+            # other modes: CUDA events around every level kernel of host-driven solves
+            topt = di.opts_default(fluid_fp64=opts.fluid_fp64, stream=stream.cuda_stream, timing=1,
+                                   alpha=opts.alpha, recompute_every=opts.recompute_every,
+                                   recompute_drop=opts.recompute_drop,
+                                   l2_window=opts.l2_window, propagation=opts.propagation,
+                                   push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
+                                   selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps)
+            te = tn = 0
+            tpush = trec = tsel = 0.0
+            npush = 0
+            reps = min(3, max(args.steps, 1))
+            for _ in range(reps):
+                flush.zero_()
+                _, ts = di.di_solve(g, B, D, tol, H, None, topt)
+                te += ts.edge_diffusions
+                tn += ts.node_diffusions
+                tpush += ts.level_seconds
+                trec += ts.recompute_seconds
+                tsel += ts.select_seconds
+                npush += ts.level_launches
+            alg_bytes = EDGE_BYTES[prec] * te + NODE_BYTES[prec] * tn + SCAN_BYTES[prec] * n * npush
+            achieved = alg_bytes / tpush / 1e9
+            peak, peak_src = measured_hbm_peak()
+            extras["roofline"] = {"bound": "hbm", "kernel": "level kernels (selection + push)",
+                                  "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "peak_source": f"{peak_src} (hbm_gbs)",
+                                  "traffic": None, "alg_bytes_per_launch": alg_bytes / max(npush, 1),
+                                  "avg_launch_us": 1e6 * tpush / max(npush, 1),
+                                  "seconds": {"level": tpush, "of_which_selection": tsel,
+                                              "recompute_and_empty_launches": trec},
+                                  "measured_by": "CUDA events around every level kernel of host-driven solves"}
         # end to end through the host-buffer entry point: H2D of B, D2H of H
         Bh = torch.from_numpy(b).pin_memory()
         Hh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -508,11 +679,9 @@ def run_native(args, world, rank, local):
             _, es = di.di_solve_host(g, Bh.data_ptr(), D, tol, Hh.data_ptr(), None, opts)
             e_secs += time.perf_counter() - t0
             e_edges += es.edge_diffusions
-        if args.workload == "web-1m" and not args.no_cpu:
-            extras["warm_start"] = warm_start_leg(args, g, B, tol, stream, flush)
-        extras["e2e"] = {"value": e_edges / e_secs, "unit": "edge_diffusions/s",
+        extras["e2e"] = {"value": args.steps / e_secs, "unit": "solves/s",
                          "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
-                         "ms_per_step": 1e3 * e_secs / args.steps,
+                         "ms_per_step": 1e3 * e_secs / args.steps, "edge_diffusions_per_s": e_edges / e_secs,
                          "api": "di_solve_host (pinned host B in, H out; graph resident)"}
         if not args.no_cpu:
             # error of the result against the exact residual bound, and the CPU oracle
@@ -525,18 +694,23 @@ def run_native(args, world, rank, local):
                                "err_bound_rel": r_cpu / (1 - D) / max(h.sum(), 1e-300)}
             # the oracle spreads a dangling diffusion over all N nodes one by one,
             # which is too slow beyond small graphs: no oracle solve then
-            if n <= (100_000 if dang else 4_000_000):
-                # error against the oracle's FP64 solution (solved to 1e-14 |B|_1)
-                x = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum(), dangling=dang).H
-                extras["check"]["rel_l1_err_vs_oracle_x"] = float(np.abs(h - x).sum() / np.abs(x).sum())
             if not dang or n <= 100_000:
+                # error against the oracle's FP64 solution (solved to 1e-12 |B|_1)
+                x = od.d_iteration(rp, col, b, D, tol=1e-12 * b.sum(), dangling=dang).H
+                extras["check"]["rel_l1_err_vs_oracle_x"] = float(np.abs(h - x).sum() / np.abs(x).sum())
                 extras["cpu_baseline"] = cpu_baseline(rp, col, b, tol, dang)
+        if args.workload == "web-1m" and not args.no_stress:
+            extras["stress_16m"] = stress_leg(args, di, stream, flush)
+        if args.workload == "web-1m" and not args.no_cfg5:
+            extras["warmstart_cfg5"] = warmstart_study(args, di, stream, flush, args.ws_train, args.ws_eval,
+                                                       args.ws_epochs, args.ws_lr)
 
     if rank == 0:
         info = g.info()
-        line = {"metric": "edge_diffusions_per_s", "value": value, "unit": "edge_diffusions/s",
+        ms = 1e3 * secs_max / args.steps
+        line = {"metric": "solves_per_s_to_tol", "value": solves_all / secs_max, "unit": "solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * secs_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": prec, "data": "synthetic",
                 "config": {"workload": desc, "n": n, "nnz": nnz, "n_dangling": info["n_dangling"],
                            "n_hot_targets": info["n_hot"], "d": D, "tol": tol, "tol_rel_b_l1": 1e-8,
@@ -558,10 +732,11 @@ def run_native(args, world, rank, local):
                            "dangling": ["zero columns", "uniform 1/N completion"][opts.dangling],
                            "level_loop": "host-driven" if args.host_loop else "CUDA graph (WHILE/IF nodes)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "time_to_tol_ms": 1e3 * secs_max / args.steps,
+                "time_to_tol_ms": ms,
+                "edge_diffusions_per_s": edges_all / secs_max,
                 "edge_diffusions_per_step": edges / args.steps,
                 "normalised_iterations": edges / args.steps / nnz,
-                "levels": levels[-1], "recomputes": last.recomputes,
+                "levels": levels[-1], "passes": last.body_iterations, "recomputes": last.recomputes,
                 "gpu_launches": launches, "clocks": clocks}
         line.update(extras)
         print(json.dumps(line), flush=True)
@@ -713,113 +888,16 @@ def run_warmstart(args, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    t_gen = time.perf_counter()
-    graphs, Bs, Xs = [], [], []
-    train_nodes = 0
-    for sp in gg.warmstart_specs("train", args.ws_train):
-        rp, col = gg.generate(sp)
-        g = di.Graph.create(rp, col, stream=stream)
-        b = torch.full((sp.n,), (1.0 - D) / sp.n, dtype=torch.float64, device="cuda")
-        h = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
-        di.di_solve(g, b, D, 1e-8 * (1.0 - D), h, None, di.opts_default(stream=stream.cuda_stream))
-        graphs.append(g)
-        Bs.append(b)
-        Xs.append(h)
-        train_nodes += sp.n
-    t_gen = time.perf_counter() - t_gen
-    model = di.Model.create(7)
-    t0 = time.perf_counter()
-    loss = model.train(graphs, Bs, Xs, di.train_opts_default(epochs=args.ws_epochs, batch=65536, lr=args.ws_lr,
-                                                             stream=stream.cuda_stream))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    for g in graphs:
-        g.close()
-    del Bs, Xs
-    rows = []
-    opts_c = di.opts_default(stream=stream.cuda_stream)
-    opts_w = di.opts_default(stream=stream.cuda_stream, warm_start=1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for sp in gg.warmstart_specs("eval", args.ws_eval):
-        rp, col = gg.generate(sp)
-        g = di.Graph.create(rp, col, stream=stream)
-        n = sp.n
-        b = torch.full((n,), (1.0 - D) / n, dtype=torch.float64, device="cuda")
-        tol = 1e-8 * (1.0 - D)
-        H = torch.zeros(n, dtype=torch.float64, device="cuda")
-        res = {}
-        for label in ("cold", "warm"):
-            times = []
-            for rep in range(max(args.warmup, 1) + max(args.steps, 1)):
-                flush.zero_()
-                if label == "cold":
-                    ev[0].record(stream)
-                    _, st = di.di_solve(g, b, D, tol, H, None, opts_c)
-                    ev[1].record(stream)
-                else:
-                    ev[0].record(stream)
-                    model.infer(g, b, H, stream)
-                    _, st = di.di_solve(g, b, D, tol, H, None, opts_w)
-                    ev[1].record(stream)
-                torch.cuda.synchronize()
-                if rep >= max(args.warmup, 1):
-                    times.append(ev[0].elapsed_time(ev[1]))
-            res[label] = {"ms": statistics.median(times), "edges": st.edge_diffusions, "levels": st.levels,
-                          "warm_used": st.warm_used, "f0_over_b": st.f0_l1 / st.b_l1, "resid": st.resid_l1}
-        if not rows:
-            # the inference parts alone on the first held-out graph: features and the network
-            feat = torch.empty((n, 9), dtype=torch.float32, device="cuda")
-            yv = torch.empty(n, dtype=torch.float32, device="cuda")
-            t_feat, t_fwd = [], []
-            for rep in range(5):
-                flush.zero_()
-                ev[0].record(stream)
-                model.features(g, b, feat, stream)
-                ev[1].record(stream)
-                torch.cuda.synchronize()
-                t_feat.append(ev[0].elapsed_time(ev[1]))
-                flush.zero_()
-                ev[0].record(stream)
-                model.forward(feat, n, yv, stream)
-                ev[1].record(stream)
-                torch.cuda.synchronize()
-                t_fwd.append(ev[0].elapsed_time(ev[1]))
-            fwd_s = statistics.median(t_fwd[1:]) * 1e-3
-            peak, peak_src = measured_hbm_peak()
-            infer_parts = {"features_ms": statistics.median(t_feat[1:]), "network_ms": fwd_s * 1e3,
-                           "network_roofline": {"bound": "hbm", "kernel": "k_mlp_fwd (BF16 mma.sync)",
-                                                "achieved": (36 + 4) * n / fwd_s / 1e9, "peak": peak,
-                                                "unit": "GB/s", "frac": (36 + 4) * n / fwd_s / 1e9 / peak,
-                                                "peak_source": f"{peak_src} (hbm_gbs)",
-                                                "tflops": 2 * (16 * 64 + 64 * 64 + 64) * n / fwd_s / 1e12,
-                                                "bytes_per_node": "36 B features in, 4 B prediction out"}}
-        rows.append(res)
-        g.close()
-    cold = [r["cold"]["ms"] for r in rows]
-    warm = [r["warm"]["ms"] for r in rows]
-    line = {"metric": "time_to_tol_ms", "value": statistics.mean(warm), "unit": "ms",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(warm),
+    r = warmstart_study(args, di, stream, flush, args.ws_train, args.ws_eval, args.ws_epochs, args.ws_lr,
+                        reps=max(args.steps, 1), warmup=max(args.warmup, 1))
+    line = {"metric": "time_to_tol_ms", "value": r["warm_ms"], "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["warm_ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["warmstart"][1], "train_graphs": args.ws_train,
-                       "train_nodes": train_nodes, "eval_graphs": args.ws_eval, "epochs": args.ws_epochs,
-                       "lr": args.ws_lr,
-                       "tol": "1e-8 |B|_1", "timed": "warm: features + network + F0 + solve; cold: solve",
-                       "l2": "flushed (256 MiB write) before each timed solve",
-                       "recompute_every": opts_c.recompute_every, "recompute_drop": opts_c.recompute_drop},
-            "cold_ms": statistics.mean(cold), "warm_ms": statistics.mean(warm),
-            "speedup": statistics.mean(cold) / statistics.mean(warm),
-            "inference": infer_parts,
-            "warm_used": sum(r["warm"]["warm_used"] for r in rows),
-            "f0_over_b_mean": statistics.mean(r["warm"]["f0_over_b"] for r in rows),
-            "edges_cold": statistics.mean(r["cold"]["edges"] for r in rows),
-            "edges_warm": statistics.mean(r["warm"]["edges"] for r in rows),
-            "levels_cold": statistics.mean(r["cold"]["levels"] for r in rows),
-            "levels_warm": statistics.mean(r["warm"]["levels"] for r in rows),
-            "train": {"loss_last_epoch": loss, "seconds": t_train, "generate_and_solve_s": t_gen},
-            "per_graph": rows}
+            "config": {k: r[k] for k in ("workload", "train_graphs", "train_nodes", "eval_graphs", "epochs", "lr",
+                                         "tol", "timed")}}
+    line.update({k: v for k, v in r.items() if k not in line["config"]})
     print(json.dumps(line), flush=True)
-    model.close()
 
 
 def run_kpid(args, world, rank, local):

@@ -155,6 +155,15 @@ def opts_default(**overrides) -> di_opts:
     return o
 
 
+def opts_copy(o: di_opts, **overrides) -> di_opts:
+    """A copy of an options struct (raw bytes: the stream pointer included),
+    with fields overridden."""
+    c = di_opts.from_buffer_copy(o)
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
 def _ptr(x) -> int | None:
     """Raw address of a torch tensor, numpy array, int, or None."""
     if x is None:

@@ -66,3 +66,10 @@ def test_invalid_arguments_are_rejected_before_gpu_work(lib):
     assert lib.di_opts_default(None) == binding.DI_EINVAL
     assert lib.di_solve(None, None, 0.85, 1e-8, None, None, None, None) == binding.DI_EINVAL
     assert lib.di_residual(None, None, 0.85, None, None, None, None) == binding.DI_EINVAL
+
+
+def test_opts_copy_keeps_every_field(lib):
+    o = binding.opts_default(alpha=2.0, resweeps=3, stream=12345)
+    c = binding.opts_copy(o, propagation=7)
+    assert c.alpha == 2.0 and c.resweeps == 3 and c.stream == 12345 and c.propagation == 7
+    assert o.propagation == 3   # the original is untouched

@@ -31,6 +31,9 @@ def test_reference_arm_prints_one_contract_line(workload):
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+    if workload == "web-10k":
+        # the native line's headline: solves per second to the tolerance
+        assert d["metric"] == "solves_per_s_to_tol" and d["unit"] == "solves/s" and d["higher_is_better"] is True
 
 
 def test_warm_start_reference_uses_the_native_metric():
