@@ -54,6 +54,10 @@ WORKLOADS = {
                            "K = 1, 2, 4, 8, uniform and cost-balanced ranges"),
     "batch-64x4": (None, "64 web-like graphs, N log-uniform in [1e4, 2e6], m ~ U[6, 14], seeds 0..63; "
                          "4 personalised right-hand sides each (B = 0.15 e_s), 256 solves per step"),
+    "kpid-sim": (gg.GraphSpec(n=100_000, mean_deg=10.0, window=64, seed=0),
+                 "time-stepped simulation of K PIDs (Secs. 2.3-2.6, Sec. 3) on the host cores: web-like N=1e5, "
+                 "m=10, PID_Speed = L/K, target error r/(1-d) <= 1/N, K = 1..64, uniform and cost-balanced "
+                 "ranges, Delay_Proba 0 / 0.5 / 0.8 at K = 8"),
 }
 # algorithmic bytes of the level kernel: per edge diffusion, per node
 # diffusion, and per node scanned (the fluid read of the selection)
@@ -289,6 +293,34 @@ def run_reference_kpid(args, desc):
                              "sample": "K=8 cost-balanced ranges on a web-like N=1e5 graph"},
             "e2e": {"value": value, "unit": "iterations (ops/L)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_reference_kpid_sim(args, world, rank, local):
+    """Reference arm of the K-PID simulation: the oracle's lock-step emulation
+    (one sweep per PID per round) on the same graph and target, K = 1 and
+    K = 64 cost-balanced; its speed-up is the one-PID cost over the largest
+    per-PID cost (the emulation has no time steps)."""
+    from oracle import kpid as ok
+    spec, desc = WORKLOADS["kpid-sim"]
+    rp, col = gg.generate(spec)
+    n, L = spec.n, int(len(col))
+    b = gg.uniform_b(n, D)
+    tol = (1.0 - D) / n
+    t0 = time.perf_counter()
+    one = ok.kpid(rp, col, b, D, tol=tol, K=1)
+    many = ok.kpid(rp, col, b, D, tol=tol, bounds=ok.cb_bounds(rp, 64))
+    secs = time.perf_counter() - t0
+    value = float(one.ops.max()) / float(many.ops.max())
+    print(json.dumps({"impl": "reference", "metric": "kpid_speedup", "value": value,
+                      "unit": "x (1-PID time / K-PID time)", "n_gpus": 0, "steps": 2, "warmup": 0,
+                      "ms_per_step": 1e3 * secs / 2, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "sample": "K = 1 and K = 64 cost-balanced, lock-step emulation",
+                                 "oracle": "sequential emulation of K PIDs, FP64, 1 core"},
+                      "cpu_baseline": {"value": value, "unit": "x (1-PID time / K-PID time)", "cores": 1,
+                                       "kind": "oracle", "sample": "K = 1 and K = 64 cost-balanced"},
+                      "e2e": {"value": value, "unit": "x (1-PID time / K-PID time)", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_reference_multi(args, desc):
@@ -900,6 +932,44 @@ def run_warmstart(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_kpid_sim(args, world, rank, local):
+    """The paper's evaluation of its distributed scheme (Sec. 3), on the host
+    cores: time in normalised iterations (steps x PID_Speed / L) to the target
+    error 1/N for K = 1..64 PIDs, uniform and cost-balanced ranges; the
+    speed-up over one PID, each PID's operations and the idle share, and the
+    impact of Delay_Proba at K = 8."""
+    from paper_1202_6168_gb300 import kpid_sim as ks
+    spec, desc = WORKLOADS["kpid-sim"]
+    rp, col = gg.generate(spec)
+    n, L = spec.n, int(len(col))
+    b = gg.uniform_b(n, D)
+    tol = (1.0 - D) / n                      # r / (1 - d) <= 1 / N
+    rows, secs = [], 0.0
+    one = None
+    grid = [(1, "uniform", 0.0)] + [(K, kind, 0.0) for K in (2, 4, 8, 16, 32, 64) for kind in ("uniform", "cb")]
+    grid += [(8, kind, p) for p in (0.5, 0.8) for kind in ("uniform", "cb")]
+    for K, kind, p in grid:
+        bounds = ks.uniform_bounds(n, K) if kind == "uniform" else ks.cb_bounds(rp, K)
+        t0 = time.perf_counter()
+        r = ks.simulate(rp, col, b, D, tol=tol, bounds=bounds, delay_proba=p, seed=7)
+        secs += time.perf_counter() - t0
+        if one is None:
+            one = r.normalised_time
+        rows.append({"K": K, "partition": kind, "delay_proba": p, "status": r.status,
+                     "normalised_time": r.normalised_time, "speedup": one / r.normalised_time,
+                     "steps": r.steps, "max_pid_cost": float(r.ops.max()) / L, "total_cost": float(r.ops.sum()) / L,
+                     "idle_share": r.idle_share, "transmissions": int(r.sends.sum()), "resid": r.resid_l1})
+    best = max((row for row in rows if row["delay_proba"] == 0.0), key=lambda row: row["speedup"])
+    line = {"metric": "kpid_speedup", "value": best["speedup"], "unit": "x (1-PID time / K-PID time)",
+            "n_gpus": 0, "steps": len(rows), "warmup": 0, "ms_per_step": 1e3 * secs / len(rows),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "nnz": L, "tol": tol, "best": {"K": best["K"],
+                       "partition": best["partition"]}, "cores": os.cpu_count(),
+                       "timed": "wall clock of every simulation (host cores, OpenMP over the PIDs)"},
+            "rows": rows, "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
 def run_kpid(args, world, rank, local):
     """K-PID asynchronous D-iteration: for every K and partition, the time to
     tol and each PID's elementary diffusions normalised by L (the paper's
@@ -954,7 +1024,12 @@ def run_kpid(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_env()
-    if args.workload == "kpid-1m" and args.impl != "reference":
+    if args.workload == "kpid-sim":
+        # a host-core simulation in both arms: the reference arm runs the oracle's
+        # lock-step emulation (see run_reference_kpid_sim)
+        if rank == 0:
+            (run_reference_kpid_sim if args.impl == "reference" else run_kpid_sim)(args, world, rank, local)
+    elif args.workload == "kpid-1m" and args.impl != "reference":
         if rank == 0:
             run_kpid(args, world, rank, local)
     elif args.workload == "warmstart" and args.impl != "reference":

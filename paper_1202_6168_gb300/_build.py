@@ -22,6 +22,8 @@ GEN_SRC = os.path.join(PKG_DIR, "gen", "graphgen.c")
 INCLUDE_DIR = os.path.join(REPO_DIR, "include")
 
 GEN_SO = os.path.join(LIB_DIR, "libdigen.so")
+SIM_SRC = os.path.join(PKG_DIR, "sim", "kpid_sim.c")
+SIM_SO = os.path.join(LIB_DIR, "libdisim.so")
 DI_SO = os.path.join(LIB_DIR, "libdi.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
@@ -71,6 +73,22 @@ def build_gen(force: bool = False) -> str:
     return GEN_SO
 
 
+def build_sim(force: bool = False) -> str:
+    """The time-stepped K-PID simulator (plain C, OpenMP over the PIDs)."""
+    os.makedirs(LIB_DIR, exist_ok=True)
+    if not force and _newer(SIM_SO, [SIM_SRC]):
+        return SIM_SO
+    tmp = SIM_SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-ffp-contract=off",
+            "-fno-fast-math", SIM_SRC, "-o", tmp, "-lm"]
+    try:
+        _run(base[:1] + ["-fopenmp"] + base[1:])
+    except RuntimeError:
+        _run(base)
+    os.replace(tmp, SIM_SO)
+    return SIM_SO
+
+
 def _cu_objects() -> list[tuple[str, str]]:
     obj_dir = os.path.join(LIB_DIR, "obj")
     os.makedirs(obj_dir, exist_ok=True)
@@ -113,4 +131,5 @@ def build_di(force: bool = False, extra_flags: list[str] | None = None) -> str:
 
 def build_all(force: bool = False) -> None:
     build_gen(force)
+    build_sim(force)
     build_di(force)

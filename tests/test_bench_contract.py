@@ -20,7 +20,7 @@ def reference_line(workload):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("workload", ["web-10k", "kpid-1m"])
+@pytest.mark.parametrize("workload", ["web-10k", "kpid-1m", "kpid-sim"])
 def test_reference_arm_prints_one_contract_line(workload):
     d = reference_line(workload)
     for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -41,3 +41,18 @@ def test_warm_start_reference_uses_the_native_metric():
     # reference arm must report the same metric and unit
     d = reference_line("warmstart")
     assert d["metric"] == "time_to_tol_ms" and d["unit"] == "ms" and d["higher_is_better"] is False
+
+
+def test_kpid_simulation_line_covers_the_papers_grid():
+    # the host-core simulation of K PIDs (no GPU): every K of the grid, both
+    # partitions, the delays at K = 8; idle shares in [0, 1) and speed-ups > 1
+    out = subprocess.run([sys.executable, os.path.join(REPO, "bench.py"), "--workload", "kpid-sim"], cwd=REPO,
+                         capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert d["metric"] == "kpid_speedup" and d["value"] > 1
+    rows = d["rows"]
+    assert {r["K"] for r in rows} == {1, 2, 4, 8, 16, 32, 64}
+    assert {r["delay_proba"] for r in rows} == {0.0, 0.5, 0.8}
+    assert all(r["status"] == 0 and 0.0 <= r["idle_share"] < 1.0 for r in rows)
+    assert all(r["speedup"] > 1 for r in rows if r["K"] > 1 and r["delay_proba"] == 0.0)
