@@ -124,7 +124,8 @@ typedef struct {
                               stochastic.  The fluid a dangling node drains is spread
                               over all nodes as one uniform add in the next frontier
                               selection; the exact residual adds d/N sum_dangling H_j.
-                              Needs propagation 3, 4, 6 or 7 and exact_residual 0 or 2 */
+                              Needs propagation 3 to 7 and exact_residual 0 or 2
+                              (di_solve_batched supports it as well) */
     double recompute_drop; /* FP32 fluid: exact FP64 residual whenever the running |F|_1
                               has fallen by this factor since the last exact value, so
                               that the FP32 rounding of the pushes stays a fraction of
@@ -333,7 +334,9 @@ DI_API di_status di_batch_info(const di_batch *b, int *n_items, int64_t *n_union
  * Solves every item of the batch: B[t], H[t] are device pointers of n_g
  * doubles (host array of n_items pointers); tol[t] > 0 is item t's absolute
  * L1 tolerance on |B + P H - H|_1 (host array).  d in (0, 1).  opts as for
- * di_solve (warm_start must be 0; timing = 1 runs the levels host-driven).
+ * di_solve (warm_start must be 0; timing = 1 runs the levels host-driven;
+ * dangling = 1 completes the dangling columns of each item's graph by 1/n_g,
+ * n_g the nodes of that graph).
  * item_stats (host array of n_items, may be NULL) receives each item's
  * statistics; total (may be NULL) the sums (levels = max over items,
  * gpu_launches and seconds of the whole call).  Returns DI_OK when every

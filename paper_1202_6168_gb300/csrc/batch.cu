@@ -58,6 +58,8 @@ struct BItem {
     unsigned long long node_diff, edge_diff;
     int level, since, recomputes, done;   // done: 0 running, 1 converged, 2 level cap, 3 non-finite
     int push, rec, confirming, pad;
+    double dang_acc;     // 1/N completion: fluid drained from the item's dangling nodes since its last selection
+    double dang_h;       // exact residual: sum of H over the item's dangling nodes
 };
 
 struct BState {
@@ -73,6 +75,7 @@ struct BDesc {
     double drop;         // exact recompute when an item's |F|_1 fell this much since its last one (0 = none)
     int R, fp64, max_levels, max_body_iters, nitems, final_mode;
     int thread_max, warp_max;  // push shape
+    int dangling;              // 1: dangling columns completed by d / n_t (uniform over item t's nodes)
     void *F;             // union fluid (float or double)
     double *B, *H;       // union B and history
     double *tmp, *g;     // exact-residual scratch
@@ -169,8 +172,10 @@ template <typename FT>
 __global__ void __launch_bounds__(kBThreads) k_bscan_level(
     const BDesc *__restrict__ desc, BItem *__restrict__ items, BState *__restrict__ st,
     const int32_t *__restrict__ item_of_chunk, const int32_t *__restrict__ outdeg, int32_t *__restrict__ front,
-    int64_t nchunks, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_rec, int ctl) {
-    const FT *__restrict__ F = static_cast<const FT *>(desc->F);
+    int64_t nchunks, const int64_t *__restrict__ base, const int32_t *__restrict__ nloc,
+    cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_rec, int ctl) {
+    FT *__restrict__ F = static_cast<FT *>(desc->F);
+    const int dangling = desc->dangling;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     __shared__ int s_cnt[kBItems * (kBThreads / 32)];
@@ -180,12 +185,18 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
         if (items[t].done) continue;                 // uniform over the block
         const FT Tc = bthr(items[t].T, FT(0));
         const int64_t c0 = c << kBChunkShift;
+        // 1/N completion (Sec. 2.2): the fluid the item's dangling nodes drained
+        // since its last selection reaches each of its n_t nodes as d / n_t of it
+        // (not the padding after its last node); added and stored before the test
+        const int64_t b0 = base[t], nl = nloc[t];
+        const FT u = dangling ? static_cast<FT>(desc->d * items[t].dang_acc / (double)nl) : FT(0);
         unsigned masks[kBItems];
         double acc = 0.0, mx = 0.0;
         unsigned long long esel = 0;
 #pragma unroll
         for (int k = 0; k < kBItems; ++k) {
             const int64_t idx = c0 + k * kBThreads + threadIdx.x;
+            if (u != FT(0) && idx - b0 < nl) F[idx] += u;
             const FT v = fabs(F[idx]);
             const bool sel = v >= Tc && v > FT(0);
             masks[k] = __ballot_sync(0xffffffffu, sel);
@@ -286,6 +297,7 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
         it.acc_max = 0ull;
         it.acc_nsel = 0ull;
         it.acc_esel = 0ull;
+        it.dang_acc = 0.0;                  // applied by every chunk of this selection
         it.push = push;
         it.rec = rec;
         any_rec |= rec;
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
 // edges), by a warp (<= 512) or by the whole CTA; very hot targets are
 // accumulated in shared memory per CTA.
 template <typename FT>
-__global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ desc, const BItem *__restrict__ items,
+__global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ desc, BItem *__restrict__ items,
                                                      BState *__restrict__ st, const int32_t *__restrict__ item_of_chunk,
                                                      const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
                                                      const int32_t *__restrict__ pcol,
@@ -350,12 +362,16 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
         FT w = FT(0);
         if (idx < count) {
             const int32_t i = __ldcs(front + idx);
-            if (items[item_of_chunk[i >> kBChunkShift]].push) {
+            const int t = item_of_chunk[i >> kBChunkShift];
+            if (items[t].push) {
                 b = __ldcs(rp + i);
                 e = __ldcs(rp + i + 1);
                 const FT f = atomic_exch_keep(F + i, FT(0), keep);
                 __stcs(H + i, __ldcs(H + i) + static_cast<double>(f));
                 w = f * __ldcs(scale + i);
+                // 1/N completion: a selected node without out-edges is dangling (the
+                // padding never holds fluid, so it is never selected)
+                if (e == b && desc->dangling) atomicAdd(&items[t].dang_acc, static_cast<double>(f));
             }
         }
         const int deg = e - b;
@@ -398,22 +414,34 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
 // ------------------------------------------------------------------ exact residual of the items that asked
 
 // tmp = B - H and g = (d / outdeg) H on the chunks of items with rec set.
-__global__ void __launch_bounds__(kBThreads) k_bres_prep(const BDesc *__restrict__ desc,
-                                                         const BItem *__restrict__ items,
+__global__ void __launch_bounds__(kBThreads) k_bres_prep(const BDesc *__restrict__ desc, BItem *__restrict__ items,
                                                          const int32_t *__restrict__ item_of_chunk,
-                                                         const double *__restrict__ s64, int64_t nchunks) {
+                                                         const double *__restrict__ s64, const int32_t *__restrict__ rp,
+                                                         const int64_t *__restrict__ base,
+                                                         const int32_t *__restrict__ nloc, int64_t nchunks) {
     const double *__restrict__ B = desc->B;
     const double *__restrict__ H = desc->H;
     double *__restrict__ tmp = desc->tmp;
     double *__restrict__ g = desc->g;
+    const int dangling = desc->dangling;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        if (!items[item_of_chunk[c]].rec) continue;
+        const int t = item_of_chunk[c];
+        if (!items[t].rec) continue;
+        const int64_t b0 = base[t], nl = nloc[t];
+        double hd = 0.0, unused = 0.0;
+        unsigned long long z = 0;
 #pragma unroll
         for (int k = 0; k < kBItems; ++k) {
             const int64_t i = (c << kBChunkShift) + k * kBThreads + threadIdx.x;
             const double h = H[i];
             tmp[i] = B[i] - h;
             g[i] = s64[i] * h;
+            // 1/N completion: H over the item's dangling nodes (padding excluded)
+            if (dangling && i - b0 < nl && rp[i + 1] == rp[i]) hd += h;
+        }
+        if (dangling) {
+            block_reduce3(hd, unused, z);
+            if (threadIdx.x == 0 && hd != 0.0) atomicAdd(&items[t].dang_h, hd);
         }
     }
 }
@@ -488,18 +516,23 @@ __global__ void __launch_bounds__(kBThreads) k_bres_flat(const BDesc *__restrict
 template <typename FT>
 __global__ void __launch_bounds__(kBThreads) k_bres_fin(const BDesc *__restrict__ desc, BItem *__restrict__ items,
                                                         BState *__restrict__ st,
-                                                        const int32_t *__restrict__ item_of_chunk, int64_t nchunks) {
+                                                        const int32_t *__restrict__ item_of_chunk,
+                                                        const int64_t *__restrict__ base,
+                                                        const int32_t *__restrict__ nloc, int64_t nchunks) {
     FT *__restrict__ F = static_cast<FT *>(desc->F);
     const double *__restrict__ tmp = desc->tmp;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int t = item_of_chunk[c];
         if (!items[t].rec) continue;
+        const int64_t b0 = base[t], nl = nloc[t];
+        // 1/N completion: every node of the item gets (d / n_t) sum_dangling H_j
+        const double du = desc->dangling ? desc->d * items[t].dang_h / (double)nl : 0.0;
         double s = 0.0, m = 0.0;
         unsigned long long z = 0;
 #pragma unroll
         for (int k = 0; k < kBItems; ++k) {
             const int64_t i = (c << kBChunkShift) + k * kBThreads + threadIdx.x;
-            const double f = tmp[i];
+            const double f = i - b0 < nl ? tmp[i] + du : tmp[i];
             F[i] = static_cast<FT>(f);
             s += fabs(f);
             m = fmax(m, fabs(f));
@@ -520,6 +553,8 @@ __global__ void __launch_bounds__(kBThreads) k_bres_fin(const BDesc *__restrict_
         it.res_sum = 0.0;
         it.res_max = 0ull;
         it.rec = 0;
+        it.dang_h = 0.0;
+        it.dang_acc = 0.0;              // the exact fluid already holds what the dangling nodes drained
         if (final_mode) continue;
         it.recomputes += 1;
         it.since = 0;
@@ -648,7 +683,7 @@ template <typename FT>
 void launch_blevel(di_batch *b, cudaStream_t s, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hr, int ctl) {
     di_graph *u = b->u;
     k_bscan_level<FT><<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->st, b->item_of_chunk, u->outdeg,
-                                                          b->front, b->nchunks, hw, hr, ctl);
+                                                          b->front, b->nchunks, b->d_base, b->d_nloc, hw, hr, ctl);
     const FT *scale = sizeof(FT) == 4 ? reinterpret_cast<const FT *>(u->s32) : reinterpret_cast<const FT *>(u->s64);
     k_bpush<FT><<<bpush_grid(b), kBThreads, u->n_hot * sizeof(FT), s>>>(b->desc, b->items, b->st, b->item_of_chunk,
                                                                        b->front, u->rp, u->pcol, u->hot_node, u->n_hot,
@@ -658,10 +693,12 @@ void launch_blevel(di_batch *b, cudaStream_t s, cudaGraphConditionalHandle hw, c
 template <typename FT>
 void launch_bres(di_batch *b, cudaStream_t s) {
     di_graph *u = b->u;
-    k_bres_prep<<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->item_of_chunk, u->s64, b->nchunks);
+    k_bres_prep<<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->item_of_chunk, u->s64, u->rp, b->d_base,
+                                                   b->d_nloc, b->nchunks);
     k_bres_flat<<<b->grid_flat, kBThreads, 0, s>>>(b->desc, b->items, b->nitems, b->d_eoff, u->in_col, u->erow,
                                                    u->nnz);
-    k_bres_fin<FT><<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->st, b->item_of_chunk, b->nchunks);
+    k_bres_fin<FT><<<b->grid_scan, kBThreads, 0, s>>>(b->desc, b->items, b->st, b->item_of_chunk, b->d_base,
+                                                      b->d_nloc, b->nchunks);
 }
 
 di_status build_batch_graph(di_batch *b, int fp64) {
@@ -875,7 +912,7 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
         return DI_EINVAL;
     }
     if (o.warm_start) { set_error("di_solve_batched: warm starts are not supported in a batch"); return DI_EINVAL; }
-    if (o.dangling) { set_error("di_solve_batched: the 1/N dangling completion is not supported in a batch"); return DI_EINVAL; }
+    if (o.dangling < 0 || o.dangling > 1) { set_error("di_solve_batched: dangling = %d outside [0, 1]", o.dangling); return DI_EINVAL; }
     for (int t = 0; t < b->nitems; ++t) {
         if (!B[t] || !H[t]) { set_error("di_solve_batched: NULL B or H of item %d", t); return DI_EINVAL; }
         if (!(tol[t] > 0.0) || !std::isfinite(tol[t])) {
@@ -912,6 +949,7 @@ extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B
     dh.nitems = b->nitems;
     dh.thread_max = b->tune.thread_max_deg;
     dh.warp_max = b->tune.warp_max_deg;
+    dh.dangling = o.dangling;
     dh.F = fp64 ? (void *)b->F64 : (void *)b->F32;
     dh.B = b->B;
     dh.H = b->H;

@@ -864,6 +864,13 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     double *__restrict__ H = desc->H;
     const FT Tc = thr_cast(st->T, FT(0));
     const int lane = threadIdx.x & 31;
+    // 1/N completion (Sec. 2.2): the fluid dangling nodes drained in the previous
+    // level reaches every node as d / N of it, added atomically (other CTAs push
+    // concurrently); what this level drains goes to dang_next
+    const int dangling = desc->dangling;
+    const FT u = dangling ? static_cast<FT>(desc->d * st->dang_acc / (double)n) : FT(0);
+    __shared__ double s_dang;
+    if (threadIdx.x == 0) s_dang = 0.0;
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max;
     auto push1 = [&](int32_t c, FT w) {
@@ -878,7 +885,10 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t idx = c0 + k * kPushThreads + threadIdx.x;
             FT v = FT(0);
-            if (idx < n) v = F[idx];
+            if (idx < n) {
+                if (u != FT(0)) atomicAdd(F + idx, u);
+                v = __ldcg(F + idx);
+            }
             const FT a = fabs(v);
             acc += static_cast<AT>(a);
             mx = max(mx, a);
@@ -894,6 +904,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
                 w = f * __ldcs(scale + idx);
                 my_nodes += 1;
                 my_edges += static_cast<unsigned long long>(e - b);
+                if (e == b && dangling) atomicAdd(&s_dang, static_cast<double>(f));
             }
             const int deg = e - b;
             if (deg <= thread_max) {
@@ -917,6 +928,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
         if (hv != FT(0)) red_add_keep(F + hot_node[sl], hv, keep);
     }
     cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->lvl_nodes, my_nodes);
+    if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_next, s_dang);   // after cta_add_counts' barriers
     double s = static_cast<double>(acc);
     double m = static_cast<double>(mx);
     block_sum_max<kPushThreads>(s, m);
@@ -958,6 +970,8 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     st->body_iters = iters;
     st->phase = phase;
     st->lvl_nodes = 0;
+    st->dang_acc = st->dang_next;   // reaches every node in the next level
+    st->dang_next = 0.0;
     st->do_recompute = rec;
     if (done) st->done = done;
     if (ctl == 1) {
@@ -1667,8 +1681,8 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (o->resweeps < 0 || o->resweeps > 8) { set_error("di_solve: resweeps = %d outside [0, 8]", o->resweeps); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
     if (o->dangling < 0 || o->dangling > 1) { set_error("di_solve: dangling = %d outside [0, 1]", o->dangling); return DI_EINVAL; }
-    if (o->dangling == 1 && ((o->propagation < 3 || o->propagation == 5) || o->exact_residual == 1)) {
-        set_error("di_solve: the 1/N dangling completion needs propagation 3, 4, 6 or 7 and exact_residual 0 or 2 "
+    if (o->dangling == 1 && (o->propagation < 3 || o->exact_residual == 1)) {
+        set_error("di_solve: the 1/N dangling completion needs propagation 3 to 7 and exact_residual 0 or 2 "
                   "(got %d, %d)", o->propagation, o->exact_residual);
         return DI_EINVAL;
     }

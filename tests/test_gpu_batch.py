@@ -219,3 +219,41 @@ def test_batch_autotune_then_parity(mixed_graphs, tmp_path):
     batch.close()
     for g in graphs:
         g.close()
+
+
+# ---------------------------------------------------------------- 1/N completion of the dangling columns (Sec. 2.2)
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_batch_dangling_completion_matches_the_completed_oracle(fp64):
+    # every item completes the dangling columns of its own graph by 1/n_g;
+    # the chunk padding between items (union nodes past n_g) takes no part
+    rng = np.random.default_rng(77)
+    graphs = [gg.generate(gg.GraphSpec(n=n, mean_deg=m, seed=s)) for n, m, s in ((2000, 6.0, 5), (4999, 9.0, 6))]
+    graphs += [csr_from_edges(1, []), csr_from_edges(700, []), random_graph(800, rng, max_deg=12)]
+    nrhs = [2, 1, 1, 1, 2]
+    gs = [di.Graph.create(rp, col) for rp, col in graphs]
+    batch = di.Batch(gs, nrhs)
+    items, Bs, Hs, tols = [], [], [], []
+    for (rp, col), k in zip(graphs, nrhs):
+        n = len(rp) - 1
+        for r in range(k):
+            b = rhs_for(n, r, rng)
+            items.append((rp, col, b))
+            Bs.append(dev(b))
+            Hs.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+            tols.append((1e-11 * (1 - D) if fp64 else 1e-8) * b.sum())
+    rc, st, _ = di.di_solve_batched(batch, Bs, D, tols, Hs, di.opts_default(fluid_fp64=1 if fp64 else 0, dangling=1))
+    eps = np.finfo(np.float64).eps
+    for (rp, col, b), h, tol, s in zip(items, Hs, tols, st):
+        h = h.cpu().numpy()
+        x = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum(), dangling=True).H
+        assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum()
+        # the stop, with the allowance for the one dangling sum every residual element shares
+        _, r_cpu = od.residual(rp, col, b, D, h, dangling=True)
+        dang = np.diff(rp) == 0
+        floor = 64 * eps * (np.abs(b).sum() + 2 * np.abs(h).sum()) + 2 * D * dang.sum() * eps * np.abs(h[dang]).sum()
+        assert r_cpu <= tol * (1 + 1e-9) + floor
+        assert abs(s.resid_l1 - r_cpu) <= 1e-9 * max(r_cpu, tol) + floor
+    batch.close()
+    for g in gs:
+        g.close()

@@ -643,7 +643,7 @@ def assert_completed_residual_close(f_gpu, f_cpu, rp, col, b, h):
     assert np.all(err <= bound + 1e-300), f"max excess {np.max(err - bound):.3e}"
 
 
-@pytest.mark.parametrize("prop", [3, 4, 6, 7])
+@pytest.mark.parametrize("prop", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_dangling_completion_matches_oracle(web10k_completed, prop, fp64):
     rp, col, b, x = web10k_completed
@@ -662,7 +662,7 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     # a personalised right-hand side (sparse early levels)
     bp = gg.personalised_b(len(b), 1234)
     xp = od.d_iteration(rp, col, bp, D, tol=1e-14 * bp.sum(), dangling=True).H
-    for prop in (4, 6, 7):
+    for prop in (4, 5, 6, 7):
         h, st, _, _ = solve(rp, col, bp, 1e-8 * bp.sum(), propagation=prop, dangling=1)
         assert np.abs(h - xp).sum() <= 1e-6 * np.abs(xp).sum()
         check_stop_completed(rp, col, bp, h, st, 1e-8 * bp.sum())
@@ -678,7 +678,7 @@ def test_dangling_completion_personalised_and_warm(web10k_completed):
     check_stop_completed(rp, col, b, h, st, 1e-8 * b.sum())
 
 
-@pytest.mark.parametrize("prop", [4, 6, 7])
+@pytest.mark.parametrize("prop", [4, 5, 6, 7])
 def test_dangling_completion_on_two_source_blocks(web5m, prop):
     # more than 2^22 nodes: the dangling sum of the exact residual spans both blocks
     rp, col, b = web5m
@@ -695,14 +695,14 @@ def test_dangling_completion_rejects_unsupported_modes():
     g = di.Graph.create(rp, col)
     B = dev(np.ones(3))
     H = torch.zeros(3, dtype=torch.float64, device="cuda")
-    for opt in (dict(dangling=2), dict(dangling=1, propagation=5), dict(dangling=1, propagation=0),
+    for opt in (dict(dangling=2), dict(dangling=1, propagation=2), dict(dangling=1, propagation=0),
                 dict(dangling=1, exact_residual=1)):
         with pytest.raises(di.DiError) as e:
             di.di_solve(g, B, D, 1e-8, H, None, di.opts_default(**opt))
         assert e.value.status == di.DI_EINVAL
     batch = di.Batch([g], [1])
     with pytest.raises(di.DiError) as e:
-        di.di_solve_batched(batch, [B], D, 1e-8, [H], di.opts_default(dangling=1))
+        di.di_solve_batched(batch, [B], D, 1e-8, [H], di.opts_default(dangling=2))
     assert e.value.status == di.DI_EINVAL
     batch.close()
     g.close()
@@ -727,7 +727,7 @@ def test_dangling_completion_edge_cases(case):
         assert x[0] == pytest.approx(0.15 / (1 - D), rel=1e-13)
     for fp64, rel in ((False, 1e-6), (True, 1e-11)):
         tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
-        for prop in (3, 6, 7):
+        for prop in (3, 5, 6, 7):
             h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, dangling=1)
             assert np.abs(h - x).sum() <= rel * np.abs(x).sum()
             check_stop_completed(rp, col, b, h, st, tol)
