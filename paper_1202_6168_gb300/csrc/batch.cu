@@ -855,6 +855,7 @@ di_status batch_create_impl(const di_graph *const *graphs, int ng, const int *nr
 
 extern "C" DI_API di_status di_batch_create(const di_graph *const *graphs, int ng, const int *nrhs, void *stream,
                                            di_batch **out) {
+    di::NvtxRange nvtx_range("di_batch_create");
     clear_error();
     if (!out) { set_error("di_batch_create: out is NULL"); return DI_EINVAL; }
     *out = nullptr;
@@ -900,6 +901,7 @@ extern "C" DI_API di_status di_batch_info(const di_batch *b, int *n_items, int64
 extern "C" DI_API di_status di_solve_batched(di_batch *b, const double *const *B, double d, const double *tol,
                                             double *const *H, const di_opts *opts, di_stats *item_stats,
                                             di_stats *total) {
+    di::NvtxRange nvtx_range("di_solve_batched");
     clear_error();
     if (!b || !B || !H || !tol) { set_error("di_solve_batched: NULL batch, B, H or tol"); return DI_EINVAL; }
     di_opts o;

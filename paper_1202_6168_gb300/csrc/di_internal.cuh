@@ -7,8 +7,18 @@
 #include <cstring>
 
 #include "di.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace di {
+
+// NVTX range for profilers' timelines (a no-op unless a tool is attached):
+// every entry point, and in the host-driven level loop every level and kernel.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------------ errors
 

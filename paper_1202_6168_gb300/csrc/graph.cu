@@ -559,6 +559,7 @@ using namespace di;
 
 extern "C" DI_API di_status di_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
                                            int on_device, void *stream, di_graph **out) {
+    di::NvtxRange nvtx_range("di_graph_create");
     clear_error();
     if (!out) { set_error("di_graph_create: out is NULL"); return DI_EINVAL; }
     *out = nullptr;

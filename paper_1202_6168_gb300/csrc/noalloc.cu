@@ -169,6 +169,7 @@ using namespace di;
 
 extern "C" DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double d, const double *H,
                                                double *F, double *r_l1, void *stream) {
+    di::NvtxRange nvtx_range("di_residual_noalloc");
     clear_error();
     if (!g || !B || !H || !F) { set_error("di_residual_noalloc: NULL argument"); return DI_EINVAL; }
     if (!(d > 0.0 && d < 1.0)) { set_error("di_residual_noalloc: d = %g outside (0, 1)", d); return DI_EINVAL; }

@@ -557,6 +557,7 @@ using namespace di;
 extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, double d, double tol, double *H,
                                                 double *F, const di_opts *opts, int32_t K, int32_t kind,
                                                 int64_t *pid_ops, int64_t *pid_sends, di_stats *stats) {
+    di::NvtxRange nvtx_range("di_solve_partitioned");
     clear_error();
     if (!g || !B || !H) { set_error("di_solve_partitioned: NULL graph, B or H"); return DI_EINVAL; }
     di_opts o;

@@ -338,6 +338,7 @@ using namespace di;
 
 extern "C" DI_API di_status di_residual(di_graph *g, const double *B, double d, const double *H, double *F,
                                        double *r_l1, void *stream) {
+    di::NvtxRange nvtx_range("di_residual");
     clear_error();
     if (!g || !B || !H || !F) { set_error("di_residual: NULL argument"); return DI_EINVAL; }
     if (!(d > 0.0 && d < 1.0)) { set_error("di_residual: d = %g outside (0, 1)", d); return DI_EINVAL; }

@@ -1789,10 +1789,11 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         DI_TRY(ensure_window(g, s));
         DI_TRY(fp64 ? prepare_tiled<double>(g) : prepare_tiled<float>(g));
     }
-    if (o.propagation == 3 || o.propagation == 7) {
+    g->push_R = 0;
+    if ((o.propagation == 3 || o.propagation == 7) && g->tune.push_window) {
         // the frontier push's fluid window (its radius follows the graph's locality)
         DI_TRY(ensure_window(g, s));
-        g->push_R = g->tune.push_window ? g->win_R : 0;
+        g->push_R = g->win_R;
     }
     if (o.propagation == 7) {
         DI_TRY(fp64 ? prepare_coop<double>(g) : prepare_coop<float>(g));
@@ -1872,6 +1873,7 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             if (!e) DI_CUDA_TRY(cudaEventCreate(&e));
         for (;;) {
             for (int l = 0; l < kBatch; ++l) {
+                NvtxRange lr("level");
                 cudaEvent_t *e = ws.tev + 4 * l;
                 DI_CUDA_TRY(cudaEventRecord(e[0], s));
                 DI_CUDA_TRY(cudaEventRecord(e[3], s));
@@ -1897,7 +1899,10 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
                     launch_pushw<float>(g, s, win);
                 }
                 DI_CUDA_TRY(cudaEventRecord(e[1], s));
-                launch_residual(g, fp64, RES_LEVEL, s);
+                {
+                    NvtxRange rr("exact residual (if due)");
+                    launch_residual(g, fp64, RES_LEVEL, s);
+                }
                 DI_CUDA_TRY(cudaEventRecord(e[2], s));
                 host_launches += (o.propagation >= 5 ? 1 : o.propagation >= 3 ? 2 : 3) + residual_kernels(g);
             }
@@ -1995,12 +2000,14 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
 
 extern "C" DI_API di_status di_solve(di_graph *g, const double *B, double d, double tol, double *H, double *F,
                                     const di_opts *opts, di_stats *stats) {
+    NvtxRange range("di_solve");
     clear_error();
     return solve_impl(g, B, d, tol, H, F, opts, stats);
 }
 
 extern "C" DI_API di_status di_solve_host(di_graph *g, const double *B, double d, double tol, double *H, double *F,
                                          const di_opts *opts, di_stats *stats) {
+    NvtxRange range("di_solve_host");
     clear_error();
     if (!g || !B || !H) { set_error("di_solve_host: NULL graph, B or H"); return DI_EINVAL; }
     di_opts o;

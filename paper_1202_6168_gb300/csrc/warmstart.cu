@@ -929,6 +929,7 @@ extern "C" DI_API di_status di_model_set(di_model *m, const float *state) {
 }
 
 extern "C" DI_API di_status di_features(di_model *m, di_graph *g, const double *B, float *feat, void *stream) {
+    di::NvtxRange nvtx_range("di_features");
     clear_error();
     DI_TRY(check_model(m, "di_features"));
     if (!g || !B || !feat) { set_error("di_features: NULL argument"); return DI_EINVAL; }
@@ -937,6 +938,7 @@ extern "C" DI_API di_status di_features(di_model *m, di_graph *g, const double *
 }
 
 extern "C" DI_API di_status di_mlp_forward(const di_model *m, const float *feat, int64_t n, float *y, void *stream) {
+    di::NvtxRange nvtx_range("di_mlp_forward");
     clear_error();
     DI_TRY(check_model(m, "di_mlp_forward"));
     if (!feat || !y || n < 1) { set_error("di_mlp_forward: NULL argument or n < 1"); return DI_EINVAL; }
@@ -988,6 +990,7 @@ extern "C" DI_API di_status di_model_adam(di_model *m, const float *grad, const 
 
 extern "C" DI_API di_status di_warmstart_train(di_model *m, di_graph *const *graphs, int ng, const double *const *B,
                                               const double *const *X, const di_train_opts *opts, double *final_loss) {
+    di::NvtxRange nvtx_range("di_warmstart_train");
     clear_error();
     DI_TRY(check_model(m, "di_warmstart_train"));
     if (!graphs || !B || !X || ng < 1) { set_error("di_warmstart_train: need ng >= 1 graphs with B and X"); return DI_EINVAL; }
@@ -1065,6 +1068,7 @@ extern "C" DI_API di_status di_warmstart_train(di_model *m, di_graph *const *gra
 }
 
 extern "C" DI_API di_status di_warmstart_infer(di_model *m, di_graph *g, const double *B, double *H0, void *stream) {
+    di::NvtxRange nvtx_range("di_warmstart_infer");
     clear_error();
     DI_TRY(check_model(m, "di_warmstart_infer"));
     if (!g || !B || !H0) { set_error("di_warmstart_infer: NULL argument"); return DI_EINVAL; }
