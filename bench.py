@@ -88,7 +88,7 @@ def parse():
                         "6 node-ordered chunks with on-chip window and hot slots, 7 persistent level loop")
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
     p.add_argument("--resweeps", type=int, default=None,
-                   help="propagations 3-6: re-selections at the same threshold before T <- T/alpha")
+                   help="propagations 3-7: re-selections at the same threshold before T <- T/alpha")
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
     p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
