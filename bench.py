@@ -89,6 +89,9 @@ def parse():
     p.add_argument("--push-ratio", type=int, default=None, help="dense-level threshold of the auto modes")
     p.add_argument("--resweeps", type=int, default=None,
                    help="propagations 3-7: re-selections at the same threshold before T <- T/alpha")
+    p.add_argument("--slice-sweeps", type=int, default=None,
+                   help="propagations 3 and 7: sweeps of each push CTA's node slice at the level's threshold "
+                        "after the frontier (nodes that crossed T while the level pushed), 0 = off")
     p.add_argument("--exact-residual", type=int, default=None,
                    help="exact FP64 residual: 0 auto, 1 binned gather, 2 source-blocked gather")
     p.add_argument("--autotune", action="store_true", help="single solves: choose the push shape by timing first")
@@ -196,19 +199,20 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def level_traffic(workload: str, prec: str, propagation: int):
+def level_traffic(workload: str, prec: str, propagation: int, slice_sweeps: int):
     """DRAM bytes (read + write) of one level's kernels (selection + push),
     averaged over the levels of one solve, from the ncu capture summarised in
-    profiles/level_traffic.txt (lines: workload precision propagation bytes);
-    None when no capture of this configuration is recorded."""
+    profiles/level_traffic.txt (lines: workload precision propagation
+    slice_sweeps bytes); None when no capture of this configuration is
+    recorded."""
     path = os.path.join(REPO, "profiles", "level_traffic.txt")
     try:
         with open(path) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) == 4 and not line.startswith("#") and parts[0] == workload and parts[1] == prec \
-                        and parts[2] == str(propagation):
-                    return float(parts[3])
+                if len(parts) == 5 and not line.startswith("#") and parts[0] == workload and parts[1] == prec \
+                        and parts[2] == str(propagation) and parts[3] == str(slice_sweeps):
+                    return float(parts[4])
     except OSError:
         return None
     return None
@@ -375,9 +379,11 @@ def phase_roofline(di, g, B, H, tol, opts, prec, n, flush, stream, workload, rep
     popt = di.opts_copy(opts, propagation=7, timing=0)
     sel_s = push_s = 0.0
     passes = nodes = edges = reds = 0
+    sweeps = 0
     for _ in range(reps):
         flush.zero_()
         _, st = di.di_solve(g, B, D, tol, H, None, popt)
+        sweeps = st.slice_sweeps
         sel_s += st.select_seconds
         push_s += st.level_seconds - st.select_seconds
         passes += st.level_launches
@@ -386,10 +392,11 @@ def phase_roofline(di, g, B, H, tol, opts, prec, n, flush, stream, workload, rep
         reds += st.red_ops
     peak, peak_src = measured_hbm_peak()
     sel_b = SCAN_BYTES[prec] * n * passes
-    push_b = EDGE_BYTES[prec] * edges + NODE_BYTES[prec] * nodes
+    # the push's slice sweeps read the fluid once more per sweep
+    push_b = EDGE_BYTES[prec] * edges + NODE_BYTES[prec] * nodes + SCAN_BYTES[prec] * n * passes * sweeps
     achieved = (sel_b + push_b) / (sel_s + push_s) / 1e9
-    traffic = level_traffic(workload, prec, 3) if not (opts.selection or opts.dangling) and opts.resweeps == 0 \
-        else None
+    traffic = level_traffic(workload, prec, 3, sweeps) \
+        if not (opts.selection or opts.dangling) and opts.resweeps == 0 else None
     out = {"bound": "hbm", "kernel": "selection + asynchronous push of a level (propagation 3's code)",
            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "peak_source": f"{peak_src} (hbm_gbs)", "traffic": traffic,
@@ -414,10 +421,10 @@ def phase_roofline(di, g, B, H, tol, opts, prec, n, flush, stream, workload, rep
 
 def stress_leg(args, di, stream, flush):
     """The N = 2^24, m = 16, +-256 window workload: FP32 fluid, FP64 history, an
-    exact FP64 residual every 8 levels (the workload's schedule), one
-    re-selection per level (the fastest measured setting); time to
-    tolerance, the phase roofline, and the error of H against the oracle's X
-    (the oracle solved to 1e-10 |B|_1, so its own error is <= 6.7e-10 |X|_1)."""
+    exact FP64 residual every 8 levels (the workload's schedule), the library's
+    default level (one slice sweep per level); time to tolerance, the phase
+    roofline, and the error of H against the oracle's X (the oracle solved to
+    1e-10 |B|_1, so its own error is <= 6.7e-10 |X|_1)."""
     import torch
     from oracle import diter as od
     sp = gg.STRESS_16M
@@ -430,7 +437,7 @@ def stress_leg(args, di, stream, flush):
     g = di.Graph.create(rp, col, stream=stream)
     B = torch.from_numpy(b).cuda()
     H = torch.zeros(n, dtype=torch.float64, device="cuda")
-    opts = di.opts_default(stream=stream.cuda_stream, recompute_every=8, recompute_drop=0.0, resweeps=1)
+    opts = di.opts_default(stream=stream.cuda_stream, recompute_every=8, recompute_drop=0.0)
     di.di_solve(g, B, D, tol, H, None, opts)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     times, st = [], None
@@ -454,8 +461,8 @@ def stress_leg(args, di, stream, flush):
            "solves_per_s": 1e3 / ms, "edge_diffusions_per_s": st.edge_diffusions / (ms * 1e-3),
            "normalised_iterations": st.edge_diffusions / nnz, "levels": st.levels,
            "passes": st.body_iterations, "recomputes": st.recomputes,
-           "options": {"propagation": "asynchronous push (3)", "resweeps": 1, "recompute_every": 8,
-                       "fluid": "f32", "history": "f64"},
+           "options": {"propagation": "asynchronous push (3)", "resweeps": 0, "slice_sweeps": st.slice_sweeps,
+                       "recompute_every": 8, "fluid": "f32", "history": "f64"},
            "roofline": roof,
            "check": {"rel_l1_err_vs_oracle_x": float(np.abs(h - x).sum() / np.abs(x).sum()),
                      "resid_l1_oracle_fp64": r_cpu, "tol": tol, "stop_ok": bool(r_cpu <= tol * (1 + 1e-9)),
@@ -610,6 +617,8 @@ def run_native(args, world, rank, local):
         opts.push_ratio = args.push_ratio
     if args.resweeps is not None:
         opts.resweeps = args.resweeps
+    if args.slice_sweeps is not None:
+        opts.slice_sweeps = args.slice_sweeps
     if args.exact_residual is not None:
         opts.exact_residual = args.exact_residual
     if args.weighted:
@@ -672,7 +681,8 @@ def run_native(args, world, rank, local):
                                    recompute_drop=opts.recompute_drop,
                                    l2_window=opts.l2_window, propagation=opts.propagation,
                                    push_ratio=opts.push_ratio, exact_residual=opts.exact_residual,
-                                   selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps)
+                                   selection=opts.selection, dangling=opts.dangling, resweeps=opts.resweeps,
+                                   slice_sweeps=opts.slice_sweeps)
             te = tn = 0
             tpush = trec = tsel = 0.0
             npush = 0
@@ -757,7 +767,7 @@ def run_native(args, world, rank, local):
                                            "node-ordered chunks, on-chip window and hot slots, one launch "
                                            "per level",
                                            "asynchronous push, persistent cooperative level loop"][opts.propagation],
-                           "push_ratio": opts.push_ratio, "resweeps": opts.resweeps,
+                           "push_ratio": opts.push_ratio, "resweeps": opts.resweeps, "slice_sweeps": last.slice_sweeps,
                            "push_shape": dict(shape, chosen_by="di_autotune" if args.autotune else "default"),
                            "exact_residual": ["auto", "binned gather", "source-blocked gather"][opts.exact_residual],
                            "selection": ["|F_i| >= T", "|F_i| / ((in_i+1)(out_i+1)) >= T"][opts.selection],

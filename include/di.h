@@ -135,14 +135,29 @@ typedef struct {
     long long spin_limit;  /* bound of a device wait, in microseconds: the grid barriers of
                               the persistent level loop (propagation 7) give up after it and
                               the solve returns DI_ETIMEOUT (no GPU fault; the context stays
-                              usable).  No other kernel waits on another CTA.  0 .. 2^40;
-                              default 2^20 (about 1 s) */
+                              usable); the push's wait for the frontier's tiles before its
+                              slice sweeps (slice_sweeps) gives up after it and sweeps what
+                              has landed (the result is unaffected).  No other kernel waits
+                              on another CTA.  0 .. 2^40; default 2^20 (about 1 s) */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
     int resweeps;          /* propagations 3-7: after a level's pass, select again at the
                               same T up to this many times (nodes whose fluid crossed T
                               while the level pushed - what the paper's sequential sweep
                               meets later in the same sweep) before T <- T / alpha; a pass
                               that selects nothing ends the level.  0 .. 8; default 0 */
+    int slice_sweeps;      /* propagations 3 and 7: once the frontier's tiles are all
+                              claimed, each CTA of the push sweeps its own slice of about
+                              n / (push CTAs) consecutive nodes at the level's threshold
+                              and diffuses every node with |F_i| >= T, up to this many
+                              times - the nodes whose fluid crossed T while the level
+                              pushed, which the sequential sweep of Sec. 2.4 diffuses in
+                              the same sweep.  Unlike resweeps, no grid-wide pass: a node
+                              that crosses T after its slice was swept keeps its fluid for
+                              the next selection.  0 = off, 1 .. 4, or -1 (default): one
+                              where it applies - propagation 3 or 7, selection 0, no
+                              re-selection and no fluid window - and none elsewhere.  An
+                              explicit count > 0 needs propagation 3 or 7 and selection 0,
+                              and turns the fluid window of di_tune off for the solve */
 } di_opts;
 
 /* Statistics of one solve. */
@@ -167,13 +182,14 @@ typedef struct {
     int32_t level_launches;    /* level kernels that did work (propagation 7: selection passes) */
     int32_t recompute_launches;/* exact residual recomputations */
     int32_t body_iterations;   /* iterations of the device-side level loop */
-    int32_t reserved;
+    int32_t slice_sweeps;      /* slice sweeps per level the push made (opts.slice_sweeps resolved) */
     double select_seconds;     /* timing mode, propagation 3/4 (propagation 7: always): the
                                   frontier-selection part of level_seconds */
     int64_t red_ops;           /* propagations 3, 6, 7: global L2 reduction sectors the push
                                   issued (a scattered red counts one, a coalesced flush of the
                                   shared-memory fluid window one per sector it touches); 0 for
                                   the other propagations */
+    int64_t slice_nodes;       /* nodes diffused by the push's slice sweeps (opts.slice_sweeps) */
 } di_stats;
 
 /* Library version string. */
@@ -185,7 +201,7 @@ DI_API const char *di_last_error(void);
 /* Defaults: alpha 1.5, FP32 fluid, recompute_every 0, recompute_drop 1024,
  * max_levels 100000, cold start (fallback on when warm), L2 window on,
  * timing off, propagation 3, push_ratio 8, exact_residual 0, selection 0,
- * dangling 0, spin_limit 2^20, stream NULL, resweeps 0.  Returns DI_EINVAL if
+ * dangling 0, spin_limit 2^20, stream NULL, resweeps 0, slice_sweeps -1 (auto).  Returns DI_EINVAL if
  * o is NULL. */
 DI_API di_status di_opts_default(di_opts *o);
 
@@ -451,7 +467,9 @@ DI_API di_status di_warmstart_load(const char *path, di_model **out);
  *   mode 0: red.global.add.f32 at pseudo-random slots with the L2 evict-last
  *           hint of the push;  1: the same in FP64;  2: 4-byte loads at
  *           pseudo-random slots (gathers);  3: red.global.add.f32 at
- *           consecutive slots per warp (coalesced, for contrast).
+ *           consecutive slots per warp (coalesced, for contrast);
+ *           4: atom.global.add.f32 at pseudo-random slots (fetch-and-add,
+ *           the old value returned to the thread).
  * The array is allocated and freed by the call (this is a measurement, not a
  * solver step).  Synchronous on stream.  DI_EINVAL on a bad mode, size or
  * count; DI_ENOMEM / DI_ECUDA on CUDA failures.

@@ -26,7 +26,7 @@ class di_opts(ctypes.Structure):
                 ("max_levels", c_int), ("warm_start", c_int), ("warm_fallback", c_int),
                 ("l2_window", c_int), ("timing", c_int), ("propagation", c_int), ("push_ratio", c_int), ("exact_residual", c_int), ("selection", c_int),
                 ("dangling", c_int), ("recompute_drop", c_dbl), ("spin_limit", ctypes.c_longlong),
-                ("stream", c_vp), ("resweeps", c_int)]
+                ("stream", c_vp), ("resweeps", c_int), ("slice_sweeps", c_int)]
 
 
 class di_train_opts(ctypes.Structure):
@@ -49,8 +49,8 @@ class di_stats(ctypes.Structure):
                 ("b_l1", c_dbl), ("f0_l1", c_dbl), ("seconds", c_dbl), ("warm_used", c_i32),
                 ("status", c_i32), ("gpu_launches", c_i64), ("level_seconds", c_dbl),
                 ("recompute_seconds", c_dbl), ("level_launches", c_i32), ("recompute_launches", c_i32),
-                ("body_iterations", c_i32), ("reserved", c_i32), ("select_seconds", c_dbl),
-                ("red_ops", c_i64)]
+                ("body_iterations", c_i32), ("slice_sweeps", c_i32), ("select_seconds", c_dbl),
+                ("red_ops", c_i64), ("slice_nodes", c_i64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -465,7 +465,7 @@ def version() -> str:
     return lib().di_version().decode()
 
 
-PROBE_MODES = {"red_f32": 0, "red_f64": 1, "gather_f32": 2, "red_f32_coalesced": 3}
+PROBE_MODES = {"red_f32": 0, "red_f64": 1, "gather_f32": 2, "red_f32_coalesced": 3, "atom_f32": 4}
 
 
 def probe_l2(mode: str, slots: int, ops: int, stream=None) -> tuple[float, float]:

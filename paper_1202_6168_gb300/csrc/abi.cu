@@ -45,5 +45,6 @@ extern "C" DI_API di_status di_opts_default(di_opts *o) {
     o->spin_limit = 1LL << 20;
     o->stream = nullptr;
     o->resweeps = 0;
+    o->slice_sweeps = -1;
     return DI_OK;
 }

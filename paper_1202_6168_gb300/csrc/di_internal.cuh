@@ -58,6 +58,7 @@ constexpr int kSrcBlockShift = 22;  // exact residual: sources in blocks of 2^22
 constexpr int kWinBins = 4;         // tiled level kernel: window radii 32 .. 256 (powers of two)
 constexpr int kMaxWinR = 32 << (kWinBins - 1);
 constexpr int kPushWin = 1024;      // frontier push: nodes of a tile's fluid window beyond its radius
+constexpr int kSliceQueueCap = 1536;   // frontier push: entries of a CTA's slice-sweep queue
 
 // ------------------------------------------------------------------ solver state
 
@@ -84,6 +85,8 @@ struct SolveDesc {
     int dangling;         // 1: columns of dangling nodes completed by d/N (uniform)
     int resweeps;         // propagations 3-7: extra selections at the same T before T <- T / alpha
     int win_R;            // frontier push (propagations 3, 7): radius of the shared-memory fluid window, 0 = none
+    int slice_sweeps;     // frontier push (propagations 3, 7): sweeps of each CTA's node slice after the frontier
+    unsigned long long wait_ns;   // bound of the push's wait for the frontier tiles before a slice sweep
 };
 
 // Device-resident level-loop state (one per graph object).
@@ -130,6 +133,9 @@ struct SolveState {
     unsigned long long t_scan_ns, t_push_ns;   // persistent loop: time in selection / push phases
     unsigned long long passes;  // persistent loop: selection passes made
     unsigned long long red_ops; // tiled level: global reduction sectors issued (scattered reds count one each)
+    double T_push;              // selection threshold of the frontier being pushed (the slice sweeps' T)
+    unsigned long long slice_nodes;  // nodes diffused by the push's slice sweeps
+    unsigned int tiles_done;    // frontier tiles whose pushes are done (slice sweeps wait for all)
 };
 
 enum ResMode : int {
@@ -150,6 +156,7 @@ struct SolverGraph {
     int grid_push = 0;    // built with this push grid
     unsigned long long timeout_ns = 0;   // built with this grid-barrier bound (persistent loop)
     int grid_coop = 0;                   // built with this persistent grid
+    int slice = 0;                       // built with the slice-sweep variant of the push
 };
 
 struct Workspace {
@@ -226,6 +233,8 @@ struct di_graph {
     int grid_coop[2] = {0, 0};
     unsigned long long coop_timeout_ns = 0;
     int push_R = 0;               // frontier push: window radius in use (0 = none)
+    int push_slice = 0;           // frontier push: the slice-sweep variant in use (opts.slice_sweeps > 0)
+    int grid_push_slice = 0;      // occupancy grid of the slice-sweep variant
     // weighted selection (Sec. 2.4 score): 1 / ((in + 1)(out + 1)), built on first use
     float *iw32 = nullptr;
     double *iw64 = nullptr;
@@ -263,6 +272,19 @@ __device__ __forceinline__ void red_add_keep(float *addr, float v, uint64_t pol)
 }
 __device__ __forceinline__ void red_add_keep(double *addr, double v, uint64_t pol) {
     asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(addr), "d"(v), "l"(pol) : "memory");
+}
+// fetch-and-add with the same policy: returns the target's value before the add
+__device__ __forceinline__ float atom_add_keep(float *addr, float v, uint64_t pol) {
+    float old;
+    asm volatile("atom.global.add.L2::cache_hint.f32 %0, [%1], %2, %3;"
+                 : "=f"(old) : "l"(addr), "f"(v), "l"(pol) : "memory");
+    return old;
+}
+__device__ __forceinline__ double atom_add_keep(double *addr, double v, uint64_t pol) {
+    double old;
+    asm volatile("atom.global.add.L2::cache_hint.f64 %0, [%1], %2, %3;"
+                 : "=d"(old) : "l"(addr), "d"(v), "l"(pol) : "memory");
+    return old;
 }
 __device__ __forceinline__ float atomic_exch_keep(float *p, float v, uint64_t pol) {
     uint32_t old;
@@ -450,7 +472,7 @@ di_status ensure_selection_weights(di_graph *g, cudaStream_t s);
 di_status ensure_window(di_graph *g, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
-int push_grid(const di_graph *g);
+int push_grid(const di_graph *g, bool slice = false);
 // tune.cu: validation of a push shape, candidates, and the JSON-lines cache
 di_status check_tune(const di_tune *t, const char *who);
 int tune_candidates(di_tune *out, int cap);

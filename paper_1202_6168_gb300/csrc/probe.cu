@@ -37,6 +37,8 @@ __device__ __forceinline__ uint32_t next_slot(uint32_t &x, uint32_t mask) {
 // mode 2: 4-byte loads at random slots (gathers), summed so they stay live
 // mode 3: red.global.add.f32 at consecutive slots per warp (coalesced), the
 //         contrast that shows the per-address cost of the scattered form
+// mode 4: atom.global.add.f32 at random slots (fetch-and-add: the old value
+//         returns to the thread and is summed so that it stays live)
 template <int kMode>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(void *arr, uint32_t mask, int iters, uint32_t seed,
                                                          float *sink) {
@@ -56,10 +58,11 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(void *arr, uint32_t mas
         for (int u = 0; u < kProbeUnroll; ++u) {
             if (kMode == 0 || kMode == 3) red_add_keep(static_cast<float *>(arr) + slot[u], 1.0f, keep);
             else if (kMode == 1) red_add_keep(static_cast<double *>(arr) + slot[u], 1.0, keep);
+            else if (kMode == 4) acc += atom_add_keep(static_cast<float *>(arr) + slot[u], 1.0f, keep);
             else acc += __ldcg(static_cast<const float *>(arr) + slot[u]);
         }
     }
-    if (kMode == 2 && acc == -1.0f) *sink = acc;   // never true for a zeroed array: keeps the loads
+    if ((kMode == 2 || kMode == 4) && acc == -1.0f) *sink = acc;   // never true (values >= 0): keeps the results
 }
 
 }  // namespace
@@ -70,7 +73,7 @@ using namespace di;
 extern "C" DI_API di_status di_probe_l2(int mode, int64_t slots, int64_t ops, double *ops_per_s, double *seconds,
                                         void *stream) {
     clear_error();
-    if (mode < 0 || mode > 3) { set_error("di_probe_l2: mode %d outside [0, 3]", mode); return DI_EINVAL; }
+    if (mode < 0 || mode > 4) { set_error("di_probe_l2: mode %d outside [0, 4]", mode); return DI_EINVAL; }
     if (slots < 1024 || slots > (int64_t(1) << 30) || (slots & (slots - 1))) {
         set_error("di_probe_l2: slots = %lld must be a power of two in [2^10, 2^30]", (long long)slots);
         return DI_EINVAL;
@@ -82,7 +85,8 @@ extern "C" DI_API di_status di_probe_l2(int mode, int64_t slots, int64_t ops, do
     DI_CUDA_TRY(cudaGetDevice(&dev));
     DI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const void *fn = mode == 0 ? (const void *)k_probe<0> : mode == 1 ? (const void *)k_probe<1>
-                   : mode == 2 ? (const void *)k_probe<2> : (const void *)k_probe<3>;
+                   : mode == 2 ? (const void *)k_probe<2> : mode == 3 ? (const void *)k_probe<3>
+                                                                       : (const void *)k_probe<4>;
     DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kProbeThreads, 0));
     const int grid = std::max(1, per_sm) * sms;
     const int64_t threads = (int64_t)grid * kProbeThreads;
@@ -115,7 +119,8 @@ extern "C" DI_API di_status di_probe_l2(int mode, int64_t slots, int64_t ops, do
             case 0: k_probe<0><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
             case 1: k_probe<1><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
             case 2: k_probe<2><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
-            default: k_probe<3><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
+            case 3: k_probe<3><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
+            default: k_probe<4><<<grid, kProbeThreads, 0, s>>>(arr, mask, (int)iters, seed, sink); break;
         }
         cudaEventRecord(e1, s);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { fail(e, "k_probe"); goto done; }

@@ -87,12 +87,15 @@ template <bool kCG, typename T>
 __device__ __forceinline__ T ld_mut(const T *p) { return kCG ? __ldcg(p) : __ldcs(p); }
 
 // Dynamic shared memory of the frontier push (propagations 3 and 7): the hot
-// slots (padded to 4 words), then the fluid window of kPushWin + 2R words
-// (none when R = 0).
+// slots (padded to 4 words), then either the fluid window of kPushWin + 2R
+// words (none when R = 0) or, for the slice-sweep variant, its queue
+// (kSliceQueueCap node ids).
 __host__ __device__ inline int push_hot_pad(int n_hot) { return (n_hot + 3) & ~3; }
 template <typename FT>
-__host__ __device__ inline size_t push_smem(int n_hot, int R) {
-    return (size_t)(push_hot_pad(n_hot) + (R > 0 ? kPushWin + 2 * R : 0)) * sizeof(FT);
+__host__ __device__ inline size_t push_smem(int n_hot, int R, bool slice = false) {
+    const size_t win = R > 0 ? (size_t)(kPushWin + 2 * R) * sizeof(FT) : 0;
+    const size_t queue = slice ? (size_t)kSliceQueueCap * sizeof(int32_t) : 0;
+    return (size_t)push_hot_pad(n_hot) * sizeof(FT) + (win > queue ? win : queue);
 }
 
 // ------------------------------------------------------------------ init (cold start)
@@ -413,6 +416,7 @@ __device__ __noinline__ void scan_control(const SolveDesc *__restrict__ desc, So
         // (a resweep) or at T / alpha, or, after an empty first pass, at the
         // first T / alpha^k <= max |F|
         push = nf;
+        if (nf > 0) st->T_push = T;   // the selection's T, which the push's slice sweeps use
         const int level0 = level;
         threshold_step(desc->resweeps, nf > 0, alpha, tm, T, phase, level, since);
         if (level != level0 && refine_due(desc, st, since, ts * est)) rec = 1;
@@ -424,6 +428,7 @@ __device__ __noinline__ void scan_control(const SolveDesc *__restrict__ desc, So
     st->max_scan = tm;
     st->nfront = 0;
     st->tile_ctr = 0;
+    st->tiles_done = 0;
     st->dang_acc = 0.0;                 // every CTA added it before this, the last one
     st->push_count = push;
     st->T = T;
@@ -469,6 +474,21 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
     scan_control(desc, st, part_sum, part_max, gridDim.x, h_while, h_rec, ctl);
 }
 
+// %globaltimer (ns), and acquire / release accesses of a flag at GPU scope
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Push of the asynchronous design, for every frontier node i: f =
 // atomicExch(F_i, 0) (fluid that arrives after the exchange waits for a
 // later level), H_i += f in FP64, and F_k += (d / outdeg_i) f for every
@@ -476,7 +496,21 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_level(
 // nodes; a row is pushed by its thread (outdeg <= 16), by a warp (<= 512)
 // or by the whole CTA.  Targets of very high in-degree are accumulated in
 // shared memory per CTA and flushed once.
-template <typename FT, bool kCG = false>
+// kSlice (slice sweeps): once every frontier tile is claimed, each CTA
+// sweeps its own slice of the nodes (about n / gridDim consecutive ids) at
+// the level's selection threshold, up to desc->slice_sweeps times, and
+// diffuses what it finds through a shared-memory queue: the nodes whose
+// fluid crossed T while the level pushed, which the sequential sweep of
+// Sec. 2.4 diffuses in the same sweep.  No CTA waits for another: a node
+// that crosses T after its slice was swept keeps its fluid for the next
+// selection.  A CTA starts its first sweep once the pushes of every
+// frontier tile are done (a counter the tiles' CTAs advance after a fence):
+// all tiles are claimed by then, so every CTA it waits for is running, and
+// the wait gives up after desc->wait_ns, sweeping what has landed.  A node
+// may be drained twice in a level (a frontier tile still running and a slice
+// sweep; the second drain takes what arrived since, often nothing), so H_i
+// is updated with an FP64 atomic add.
+template <typename FT, bool kCG = false, bool kSlice = false>
 __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                               const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
                                               const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node,
@@ -487,11 +521,15 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     FT *s_hot = reinterpret_cast<FT *>(smem_raw);
     // fluid window of the tile: targets in [lo - R, lo - R + span) with lo the
     // tile's first frontier node (span = kPushWin + 2R, 0 when R = 0)
-    const int R = desc->win_R;
+    const int R = kSlice ? 0 : desc->win_R;
     const unsigned span = R > 0 ? (unsigned)(kPushWin + 2 * R) : 0u;
     FT *s_win = s_hot + push_hot_pad(n_hot);
-    __shared__ unsigned s_tile;
-    __shared__ int s_qn;
+    // slice-sweep queue (kSlice), in place of the window
+    int32_t *s_sq = reinterpret_cast<int32_t *>(s_hot + push_hot_pad(n_hot));
+    __shared__ unsigned s_pair;   // thread 0's tile claims: the pair, the next of the two, frontier exhausted
+    __shared__ int s_sub, s_gdone;
+    __shared__ int s_qn, s_src, s_first, s_sqn, s_sbase, s_sbt, s_sweep, s_waited;
+    __shared__ long long s_pos, s_seg;
     __shared__ int32_t s_qb[kPushThreads], s_qe[kPushThreads];
     __shared__ FT s_qw[kPushThreads];
     __shared__ double s_dang;    // fluid drained from dangling nodes (1/N completion)
@@ -500,12 +538,27 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     double *__restrict__ H = desc->H;
     const int64_t n = desc->n_nodes;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_dang = 0.0;   // ordered before any add by the loop's first barrier
+    // the CTA's slice [s_lo, s_hi), a multiple of 4 nodes long (vector loads;
+    // the fluid vector is padded with zeros to a multiple of 4)
+    const int64_t per = kSlice ? ((n + gridDim.x - 1) / gridDim.x + 3) / 4 * 4 : 0;
+    const int64_t s_lo = kSlice ? min(n, (int64_t)blockIdx.x * per) : 0;
+    const int64_t s_hi = kSlice ? min(n, s_lo + per) : 0;
+    if (threadIdx.x == 0) {   // ordered before any use by the loop's first barrier
+        s_dang = 0.0;
+        s_sub = 2;
+        s_gdone = 0;
+        s_sqn = 0;
+        s_sweep = 0;
+        s_waited = 0;
+        s_pos = s_lo;
+    }
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
     for (unsigned q = threadIdx.x; q < span; q += kPushThreads) s_win[q] = FT(0);
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max, warp_max = desc->warp_max;
-    unsigned long long my_edges = 0, my_nodes = 0, my_reds = 0;
+    const int sweeps = kSlice ? desc->slice_sweeps : 0;
+    const FT Tc = kSlice ? thr_cast(__ldcg(&st->T_push), FT(0)) : FT(0);
+    unsigned long long my_edges = 0, my_nodes = 0, my_reds = 0, my_slice = 0;
     int64_t wlo = 0;
 
     auto push1 = [&](int32_t c, FT w) {
@@ -522,38 +575,139 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
         }
     };
 
-    // tiles are claimed two at a time (one atomic on the shared counter per
-    // 512 frontier entries) and pushed one after the other
-    unsigned pair = 0;
-    int sub = 2;
+    // thread 0 picks the work of each step: a frontier tile (tiles are claimed
+    // two at a time, one atomic on the shared counter per 512 entries); with
+    // kSlice, a full queue batch first, then once the frontier is exhausted
+    // the slice's segments of 1024 nodes (select into the queue), the queue's
+    // rest after each sweep, and the next sweep
     for (;;) {
-        if (sub == 2) {
-            if (threadIdx.x == 0) s_tile = atomicAdd(&st->tile_ctr, 2u);
-            sub = 0;
+        if (threadIdx.x == 0) {
+            s_qn = 0;
+            int src = 2;
+            const int qn = kSlice ? min(s_sqn, kSliceQueueCap) : 0;
+            if (kSlice && qn >= kPushThreads) {
+                src = 1;
+            } else if (!s_gdone) {
+                if (s_sub == 2) {
+                    s_pair = atomicAdd(&st->tile_ctr, 2u);
+                    s_sub = 0;
+                }
+                const int64_t first = (int64_t)(s_pair + s_sub) * kPushThreads;
+                ++s_sub;
+                if (first < count) {
+                    src = 0;
+                    s_first = (int)first;
+                } else {
+                    s_gdone = 1;
+                }
+            }
+            if (kSlice && src == 2 && s_gdone) {
+                if (!s_waited && sweeps > 0) {
+                    // the frontier's pushes first (bounded by the timer and a poll count)
+                    const unsigned ntiles = (unsigned)((count + kPushThreads - 1) / kPushThreads);
+                    const unsigned long long t0 = global_ns(), limit = desc->wait_ns;
+                    const unsigned long long max_polls = (limit >> 5) + 1024ull;
+                    unsigned long long polls = 0;
+                    while (ld_acquire_gpu(&st->tiles_done) < ntiles && global_ns() - t0 <= limit &&
+                           ++polls <= max_polls)
+                        __nanosleep(64);
+                    s_waited = 1;
+                }
+                while (s_sweep < sweeps) {
+                    if (s_pos < s_hi) {
+                        src = 3;
+                        s_seg = s_pos;
+                        s_pos += 4 * kPushThreads;
+                        break;
+                    }
+                    if (qn > 0) {
+                        src = 1;
+                        break;
+                    }
+                    ++s_sweep;   // the slice is swept and its finds are pushed: sweep again
+                    s_pos = s_lo;
+                }
+            }
+            if (src == 1) {   // the queue's top batch
+                const int bt = min(qn, kPushThreads);
+                s_sbase = qn - bt;
+                s_sbt = bt;
+                s_sqn = qn - bt;
+            }
+            s_src = src;
         }
-        if (threadIdx.x == 0) s_qn = 0;
         __syncthreads();
-        pair = s_tile;
-        const int64_t first = (int64_t)(pair + sub) * kPushThreads;
-        ++sub;
-        if (first >= count) break;
-        // the frontier of a CTA's scan slice is in node order, so in a dense
-        // level the tile's nodes (and most of their near targets) fall in the window
-        if (span) wlo = (int64_t)ld_mut<kCG>(front + first) - R;
-        const int64_t idx = first + threadIdx.x;
+        const int src = s_src;
+        if (src == 2) break;
+        if (kSlice && src == 3) {
+            // select |F_i| >= T over 1024 nodes of the slice into the queue (reads
+            // past L1: the other CTAs' pushes land in L2)
+            const int64_t i0 = s_seg + 4 * (int64_t)threadIdx.x;
+            unsigned msk = 0;
+            if (i0 < s_hi) {
+                Vec4<FT> f;
+                f.load_cg(F + i0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const FT a = fabs(f.v[j]);
+                    if (i0 + j < s_hi && a >= Tc && a > FT(0)) msk |= 1u << j;
+                }
+            }
+            const int c = __popc(msk);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int base = 0;
+            if (lane == 31 && incl > 0) base = atomicAdd(&s_sqn, incl);
+            int pos = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((msk >> j) & 1u) {
+                    if (pos < kSliceQueueCap) s_sq[pos] = static_cast<int32_t>(i0 + j);   // a full queue drops
+                    ++pos;
+                }
+            __syncthreads();
+            continue;
+        }
+        int32_t node = -1;
+        if (src == 0) {
+            const int64_t first = s_first;
+            // the frontier of a CTA's scan slice is in node order, so in a dense
+            // level the tile's nodes (and most of their near targets) fall in the window
+            if (span) wlo = (int64_t)ld_mut<kCG>(front + first) - R;
+            const int64_t idx = first + threadIdx.x;
+            if (idx < count) node = ld_mut<kCG>(front + idx);
+        } else if (kSlice && (int)threadIdx.x < s_sbt) {
+            node = s_sq[s_sbase + threadIdx.x];
+        }
         int32_t b = 0, e = 0;
         FT w = FT(0);
-        if (idx < count) {
-            const int32_t i = ld_mut<kCG>(front + idx);
+        if (node >= 0) {
+            const int32_t i = node;
             b = __ldcs(rp + i);
             e = __ldcs(rp + i + 1);
             const FT f = atomic_exch_keep(F + i, FT(0), keep);
             const double fd = static_cast<double>(f);
-            __stcs(H + i, ld_mut<kCG>(H + i) + fd);   // i appears once per frontier
-            if (e == b && desc->dangling) atomicAdd(&s_dang, fd);   // 1/N completion
+            if (kSlice) {
+                if (f != FT(0)) {
+                    atomicAdd(H + i, fd);   // a node may be drained twice in a level
+                    if (e == b && desc->dangling) atomicAdd(&s_dang, fd);
+                    my_nodes += 1;
+                    my_edges += static_cast<unsigned long long>(e - b);
+                    my_slice += src == 1 ? 1u : 0u;
+                } else {
+                    e = b;   // drained already: nothing to send
+                }
+            } else {
+                __stcs(H + i, ld_mut<kCG>(H + i) + fd);   // i appears once per frontier
+                if (e == b && desc->dangling) atomicAdd(&s_dang, fd);   // 1/N completion
+                my_nodes += 1;
+                my_edges += static_cast<unsigned long long>(e - b);
+            }
             w = f * __ldcs(scale + i);
-            my_nodes += 1;
-            my_edges += static_cast<unsigned long long>(e - b);
         }
         const int deg = e - b;
         if (deg <= thread_max) {
@@ -562,10 +716,10 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
         }
         unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
         while (wm) {
-            const int src = __ffs(wm) - 1;
+            const int src_lane = __ffs(wm) - 1;
             wm &= wm - 1;
-            const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
-            const FT mw = __shfl_sync(0xffffffffu, w, src);
+            const int32_t mb = __shfl_sync(0xffffffffu, b, src_lane), me = __shfl_sync(0xffffffffu, e, src_lane);
+            const FT mw = __shfl_sync(0xffffffffu, w, src_lane);
             auto pw = [&](int32_t c) { push1(c, mw); };
             push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
         }
@@ -584,19 +738,24 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             push_range<2>(pcol, (int64_t)hb + threadIdx.x, he, kPushThreads, pw);
         }
         __syncthreads();
+        if (kSlice && src == 0 && threadIdx.x == 0) {
+            __threadfence();   // the tile's adds, ordered by the barrier, before the count
+            atomicAdd(&st->tiles_done, 1u);
+        }
         // flush the window and clear it: consecutive threads, consecutive nodes
         // (coalesced reductions, eight FP32 or four FP64 words per sector)
         for (unsigned q = threadIdx.x; q < span; q += kPushThreads) {
             const FT v = s_win[q];
             s_win[q] = FT(0);
-            const int64_t node = wlo + q;
-            const bool go = v != FT(0) && node >= 0 && node < n;
+            const int64_t wnode = wlo + q;
+            const bool go = v != FT(0) && wnode >= 0 && wnode < n;
             const unsigned m = __ballot_sync(0xffffffffu, go);
             if (lane == 0) {
-                constexpr int per = 32 / (int)sizeof(FT);
-                for (int g = 0; g < 32; g += per) my_reds += ((m >> g) & ((1u << per) - 1u)) ? 1u : 0u;
+                constexpr int per_sector = 32 / (int)sizeof(FT);
+                for (int g = 0; g < 32; g += per_sector)
+                    my_reds += ((m >> g) & ((1u << per_sector) - 1u)) ? 1u : 0u;
             }
-            if (go) red_add_keep(F + node, v, keep);
+            if (go) red_add_keep(F + wnode, v, keep);
         }
     }
     __syncthreads();
@@ -607,33 +766,20 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             ++my_reds;
         }
     }
-    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->red_ops, my_reds);
+    cta_add_counts(&st->node_diff, my_nodes, &st->edge_diff, my_edges, &st->red_ops, my_reds,
+                   kSlice ? &st->slice_nodes : nullptr, my_slice);
     if (threadIdx.x == 0 && s_dang != 0.0) atomicAdd(&st->dang_acc, s_dang);
 }
 
-template <typename FT>
+template <typename FT, bool kSlice>
 __global__ void __launch_bounds__(kPushThreads, 6)
     k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ front,
                  const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
                  const int32_t *__restrict__ hot_node, int n_hot, const FT *__restrict__ scale) {
-    push_frontier<FT>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
+    push_frontier<FT, false, kSlice>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
 }
 
 // ------------------------------------------------------------------ persistent level loop (propagation 7)
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Grid barrier of a cooperative launch (every CTA resident).  The last CTA to
 // arrive runs control() with all its threads (it sees every write made
@@ -694,7 +840,7 @@ __device__ __forceinline__ bool grid_barrier(SolveState *st, unsigned long long 
 // refinement) or the solve ended; a CUDA graph runs the residual in an IF
 // node and relaunches it in its WHILE node.  The controller also adds the
 // wall time of each phase (%globaltimer) to the solve state.
-template <typename FT>
+template <typename FT, bool kSlice>
 __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 4 : 6) k_levels_coop(
     const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, int32_t *__restrict__ front,
     const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol, const int32_t *__restrict__ hot_node, int n_hot,
@@ -716,7 +862,7 @@ __global__ void __launch_bounds__(kPushThreads, sizeof(FT) == 8 ? 4 : 6) k_level
         });
         if (!ok) break;
         if (__ldcg(&st->push_count) > 0) {
-            push_frontier<FT, true>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
+            push_frontier<FT, true, kSlice>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
             ok = grid_barrier(st, timeout_ns, [&] {
                 if (threadIdx.x == 0) {
                     const unsigned long long t = global_ns();
@@ -1399,8 +1545,12 @@ void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
         launch_ex(k_push_warp<FT>, push_grid(g), kPushThreads, g->n_hot * sizeof(FT), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
+    else if (g->push_slice)
+        launch_ex(k_push_async<FT, true>, push_grid(g, true), kPushThreads, push_smem<FT>(g->n_hot, 0, true), s,
+                  win, (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
+                  (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
     else
-        launch_ex(k_push_async<FT>, push_grid(g), kPushThreads, push_smem<FT>(g->n_hot, g->push_R), s, win,
+        launch_ex(k_push_async<FT, false>, push_grid(g), kPushThreads, push_smem<FT>(g->n_hot, g->push_R), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
 }
@@ -1466,8 +1616,12 @@ template <typename FT>
 di_status prepare_coop(di_graph *g) {
     const int fp64 = sizeof(FT) == 8;
     int per_sm = 0;
-    DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_coop<FT>, kPushThreads,
-                                                              push_smem<FT>(g->n_hot, g->push_R)));
+    if (g->push_slice)
+        DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_coop<FT, true>, kPushThreads,
+                                                                  push_smem<FT>(g->n_hot, 0, true)));
+    else
+        DI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_coop<FT, false>, kPushThreads,
+                                                                  push_smem<FT>(g->n_hot, g->push_R)));
     if (per_sm < 1) { set_error("persistent level loop: the kernel does not fit on an SM"); return DI_ECUDA; }
     // the push shape's CTAs per SM (di_tune) caps the grid, as for the push kernels
     if (g->tune.push_ctas_per_sm > 0) per_sm = std::min(per_sm, g->tune.push_ctas_per_sm);
@@ -1485,7 +1639,7 @@ void launch_coop(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cud
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g->grid_coop[fp64]);
     cfg.blockDim = dim3(kPushThreads);
-    cfg.dynamicSmemBytes = push_smem<FT>(g->n_hot, g->push_R);
+    cfg.dynamicSmemBytes = g->push_slice ? push_smem<FT>(g->n_hot, 0, true) : push_smem<FT>(g->n_hot, g->push_R);
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     int na = 0;
@@ -1499,9 +1653,14 @@ void launch_coop(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cud
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    cudaLaunchKernelEx(&cfg, k_levels_coop<FT>, (const SolveDesc *)ws.desc, ws.st, ws.front, (const int32_t *)g->rp,
-                       (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale, (int64_t)g->n,
-                       ws.part_sum, ws.part_max, timeout_ns, hw, hr, ctl);
+    if (g->push_slice)
+        cudaLaunchKernelEx(&cfg, k_levels_coop<FT, true>, (const SolveDesc *)ws.desc, ws.st, ws.front,
+                           (const int32_t *)g->rp, (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot,
+                           scale, (int64_t)g->n, ws.part_sum, ws.part_max, timeout_ns, hw, hr, ctl);
+    else
+        cudaLaunchKernelEx(&cfg, k_levels_coop<FT, false>, (const SolveDesc *)ws.desc, ws.st, ws.front,
+                           (const int32_t *)g->rp, (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot,
+                           scale, (int64_t)g->n, ws.part_sum, ws.part_max, timeout_ns, hw, hr, ctl);
 }
 
 template <typename FT>
@@ -1546,7 +1705,7 @@ void launch_pushw(di_graph *g, cudaStream_t s, int l2) {
 di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     SolverGraph &sg = g->sg[fp64];
     if (sg.built && sg.l2 == l2 && sg.prop == prop && sg.res_form == g->res_form && sg.grid_push == push_grid(g) &&
-        sg.timeout_ns == g->coop_timeout_ns && sg.grid_coop == g->grid_coop[fp64])
+        sg.timeout_ns == g->coop_timeout_ns && sg.grid_coop == g->grid_coop[fp64] && sg.slice == g->push_slice)
         return DI_OK;
     if (sg.built) {   // rebuilt with the other window setting
         cudaGraphExecDestroy(sg.exec);
@@ -1647,6 +1806,7 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     sg.grid_push = push_grid(g);
     sg.timeout_ns = g->coop_timeout_ns;
     sg.grid_coop = g->grid_coop[fp64];
+    sg.slice = g->push_slice;
     return DI_OK;
 }
 
@@ -1680,6 +1840,15 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
     if (o->exact_residual < 0 || o->exact_residual > 2) { set_error("di_solve: exact_residual = %d outside [0, 2]", o->exact_residual); return DI_EINVAL; }
     if (o->resweeps < 0 || o->resweeps > 8) { set_error("di_solve: resweeps = %d outside [0, 8]", o->resweeps); return DI_EINVAL; }
     if (o->selection < 0 || o->selection > 1) { set_error("di_solve: selection = %d outside [0, 1]", o->selection); return DI_EINVAL; }
+    if (o->slice_sweeps < -1 || o->slice_sweeps > 4) {
+        set_error("di_solve: slice_sweeps = %d outside [-1, 4]", o->slice_sweeps);
+        return DI_EINVAL;
+    }
+    if (o->slice_sweeps > 0 && ((o->propagation != 3 && o->propagation != 7) || o->selection != 0)) {
+        set_error("di_solve: slice sweeps need propagation 3 or 7 and selection 0 (got %d, %d)",
+                  o->propagation, o->selection);
+        return DI_EINVAL;
+    }
     if (o->dangling < 0 || o->dangling > 1) { set_error("di_solve: dangling = %d outside [0, 1]", o->dangling); return DI_EINVAL; }
     if (o->dangling == 1 && (o->propagation < 3 || o->exact_residual == 1)) {
         set_error("di_solve: the 1/N dangling completion needs propagation 3 to 7 and exact_residual 0 or 2 "
@@ -1696,8 +1865,8 @@ di_status check_solve_args(di_graph *g, const double *B, double d, double tol, d
 }  // namespace
 
 // Push grid: the occupancy maximum, or the tuned CTAs per SM below it.
-int push_grid(const di_graph *g) {
-    const int occ = g->grid_push;
+int push_grid(const di_graph *g, bool slice) {
+    const int occ = slice ? g->grid_push_slice : g->grid_push;
     const int want = g->tune.push_ctas_per_sm > 0 ? g->tune.push_ctas_per_sm * g->num_sms : occ;
     return std::max(1, std::min(occ, want));
 }
@@ -1720,8 +1889,10 @@ di_status ensure_workspace(di_graph *g) {
                                         g->num_sms);
         const int64_t chunks = (n + kChunkNodes - 1) / kChunkNodes;
         g->grid_pushw = (int)std::max<int64_t>(1, std::min<int64_t>(push, (chunks + 7) / 8));
-        g->grid_push = occupancy_grid((const void *)k_push_async<double>, kPushThreads,
+        g->grid_push = occupancy_grid((const void *)k_push_async<double, false>, kPushThreads,
                                       push_smem<double>(kMaxHot, kMaxWinR), g->num_sms);
+        g->grid_push_slice = occupancy_grid((const void *)k_push_async<double, true>, kPushThreads,
+                                           push_smem<double>(kMaxHot, 0, true), g->num_sms);
         const int flat = occupancy_grid((const void *)k_pull_flat<double>, kLevelThreads, 0, g->num_sms);
         const int64_t fchunks = (g->nnz + kFlatEdges - 1) / kFlatEdges;
         g->grid_flat =
@@ -1790,7 +1961,13 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         DI_TRY(fp64 ? prepare_tiled<double>(g) : prepare_tiled<float>(g));
     }
     g->push_R = 0;
-    if ((o.propagation == 3 || o.propagation == 7) && g->tune.push_window) {
+    // slice sweeps: -1 (auto) takes one where they apply and nothing else
+    // re-orders the level (no re-selection, no fluid window)
+    const bool frontier_push = o.propagation == 3 || o.propagation == 7;
+    const int slice_sweeps = o.slice_sweeps >= 0 ? o.slice_sweeps
+                           : (frontier_push && o.selection == 0 && o.resweeps == 0 && !g->tune.push_window) ? 1 : 0;
+    g->push_slice = frontier_push && slice_sweeps > 0;
+    if ((o.propagation == 3 || o.propagation == 7) && g->tune.push_window && !g->push_slice) {
         // the frontier push's fluid window (its radius follows the graph's locality)
         DI_TRY(ensure_window(g, s));
         g->push_R = g->win_R;
@@ -1825,6 +2002,8 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
     dh.dangling = o.dangling;
     dh.resweeps = o.propagation >= 3 ? o.resweeps : 0;
     dh.win_R = (o.propagation == 3 || o.propagation == 7) ? g->push_R : 0;
+    dh.slice_sweeps = g->push_slice ? slice_sweeps : 0;
+    dh.wait_ns = (unsigned long long)o.spin_limit * 1000ull;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));
@@ -1985,6 +2164,8 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
         stats->body_iterations = st.body_iters;
         stats->select_seconds = t_sel;
         stats->red_ops = (int64_t)st.red_ops;
+        stats->slice_nodes = (int64_t)st.slice_nodes;
+        stats->slice_sweeps = g->push_slice ? slice_sweeps : 0;
         if (o.propagation == 7) {
             // the persistent loop times its own phases on the device (%globaltimer), in
             // either loop mode: selection phases and push phases of every pass

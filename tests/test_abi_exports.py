@@ -54,7 +54,12 @@ def test_version_and_defaults(lib):
     assert o.warm_fallback == 1 and o.max_levels == 100000
     # the fields after the double keep their place in the C layout
     assert o.propagation == 3 and o.push_ratio == 8 and o.selection == 0 and o.spin_limit == 1 << 20
-    assert o.resweeps == 0   # the last field, after the stream pointer
+    assert o.resweeps == 0 and o.slice_sweeps == -1   # the last fields, after the stream pointer
+    # the C side writes every field the binding declares: start from all-ones bytes
+    raw = binding.di_opts()
+    ctypes.memset(ctypes.byref(raw), 0xFF, ctypes.sizeof(raw))
+    assert lib.di_opts_default(ctypes.byref(raw)) == binding.DI_OK
+    assert raw.resweeps == 0 and raw.slice_sweeps == -1 and raw.stream is None and raw.alpha == 1.5
 
 
 def test_invalid_arguments_are_rejected_before_gpu_work(lib):

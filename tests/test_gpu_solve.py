@@ -388,6 +388,128 @@ def test_resweeps_out_of_range_are_rejected(web10k):
     g.close()
 
 
+@pytest.mark.parametrize("prop", [3, 7])
+@pytest.mark.parametrize("sweeps", [1, 2, 4])
+def test_parity_every_slice_sweep_count(web10k, prop, sweeps):
+    # slice sweeps diffuse, in the same level, nodes whose fluid crossed T
+    # while the level pushed: another order of the diffusions, the same limit
+    # (Sec. 2: any order that keeps diffusing every node)
+    rp, col, b, x = web10k
+    for fp64, rel in ((False, 1e-6), (True, 1e-11)):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        h, st, f, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, slice_sweeps=sweeps)
+        assert np.abs(h - x).sum() <= rel * np.abs(x).sum(), (fp64, sweeps)
+        check_stop(rp, col, b, h, st, tol)
+        assert 0 < st.slice_nodes < st.node_diffusions
+
+
+def test_slice_sweeps_with_resweeps_and_persistent_timing(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    for prop, timing in ((3, 0), (3, 1), (7, 0), (7, 1)):
+        h, st, _, _ = solve(rp, col, b, tol, propagation=prop, slice_sweeps=1, resweeps=1, timing=timing)
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum(), (prop, timing)
+        check_stop(rp, col, b, h, st, tol)
+        assert st.slice_nodes > 0 and st.body_iterations >= st.levels
+
+
+@pytest.fixture(scope="module")
+def web100k():
+    spec = gg.GraphSpec(n=100_000, mean_deg=10.0, window=64, seed=0)
+    rp, col = gg.generate(spec)
+    b = gg.uniform_b(spec.n, D)
+    return rp, col, b, oracle_x(rp, col, b)
+
+
+def test_slice_sweeps_cut_the_diffusions(web100k):
+    # a level that selects its frontier first diffuses each node at most once;
+    # the sequential sweep also diffuses the nodes whose fluid crosses T before
+    # their turn.  Slice sweeps recover most of that: far fewer elementary
+    # diffusions to the same tolerance, and no more levels.
+    rp, col, b, x = web100k
+    tol = 1e-8 * b.sum()
+    runs = {}
+    for sweeps in (0, 1, 2):
+        h, st, _, _ = solve(rp, col, b, tol, propagation=3, slice_sweeps=sweeps)
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+        check_stop(rp, col, b, h, st, tol)
+        runs[sweeps] = st
+    assert runs[0].slice_nodes == 0
+    assert runs[1].edge_diffusions < 0.8 * runs[0].edge_diffusions
+    assert runs[2].edge_diffusions < 0.8 * runs[0].edge_diffusions
+    assert runs[1].levels <= runs[0].levels
+    # the oracle's sequential sweep, for scale (the same graph and tolerance)
+    seq = od.d_iteration(rp, col, b, D, tol=tol)
+    assert runs[1].edge_diffusions < 1.5 * seq.edge_diffusions   # measured: 1.22x
+
+
+def test_slice_sweeps_on_many_segments(web5m):
+    # about 5.5e3 nodes per CTA slice: several 1024-node segments and queue
+    # batches per sweep; two source blocks in the exact residual
+    rp, col, b = web5m
+    tol = 1e-8 * b.sum()
+    h0, st0, _, _ = solve(rp, col, b, tol, propagation=3)
+    h, st, _, _ = solve(rp, col, b, tol, propagation=3, slice_sweeps=2)
+    check_stop(rp, col, b, h, st, tol)
+    assert st.slice_nodes > 0 and st.edge_diffusions < st0.edge_diffusions
+    # both are within |F|_1 / (1 - d) of X, so within twice that of each other
+    assert np.abs(h - h0).sum() <= 2 * tol / (1 - D) * 1.01
+
+
+def test_slice_sweeps_on_tiny_and_ragged_graphs():
+    # fewer nodes than push CTAs: most slices are empty, the last is ragged
+    rng = np.random.default_rng(71)
+    for n in (1, 7, 1001):
+        rp, col = random_graph(n, rng)
+        b = rng.random(n) + 0.1
+        x = oracle_x(rp, col, b)
+        for fp64 in (False, True):
+            tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+            h, st, _, _ = solve(rp, col, b, tol, fp64=fp64, propagation=3, slice_sweeps=3)
+            assert np.abs(h - x).sum() <= (1e-11 if fp64 else 1e-6) * np.abs(x).sum(), (n, fp64)
+            check_stop(rp, col, b, h, st, tol)
+
+
+def test_slice_sweeps_with_dangling_completion_and_warm_start(web10k_completed):
+    rp, col, b, x = web10k_completed
+    tol = 1e-8 * b.sum()
+    for prop in (3, 7):
+        h, st, _, _ = solve(rp, col, b, tol, propagation=prop, dangling=1, slice_sweeps=1)
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+        check_stop_completed(rp, col, b, h, st, tol)
+        assert st.slice_nodes > 0
+    # a warm start: signed fluid, selected on |F_i|
+    rng = np.random.default_rng(45)
+    h0 = x * (1 + 0.05 * rng.standard_normal(len(x)))
+    h, st, _, _ = solve(rp, col, b, tol, h0=h0, propagation=3, dangling=1, slice_sweeps=2)
+    assert st.warm_used == 1
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop_completed(rp, col, b, h, st, tol)
+
+
+def test_slice_sweeps_turn_the_fluid_window_off(web10k):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    h, st, _, _ = solve(rp, col, b, tol, propagation=3, slice_sweeps=1, window=True)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    assert st.slice_nodes > 0 and st.red_ops > 0
+
+
+def test_slice_sweeps_rejections(web10k):
+    rp, col, b, _ = web10k
+    g = di.Graph.create(rp, col)
+    H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    bad = [dict(slice_sweeps=-2), dict(slice_sweeps=5)]
+    bad += [dict(slice_sweeps=1, propagation=p) for p in (0, 1, 2, 4, 5, 6)]
+    bad.append(dict(slice_sweeps=1, selection=1))
+    for opt in bad:
+        with pytest.raises(di.DiError) as e:
+            di.di_solve(g, dev(b), D, 1e-8, H, None, di.opts_default(**opt))
+        assert e.value.status == di.DI_EINVAL, opt
+    g.close()
+
+
 @pytest.mark.parametrize("prop", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_personalised_sparse_levels_every_mode(prop):
     # a personalised right-hand side keeps the early frontiers tiny (scatter levels)
