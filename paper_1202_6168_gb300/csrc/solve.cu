@@ -526,8 +526,10 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     FT *s_win = s_hot + push_hot_pad(n_hot);
     // slice-sweep queue (kSlice), in place of the window
     int32_t *s_sq = reinterpret_cast<int32_t *>(s_hot + push_hot_pad(n_hot));
-    __shared__ unsigned s_pair;   // thread 0's tile claims: the pair, the next of the two, frontier exhausted
-    __shared__ int s_sub, s_gdone;
+    // thread 0's claims: the claimed tiles [s_tile, s_tile + s_unit), the next of them, the
+    // number of claims, frontier exhausted
+    __shared__ long long s_tile;
+    __shared__ int s_unit, s_sub, s_claims, s_gdone;
     __shared__ int s_qn, s_src, s_first, s_sqn, s_sbase, s_sbt, s_sweep, s_waited;
     __shared__ long long s_pos, s_seg;
     __shared__ int32_t s_qb[kPushThreads], s_qe[kPushThreads];
@@ -545,7 +547,9 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     const int64_t s_hi = kSlice ? min(n, s_lo + per) : 0;
     if (threadIdx.x == 0) {   // ordered before any use by the loop's first barrier
         s_dang = 0.0;
-        s_sub = 2;
+        s_unit = 0;
+        s_sub = 0;
+        s_claims = 0;
         s_gdone = 0;
         s_sqn = 0;
         s_sweep = 0;
@@ -575,8 +579,13 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
         }
     };
 
-    // thread 0 picks the work of each step: a frontier tile (tiles are claimed
-    // two at a time, one atomic on the shared counter per 512 entries); with
+    // thread 0 picks the work of each step: a frontier tile.  Tiles are
+    // claimed in pairs, pushed one after the other (fluid a tile sends to the
+    // next tile's nodes then goes with them in the same level), while more
+    // than four pairs per CTA remain, and one at a time after that, so that
+    // the last tiles spread over the CTAs.  A CTA's first claim is its block
+    // index (no atomic at the start), later ones come from the shared
+    // counter.  With
     // kSlice, a full queue batch first, then once the frontier is exhausted
     // the slice's segments of 1024 nodes (select into the queue), the queue's
     // rest after each sweep, and the next sweep
@@ -588,12 +597,22 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             if (kSlice && qn >= kPushThreads) {
                 src = 1;
             } else if (!s_gdone) {
-                if (s_sub == 2) {
-                    s_pair = atomicAdd(&st->tile_ctr, 2u);
+                if (s_sub >= s_unit) {
+                    const int64_t ntiles = ((int64_t)count + kPushThreads - 1) / kPushThreads;
+                    const int64_t grid = gridDim.x;
+                    const int u0 = ntiles >= 2 * grid ? 2 : 1;   // the static first claim
+                    if (s_claims == 0) {
+                        s_unit = u0;
+                        s_tile = (int64_t)blockIdx.x * u0;
+                    } else {
+                        const int u = s_tile + 8 * grid < ntiles ? 2 : 1;
+                        s_unit = u;
+                        s_tile = grid * u0 + (int64_t)atomicAdd(&st->tile_ctr, (unsigned)u);
+                    }
+                    ++s_claims;
                     s_sub = 0;
                 }
-                const int64_t first = (int64_t)(s_pair + s_sub) * kPushThreads;
-                ++s_sub;
+                const int64_t first = (s_tile + s_sub++) * kPushThreads;
                 if (first < count) {
                     src = 0;
                     s_first = (int)first;
