@@ -312,11 +312,17 @@ DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double 
  * decided on the exact FP64 residual, which includes the fluid still owed.
  * B, H (out), F (out, may be NULL) are device vectors of n doubles as in
  * di_solve.  Supports FP32 fluid, a cold start, the plain selection and zero
- * dangling columns; opts->alpha, max_levels, recompute_drop and stream apply
- * (NULL opts = defaults).  pid_ops / pid_sends (host, K entries, may be
+ * dangling columns; opts->alpha, max_levels, recompute_drop, timing and
+ * stream apply (NULL opts = defaults).  timing = 1 runs the rounds
+ * host-driven, one synchronisation per round, with CUDA events that fill
+ * stats->select_seconds (k_pscan), level_seconds (selection, push and
+ * transmission) and recompute_seconds (the IF body's kernels).  pid_ops / pid_sends (host, K entries, may be
  * NULL) receive each PID's elementary diffusions (local children plus
  * transmitted external edges) and its number of transmissions.  1 <= K <= 64.
- * Synchronous; the rounds run on the device in one CUDA graph (WHILE node).
+ * Synchronous; the rounds run on the device in one CUDA graph (WHILE node),
+ * which is kept on the graph object (with the ranges of the last K and kind,
+ * the per-node range table and H_old) and reused by later calls; it is freed
+ * with the graph.
  */
 DI_API di_status di_solve_partitioned(di_graph *g, const double *B, double d, double tol, double *H,
                                       double *F, const di_opts *opts, int32_t K, int32_t kind,

@@ -180,6 +180,7 @@ struct Workspace {
     cudaEvent_t tev[64] = {};       // timing mode: 4 per level, 16 levels per batch
 };
 
+struct KpidCache;   // partition.cu: what di_solve_partitioned keeps on a graph
 }  // namespace di
 
 constexpr int kThreadMaxDegDefault = di::kThreadMaxDeg;
@@ -233,6 +234,7 @@ struct di_graph {
     int grid_coop[2] = {0, 0};
     unsigned long long coop_timeout_ns = 0;
     int push_R = 0;               // frontier push: window radius in use (0 = none)
+    di::KpidCache *kpid = nullptr;   // di_solve_partitioned: ranges, buffers and round graph of the last K
     int push_slice = 0;           // frontier push: the slice-sweep variant in use (opts.slice_sweeps > 0)
     int grid_push_slice = 0;      // occupancy grid of the slice-sweep variant
     // weighted selection (Sec. 2.4 score): 1 / ((in + 1)(out + 1)), built on first use
@@ -473,6 +475,7 @@ di_status ensure_window(di_graph *g, cudaStream_t s);
 // solve.cu
 di_status ensure_workspace(di_graph *g);
 int push_grid(const di_graph *g, bool slice = false);
+void free_kpid_cache(di_graph *g);   // partition.cu
 // tune.cu: validation of a push shape, candidates, and the JSON-lines cache
 di_status check_tune(const di_tune *t, const char *who);
 int tune_candidates(di_tune *out, int cap);

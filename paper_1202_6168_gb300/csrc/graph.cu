@@ -308,6 +308,7 @@ void free_graph(di_graph *g) {
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
         if (sg.graph) cudaGraphDestroy(sg.graph);
     }
+    free_kpid_cache(g);
     void *dev[] = {g->rp, g->pcol, g->hot_node, g->in_rp, g->in_col, g->long_rows, g->long_seg0,
                    g->seg_row, g->seg_beg, g->frows, g->fseg0, g->fseg_row, g->fseg_beg,
                    g->pl_rows, g->pl_seg_row, g->pl_seg_beg, g->pl_lrows, g->pl_lseg0, g->pl_b12_off,

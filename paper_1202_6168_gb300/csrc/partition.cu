@@ -34,6 +34,7 @@ namespace {
 
 constexpr int kMaxParts = 64;
 constexpr int kPThreads = 256;
+constexpr int kPThreadRow = 16;   // rows up to this many edges go to one thread, longer ones to a warp
 
 // Per-range state on the device.  Sums are cleared by the step that consumes them.
 struct PartState {
@@ -65,6 +66,18 @@ __device__ __forceinline__ unsigned long long double_to_bits(double v) {
 __device__ __forceinline__ int64_t cta_span(int64_t n) {
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     return (per + kPThreads - 1) / kPThreads * kPThreads;
+}
+
+// The range of node j: the last k with bounds[k] <= j (bounds in shared
+// memory, K + 1 entries, non-decreasing; at most 7 steps for K <= 64).
+__device__ __forceinline__ int range_of(const int64_t *s_b, int K, int64_t j) {
+    int lo = 0, hi = K;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (j >= s_b[mid]) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // F = B (FP32 fluid), H = H_old = 0, |B|_1, and T_k = max |B_i| over Omega_k.
@@ -128,43 +141,50 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
                                                      PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
                                                      int32_t *__restrict__ front, int64_t n,
                                                      cudaGraphConditionalHandle h_while,
-                                                     cudaGraphConditionalHandle h_rec) {
+                                                     cudaGraphConditionalHandle h_rec, int ctl) {
     if (st->done) {                                     // converged, capped or not finite: end the loop
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->push_count = 0;
             ps->any_send = 0;
-            cudaGraphSetConditional(h_rec, 0);
-            cudaGraphSetConditional(h_while, 0);
+            if (ctl == 1) {
+                cudaGraphSetConditional(h_rec, 0);
+                cudaGraphSetConditional(h_while, 0);
+            }
         }
         return;
     }
     __shared__ float s_T[kMaxParts];
     __shared__ double s_r[kMaxParts];
-    __shared__ unsigned long long s_m[kMaxParts], s_sel[kMaxParts];
+    __shared__ unsigned s_m[kMaxParts], s_sel[kMaxParts];   // max |F| as float bits (non-negative floats order like integers)
     __shared__ int s_warp[kPThreads / 32];
     __shared__ int s_base;
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_T[k] = __double2float_ru(ps->T[k]);   // |F_i| >= T in FP32: T rounded up to a float
         s_r[k] = 0.0;
-        s_m[k] = 0ull;
-        s_sel[k] = 0ull;
+        s_m[k] = 0u;
+        s_sel[k] = 0u;
     }
     __syncthreads();
     const float *__restrict__ F = static_cast<const float *>(desc->F);
     const int64_t span = cta_span(n), lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < n ? lo + span : n;
-    // pass 1: sums and counts
-    double r = 0.0, mx = 0.0;
-    unsigned long long nsel = 0;
+    // pass 1: sums and counts, per thread for its current range; a range
+    // change flushes the thread's sums (rare: a CTA's span meets few range
+    // bounds), the last flush is reduced over the warp first when all its
+    // lanes end in the same range
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double r = 0.0;
+    float mx = 0.f;
+    unsigned nsel = 0;
     int cur = -1, mine = 0;
     auto flush = [&]() {
         if (cur < 0) return;
         if (r != 0.0) atomicAdd(&s_r[cur], r);
-        if (mx > 0.0) atomicMax(&s_m[cur], double_to_bits(mx));
+        if (mx > 0.f) atomicMax(&s_m[cur], __float_as_uint(mx));
         if (nsel) atomicAdd(&s_sel[cur], nsel);
         r = 0.0;
-        mx = 0.0;
+        mx = 0.f;
         nsel = 0;
     };
     for (int64_t i = lo + threadIdx.x; i < hi; i += kPThreads) {
@@ -175,15 +195,23 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         }
         const float a = fabsf(F[i]);
         r += a;
-        mx = fmax(mx, static_cast<double>(a));
+        mx = fmaxf(mx, a);
         if (a >= s_T[k] && a > 0.f) {
             ++nsel;
             ++mine;
         }
     }
-    flush();
+    {
+        const int c0 = __shfl_sync(0xffffffffu, cur, 0);
+        if (__all_sync(0xffffffffu, cur == c0)) {
+            r = warp_sum(r);
+            mx = warp_max(mx);
+            nsel = warp_sum(nsel);
+            if (lane != 0) cur = -1;   // lane 0 flushes the warp's sums
+        }
+        flush();
+    }
     // exclusive prefix of the per-thread counts, one atomic for the CTA's slice
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -211,8 +239,8 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         if (s_r[k] != 0.0) atomicAdd(&ps->r[k], s_r[k]);
-        if (s_m[k]) atomicMax(&ps->m[k], s_m[k]);
-        if (s_sel[k]) atomicAdd(&ps->sel[k], s_sel[k]);
+        if (s_m[k]) atomicMax(&ps->m[k], double_to_bits(static_cast<double>(__uint_as_float(s_m[k]))));
+        if (s_sel[k]) atomicAdd(&ps->sel[k], (unsigned long long)s_sel[k]);
     }
     if (!last_block(&ps->scan_blocks)) return;
 
@@ -277,8 +305,10 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         st->tile_ctr = 0;
         ps->any_send = any;
         s_stop = stop || done;
-        cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
-        if (done) cudaGraphSetConditional(h_while, 0);
+        if (ctl == 1) {   // in a CUDA graph; host-driven rounds read st instead
+            cudaGraphSetConditional(h_rec, rec ? 1u : 0u);
+            if (done) cudaGraphSetConditional(h_while, 0);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) ps->send[k] = s_stop ? 0 : s_snd[k];
@@ -295,14 +325,17 @@ __device__ __forceinline__ int32_t push_target(const int32_t *__restrict__ pcol,
 // The fluid owed to other ranges, |w| per external child, accumulates in s_k.
 __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                      PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     const int64_t *__restrict__ bounds,
                                                      const int32_t *__restrict__ front, const int32_t *__restrict__ rp,
                                                      const int32_t *__restrict__ pcol,
                                                      const int32_t *__restrict__ hot_node, int n_hot,
                                                      const float *__restrict__ scale) {
     const int count = st->push_count;
     if (count == 0) return;
-    __shared__ double s_s[kMaxParts];
-    __shared__ unsigned long long s_ops[kMaxParts];
+    // per range: fluid owed (FP32 in the CTA, FP64 across CTAs) and diffusions
+    __shared__ float s_s[kMaxParts];
+    __shared__ unsigned s_ops[kMaxParts];
+    __shared__ int64_t s_b[kMaxParts + 1];
     // targets of very high in-degree (hot slots, encoded -1 - slot in pcol)
     // are accumulated per CTA in shared memory and flushed once, as in the
     // main push: hot-node ranges, then the sums
@@ -311,9 +344,10 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
     uint8_t *s_hot_part = reinterpret_cast<uint8_t *>(s_hot + n_hot);
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        s_s[k] = 0.0;
-        s_ops[k] = 0ull;
+        s_s[k] = 0.f;
+        s_ops[k] = 0u;
     }
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) s_b[k] = bounds[k];
     for (int sl = threadIdx.x; sl < n_hot; sl += blockDim.x) {
         s_hot[sl] = 0.f;
         s_hot_part[sl] = part_of[hot_node[sl]];
@@ -325,6 +359,24 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_nodes = 0, my_edges = 0;
+    // one target of a row of range k (children [lo, hi)): inside the range it
+    // is diffused (hot targets in their shared-memory slot), outside it only
+    // counts towards the fluid owed
+    auto push1 = [&](int32_t c, float w, int k, int64_t lo, int64_t hi, unsigned &loc, unsigned &ext) {
+        if (c < 0) {
+            if (s_hot_part[-1 - c] == k) {
+                atomicAdd(&s_hot[-1 - c], w);
+                ++loc;
+            } else {
+                ++ext;
+            }
+        } else if (c >= lo && c < hi) {
+            red_add(F + c, w);
+            ++loc;
+        } else {
+            ++ext;
+        }
+    };
     for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
         const int64_t idx = base + lane;
         int32_t b = 0, e = 0;
@@ -341,57 +393,59 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
             my_nodes += 1;
         }
         const int deg = e - b;
-        if (deg <= 32) {
-            unsigned long long loc = 0, ext = 0;
-            for (int32_t q = b; q < e; ++q) {
-                const int32_t c = pcol[q];
-                if (c < 0) {
-                    if (s_hot_part[-1 - c] == k) {
-                        atomicAdd(&s_hot[-1 - c], w);
-                        ++loc;
-                    } else {
-                        ++ext;
-                    }
-                } else if (part_of[c] == k) {
-                    red_add(F + c, w);
-                    ++loc;
-                } else {
-                    ++ext;
-                }
+        unsigned loc = 0, ext = 0;
+        if (deg <= kPThreadRow) {
+            // the row by its thread, 8 column loads in flight
+            const int64_t lo = s_b[k], hi = s_b[k + 1];
+            for (int32_t q0 = b; q0 < e; q0 += 8) {
+                int32_t c[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) c[t] = q0 + t < e ? __ldcs(pcol + q0 + t) : 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (q0 + t < e) push1(c[t], w, k, lo, hi, loc, ext);
             }
-            if (loc) atomicAdd(&s_ops[k], loc);
-            if (ext) atomicAdd(&s_s[k], fabs(static_cast<double>(w)) * static_cast<double>(ext));
-            my_edges += loc;
         }
-        unsigned big = __ballot_sync(0xffffffffu, deg > 32);
+        {
+            // the thread rows' counts (all lanes; zero for the others), reduced
+            // over the warp first when its lanes share a range
+            float owed = fabsf(w) * static_cast<float>(ext);
+            int kk = k;
+            const int k0 = __shfl_sync(0xffffffffu, k, 0);
+            if (__all_sync(0xffffffffu, k == k0)) {
+                loc = warp_sum(loc);
+                owed = warp_sum(owed);
+                if (lane != 0) kk = -1;
+            }
+            if (kk >= 0) {
+                if (loc) atomicAdd(&s_ops[kk], loc);
+                if (owed != 0.f) atomicAdd(&s_s[kk], owed);
+                my_edges += loc;
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, deg > kPThreadRow);
         while (big) {
+            // a longer row by the whole warp, 4 column loads in flight per lane
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const float mw = __shfl_sync(0xffffffffu, w, src);
             const int mk = __shfl_sync(0xffffffffu, k, src);
-            unsigned long long loc = 0, ext = 0;
-            for (int32_t q = mb + lane; q < me; q += 32) {
-                const int32_t c = pcol[q];
-                if (c < 0) {
-                    if (s_hot_part[-1 - c] == mk) {
-                        atomicAdd(&s_hot[-1 - c], mw);
-                        ++loc;
-                    } else {
-                        ++ext;
-                    }
-                } else if (part_of[c] == mk) {
-                    red_add(F + c, mw);
-                    ++loc;
-                } else {
-                    ++ext;
-                }
+            const int64_t lo = s_b[mk], hi = s_b[mk + 1];
+            unsigned loc = 0, ext = 0;
+            for (int32_t q0 = mb + lane; q0 < me; q0 += 4 * 32) {
+                int32_t c[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) c[t] = q0 + 32 * t < me ? __ldcs(pcol + q0 + 32 * t) : 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (q0 + 32 * t < me) push1(c[t], mw, mk, lo, hi, loc, ext);
             }
             loc = warp_sum(loc);
             ext = warp_sum(ext);
             if (lane == 0) {
                 if (loc) atomicAdd(&s_ops[mk], loc);
-                if (ext) atomicAdd(&s_s[mk], fabs(static_cast<double>(mw)) * static_cast<double>(ext));
+                if (ext) atomicAdd(&s_s[mk], fabsf(mw) * static_cast<float>(ext));
                 my_edges += loc;
             }
         }
@@ -408,8 +462,8 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
         if (v != 0.f) red_add(F + hot_node[sl], v);
     }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        if (s_s[k] != 0.0) atomicAdd(&ps->s[k], s_s[k]);
-        if (s_ops[k]) atomicAdd(&ps->ops[k], s_ops[k]);
+        if (s_s[k] != 0.f) atomicAdd(&ps->s[k], static_cast<double>(s_s[k]));
+        if (s_ops[k]) atomicAdd(&ps->ops[k], (unsigned long long)s_ops[k]);
     }
 }
 
@@ -418,20 +472,23 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
 // and H_old_i = H_i.  The last CTA rescales the receivers' thresholds.
 __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st,
                                                      PartState *__restrict__ ps, const uint8_t *__restrict__ part_of,
+                                                     const int64_t *__restrict__ bounds,
                                                      const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
                                                      const int32_t *__restrict__ hot_node,
                                                      const double *__restrict__ scale64, double *__restrict__ H_old,
                                                      int64_t n) {
     if (!ps->any_send) return;
     __shared__ int s_send[kMaxParts];
-    __shared__ double s_recv[kMaxParts];
-    __shared__ unsigned long long s_ops[kMaxParts];
+    __shared__ float s_recv[kMaxParts];       // received per range (FP32 in the CTA, FP64 across CTAs)
+    __shared__ unsigned s_ops[kMaxParts];
+    __shared__ int64_t s_b[kMaxParts + 1];
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_send[k] = ps->send[k];
-        s_recv[k] = 0.0;
-        s_ops[k] = 0ull;
+        s_recv[k] = 0.f;
+        s_ops[k] = 0u;
     }
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) s_b[k] = bounds[k];
     __syncthreads();
     float *__restrict__ F = static_cast<float *>(desc->F);
     const double *__restrict__ H = desc->H;
@@ -439,6 +496,27 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_edges = 0;
+    // one child j of a transmitting row of range k: sent if outside the range;
+    // the amount a receiving range gets is summed in registers over runs of
+    // children in the same range (rkj, racc) and added to shared memory per run
+    int rkj = -1;
+    float racc = 0.f;
+    auto flush_recv = [&]() {
+        if (rkj >= 0) atomicAdd(&s_recv[rkj], racc);
+        rkj = -1;
+        racc = 0.f;
+    };
+    auto send1 = [&](int32_t j, float w, int64_t lo, int64_t hi, unsigned &sent) {
+        if (j >= lo && j < hi) return;
+        red_add(F + j, w);
+        const int kj = range_of(s_b, K, j);
+        if (kj != rkj) {
+            flush_recv();
+            rkj = kj;
+        }
+        racc += fabsf(w);
+        ++sent;
+    };
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
         const int64_t i = base + lane;
         int32_t b = 0, e = 0;
@@ -457,41 +535,51 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
             }
         }
         const int deg = e - b;
-        if (deg <= 32) {
-            for (int32_t q = b; q < e; ++q) {
-                const int32_t j = push_target(pcol, hot_node, q);
-                const int kj = part_of[j];
-                if (kj == k) continue;
-                red_add(F + j, w);
-                atomicAdd(&s_recv[kj], fabs(static_cast<double>(w)));
-                atomicAdd(&s_ops[k], 1ull);
-                ++my_edges;
+        if (deg <= kPThreadRow) {
+            const int64_t lo = s_b[k], hi = s_b[k + 1];
+            unsigned sent = 0;
+            for (int32_t q0 = b; q0 < e; q0 += 8) {
+                int32_t c[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) c[t] = q0 + t < e ? push_target(pcol, hot_node, q0 + t) : 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (q0 + t < e) send1(c[t], w, lo, hi, sent);
             }
+            if (sent) atomicAdd(&s_ops[k], sent);
+            my_edges += sent;
         }
-        unsigned big = __ballot_sync(0xffffffffu, deg > 32);
+        unsigned big = __ballot_sync(0xffffffffu, deg > kPThreadRow);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int32_t mb = __shfl_sync(0xffffffffu, b, src), me = __shfl_sync(0xffffffffu, e, src);
             const float mw = __shfl_sync(0xffffffffu, w, src);
             const int mk = __shfl_sync(0xffffffffu, k, src);
-            for (int32_t q = mb + lane; q < me; q += 32) {
-                const int32_t j = push_target(pcol, hot_node, q);
-                const int kj = part_of[j];
-                if (kj == mk) continue;
-                red_add(F + j, mw);
-                atomicAdd(&s_recv[kj], fabs(static_cast<double>(mw)));
-                atomicAdd(&s_ops[mk], 1ull);
-                ++my_edges;
+            const int64_t lo = s_b[mk], hi = s_b[mk + 1];
+            unsigned sent = 0;
+            for (int32_t q0 = mb + lane; q0 < me; q0 += 4 * 32) {
+                int32_t c[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) c[t] = q0 + 32 * t < me ? push_target(pcol, hot_node, q0 + 32 * t) : 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (q0 + 32 * t < me) send1(c[t], mw, lo, hi, sent);
+            }
+            sent = warp_sum(sent);
+            if (lane == 0 && sent) {
+                atomicAdd(&s_ops[mk], sent);
+                my_edges += sent;
             }
         }
     }
+    flush_recv();
     my_edges = warp_sum(my_edges);
     if (lane == 0 && my_edges) atomicAdd(&st->edge_diff, my_edges);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        if (s_recv[k] != 0.0) atomicAdd(&ps->recv[k], s_recv[k]);
-        if (s_ops[k]) atomicAdd(&ps->ops[k], s_ops[k]);
+        if (s_recv[k] != 0.f) atomicAdd(&ps->recv[k], static_cast<double>(s_recv[k]));
+        if (s_ops[k]) atomicAdd(&ps->ops[k], (unsigned long long)s_ops[k]);
     }
     if (!last_block(&ps->send_blocks)) return;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -550,6 +638,34 @@ std::vector<int64_t> partition_bounds(const std::vector<int32_t> &rp, int64_t n,
 }
 
 }  // namespace
+
+// What di_solve_partitioned keeps on a graph between calls.
+struct KpidCache {
+    int K = -1, kind = -1;            // ranges loaded in part_of / bounds
+    int grid = 0, res_form = -1;      // the round graph was built for these
+    std::vector<int64_t> bounds_h;
+    uint8_t *part_of = nullptr;       // [n] range of every node
+    int64_t *bounds = nullptr;        // [kMaxParts + 1] range bounds
+    double *H_old = nullptr;          // [n] history at the last transmission
+    PartState *ps = nullptr, *ps_h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+void free_kpid_cache(di_graph *g) {
+    KpidCache *kc = g->kpid;
+    if (!kc) return;
+    if (kc->exec) cudaGraphExecDestroy(kc->exec);
+    if (kc->graph) cudaGraphDestroy(kc->graph);
+    if (kc->part_of) cudaFree(kc->part_of);
+    if (kc->bounds) cudaFree(kc->bounds);
+    if (kc->H_old) cudaFree(kc->H_old);
+    if (kc->ps) cudaFree(kc->ps);
+    if (kc->ps_h) cudaFreeHost(kc->ps_h);
+    delete kc;
+    g->kpid = nullptr;
+}
+
 }  // namespace di
 
 using namespace di;
@@ -588,34 +704,35 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
         DI_CUDA_TRY(cudaMemsetAsync(ws.F32, 0, npad * sizeof(float), s));
     }
 
-    // ranges and the node -> range table
-    std::vector<int32_t> rp(n + 1);
-    DI_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DI_CUDA_TRY(cudaStreamSynchronize(s));
-    const std::vector<int64_t> bounds = partition_bounds(rp, n, K, kind);
-    std::vector<uint8_t> part(n > 0 ? n : 1, 0);
-    for (int k = 0; k < K; ++k)
-        for (int64_t i = bounds[k]; i < bounds[k + 1]; ++i) part[i] = static_cast<uint8_t>(k);
-
-    struct Scratch {
-        uint8_t *part_of = nullptr;
-        double *H_old = nullptr;
-        PartState *ps = nullptr, *ps_h = nullptr;
-        ~Scratch() {
-            if (part_of) cudaFree(part_of);
-            if (H_old) cudaFree(H_old);
-            if (ps) cudaFree(ps);
-            if (ps_h) cudaFreeHost(ps_h);
-        }
-    } sc;
-    DI_CUDA_TRY(cudaMalloc(&sc.part_of, part.size()));
-    DI_CUDA_TRY(cudaMalloc(&sc.H_old, (n > 0 ? n : 1) * sizeof(double)));
-    DI_CUDA_TRY(cudaMalloc(&sc.ps, sizeof(PartState)));
-    DI_CUDA_TRY(cudaMallocHost(&sc.ps_h, sizeof(PartState)));
-    DI_CUDA_TRY(cudaMemcpyAsync(sc.part_of, part.data(), part.size(), cudaMemcpyHostToDevice, s));
-    std::memset(sc.ps_h, 0, sizeof(PartState));
-    sc.ps_h->K = K;
-    DI_CUDA_TRY(cudaMemcpyAsync(sc.ps, sc.ps_h, sizeof(PartState), cudaMemcpyHostToDevice, s));
+    // ranges, node -> range table and round graph: kept on the graph object
+    // and reused while K, the partition kind, the grid and the residual form
+    // are unchanged (the buffers do not depend on K, so a new K only reloads
+    // the tables)
+    if (!g->kpid) g->kpid = new KpidCache();
+    KpidCache &kc = *g->kpid;
+    if (!kc.part_of) {
+        DI_CUDA_TRY(cudaMalloc(&kc.part_of, n > 0 ? n : 1));
+        DI_CUDA_TRY(cudaMalloc(&kc.bounds, (kMaxParts + 1) * sizeof(int64_t)));
+        DI_CUDA_TRY(cudaMalloc(&kc.H_old, (n > 0 ? n : 1) * sizeof(double)));
+        DI_CUDA_TRY(cudaMalloc(&kc.ps, sizeof(PartState)));
+        DI_CUDA_TRY(cudaMallocHost(&kc.ps_h, sizeof(PartState)));
+    }
+    if (kc.K != K || kc.kind != kind) {
+        std::vector<int32_t> rp(n + 1);
+        DI_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        DI_CUDA_TRY(cudaStreamSynchronize(s));
+        kc.bounds_h = partition_bounds(rp, n, K, kind);
+        std::vector<uint8_t> part(n > 0 ? n : 1, 0);
+        for (int k = 0; k < K; ++k)
+            for (int64_t i = kc.bounds_h[k]; i < kc.bounds_h[k + 1]; ++i) part[i] = static_cast<uint8_t>(k);
+        DI_CUDA_TRY(cudaMemcpy(kc.part_of, part.data(), part.size(), cudaMemcpyHostToDevice));
+        DI_CUDA_TRY(cudaMemcpy(kc.bounds, kc.bounds_h.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        kc.K = K;
+        kc.kind = kind;
+    }
+    std::memset(kc.ps_h, 0, sizeof(PartState));
+    kc.ps_h->K = K;
+    DI_CUDA_TRY(cudaMemcpyAsync(kc.ps, kc.ps_h, sizeof(PartState), cudaMemcpyHostToDevice, s));
 
     // descriptor and state (the previous call on this graph has completed: every solve synchronises)
     SolveDesc &dh = *ws.desc_h;
@@ -645,68 +762,116 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
     const int64_t parts = std::max({g->grid_scan, g->grid_select, residual_partials(g), g->grid_push});
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>({(int64_t)per_sm * g->num_sms, (n + kPThreads - 1) / kPThreads, parts}));
-    k_pinit<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, sc.ps, sc.part_of, sc.H_old, n, ws.part_sum);
-    DI_CUDA_TRY(cudaGetLastError());
+    k_pinit<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, kc.ps, kc.part_of, kc.H_old, n, ws.part_sum);
     DI_CUDA_TRY(cudaGetLastError());
 
-    // the rounds as a CUDA graph: WHILE [scan -> push -> send -> IF(hold -> exact residual)]
-    struct GraphGuard {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        cudaStream_t cs = nullptr;
-        ~GraphGuard() {
-            if (exec) cudaGraphExecDestroy(exec);
-            if (graph) cudaGraphDestroy(graph);
-            if (cs) cudaStreamDestroy(cs);
-        }
-    } gg;
-    DI_CUDA_TRY(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
-    DI_CUDA_TRY(cudaGraphCreate(&gg.graph, 0));
-    cudaGraphConditionalHandle h_while, h_if;
-    DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_while, gg.graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams wp = {};
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = h_while;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    cudaGraphNode_t wnode;
-    DI_CUDA_TRY(cudaGraphAddNode(&wnode, gg.graph, nullptr, nullptr, 0, &wp));
-    cudaGraph_t body = wp.conditional.phGraph_out[0];
-    DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_if, body, 0, 0));
-    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(gg.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    k_pscan<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, n, h_while, h_if);
     const size_t hot_smem = (size_t)g->n_hot * (sizeof(float) + 1);
-    k_ppush<<<grid, kPThreads, hot_smem, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, ws.front, g->rp, g->pcol,
-                                                  g->hot_node, g->n_hot, g->s32);
-    k_psend<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.part_of, g->rp, g->pcol, g->hot_node, g->s64,
-                                           sc.H_old, n);
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    cudaGraph_t capg = nullptr, ended = nullptr;
-    DI_CUDA_TRY(cudaStreamGetCaptureInfo(gg.cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = h_if;
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    cudaGraphNode_t inode;
-    DI_CUDA_TRY(cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip));
-    DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(gg.cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    DI_CUDA_TRY(cudaStreamEndCapture(gg.cs, &ended));
-    DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(gg.cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeThreadLocal));
-    k_phold<<<grid, kPThreads, 0, gg.cs>>>(ws.desc, ws.st, sc.ps, sc.H_old, n);
-    launch_residual(g, 0, RES_LEVEL, gg.cs);
-    DI_CUDA_TRY(cudaStreamEndCapture(gg.cs, &ended));
-    DI_CUDA_TRY(cudaGetLastError());
-    DI_CUDA_TRY(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
-    DI_CUDA_TRY(cudaGraphLaunch(gg.exec, s));
+    double t_scan = 0.0, t_push = 0.0, t_send = 0.0, t_res = 0.0;
+    int timed_rounds = 0;
+    if (o.timing) {
+        // host-driven rounds with a CUDA event around every kernel (profilers
+        // see the kernels; the residual kernels return at once unless k_pscan
+        // asked for a recompute)
+        cudaEvent_t ev[5];
+        for (auto &e : ev) e = nullptr;
+        struct EventGuard {
+            cudaEvent_t *e;
+            ~EventGuard() {
+                for (int q = 0; q < 5; ++q)
+                    if (e[q]) cudaEventDestroy(e[q]);
+            }
+        } eg{ev};
+        for (auto &e : ev) DI_CUDA_TRY(cudaEventCreate(&e));
+        const cudaGraphConditionalHandle none = 0;
+        for (;;) {
+            DI_CUDA_TRY(cudaEventRecord(ev[0], s));
+            k_pscan<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, kc.ps, kc.part_of, ws.front, n, none, none, 2);
+            DI_CUDA_TRY(cudaEventRecord(ev[1], s));
+            k_ppush<<<grid, kPThreads, hot_smem, s>>>(ws.desc, ws.st, kc.ps, kc.part_of, kc.bounds, ws.front, g->rp,
+                                                      g->pcol, g->hot_node, g->n_hot, g->s32);
+            DI_CUDA_TRY(cudaEventRecord(ev[2], s));
+            k_psend<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, kc.ps, kc.part_of, kc.bounds, g->rp, g->pcol,
+                                               g->hot_node, g->s64, kc.H_old, n);
+            DI_CUDA_TRY(cudaEventRecord(ev[3], s));
+            k_phold<<<grid, kPThreads, 0, s>>>(ws.desc, ws.st, kc.ps, kc.H_old, n);
+            launch_residual(g, 0, RES_LEVEL, s);
+            DI_CUDA_TRY(cudaEventRecord(ev[4], s));
+            DI_CUDA_TRY(cudaGetLastError());
+            DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+            DI_CUDA_TRY(cudaStreamSynchronize(s));
+            float t[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < 4; ++q) DI_CUDA_TRY(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
+            t_scan += 1e-3 * t[0];
+            t_push += 1e-3 * t[1];
+            t_send += 1e-3 * t[2];
+            t_res += 1e-3 * t[3];
+            ++timed_rounds;
+            if (ws.st_h->done) break;
+        }
+    } else {
+    // the rounds as a CUDA graph: WHILE [scan -> push -> send -> IF(hold -> exact residual)]
+    if (!kc.exec || kc.grid != grid || kc.res_form != g->res_form) {
+        if (kc.exec) cudaGraphExecDestroy(kc.exec);
+        if (kc.graph) cudaGraphDestroy(kc.graph);
+        kc.exec = nullptr;
+        kc.graph = nullptr;
+        struct StreamGuard {
+            cudaStream_t cs = nullptr;
+            ~StreamGuard() {
+                if (cs) cudaStreamDestroy(cs);
+            }
+        } sg;
+        DI_CUDA_TRY(cudaStreamCreateWithFlags(&sg.cs, cudaStreamNonBlocking));
+        DI_CUDA_TRY(cudaGraphCreate(&kc.graph, 0));
+        cudaGraphConditionalHandle h_while, h_if;
+        DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_while, kc.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = h_while;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        DI_CUDA_TRY(cudaGraphAddNode(&wnode, kc.graph, nullptr, nullptr, 0, &wp));
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_if, body, 0, 0));
+        DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(sg.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        k_pscan<<<grid, kPThreads, 0, sg.cs>>>(ws.desc, ws.st, kc.ps, kc.part_of, ws.front, n, h_while, h_if, 1);
+        k_ppush<<<grid, kPThreads, hot_smem, sg.cs>>>(ws.desc, ws.st, kc.ps, kc.part_of, kc.bounds, ws.front, g->rp,
+                                                      g->pcol, g->hot_node, g->n_hot, g->s32);
+        k_psend<<<grid, kPThreads, 0, sg.cs>>>(ws.desc, ws.st, kc.ps, kc.part_of, kc.bounds, g->rp, g->pcol,
+                                               g->hot_node, g->s64, kc.H_old, n);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t capg = nullptr, ended = nullptr;
+        DI_CUDA_TRY(cudaStreamGetCaptureInfo(sg.cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams ip = {};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_if;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode;
+        DI_CUDA_TRY(cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip));
+        DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(sg.cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        DI_CUDA_TRY(cudaStreamEndCapture(sg.cs, &ended));
+        DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(sg.cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+        k_phold<<<grid, kPThreads, 0, sg.cs>>>(ws.desc, ws.st, kc.ps, kc.H_old, n);
+        launch_residual(g, 0, RES_LEVEL, sg.cs);
+        DI_CUDA_TRY(cudaStreamEndCapture(sg.cs, &ended));
+        DI_CUDA_TRY(cudaGetLastError());
+        DI_CUDA_TRY(cudaGraphInstantiate(&kc.exec, kc.graph, 0));
+        kc.grid = grid;
+        kc.res_form = g->res_form;
+    }
+    DI_CUDA_TRY(cudaGraphLaunch(kc.exec, s));
+    }
     DI_CUDA_TRY(cudaMemcpyAsync(ws.st_h, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     DI_CUDA_TRY(cudaStreamSynchronize(s));
     // k_pinit; the three kernels of every round, and of the round that ends
     // the loop; the IF body's when a recompute ran
-    long long launches = 1 + 3LL * (ws.st_h->body_iters + 1) + (1LL + residual_kernels(g)) * ws.st_h->recomputes;
+    long long launches = o.timing ? 1 + (4LL + residual_kernels(g)) * timed_rounds
+                                  : 1 + 3LL * (ws.st_h->body_iters + 1) + (1LL + residual_kernels(g)) * ws.st_h->recomputes;
     SolveState st = *ws.st_h;
     const bool refresh = st.done != 1 || (F != nullptr && st.recomputes == 0);
     if (refresh) {
@@ -717,14 +882,14 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
         DI_CUDA_TRY(cudaStreamSynchronize(s));
         st.r_exact = ws.st_h->r_exact;
     }
-    DI_CUDA_TRY(cudaMemcpyAsync(sc.ps_h, sc.ps, sizeof(PartState), cudaMemcpyDeviceToHost, s));
+    DI_CUDA_TRY(cudaMemcpyAsync(kc.ps_h, kc.ps, sizeof(PartState), cudaMemcpyDeviceToHost, s));
     DI_CUDA_TRY(cudaEventRecord(ws.ev1, s));
     DI_CUDA_TRY(cudaEventSynchronize(ws.ev1));
     float ms = 0.f;
     DI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
     for (int k = 0; k < K; ++k) {
-        if (pid_ops) pid_ops[k] = (int64_t)sc.ps_h->ops[k];
-        if (pid_sends) pid_sends[k] = (int64_t)sc.ps_h->sends[k];
+        if (pid_ops) pid_ops[k] = (int64_t)kc.ps_h->ops[k];
+        if (pid_sends) pid_sends[k] = (int64_t)kc.ps_h->sends[k];
     }
     di_status rc = DI_OK;
     if (st.done == 3 || !std::isfinite(st.r_exact)) {
@@ -748,6 +913,13 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
         stats->status = rc;
         stats->gpu_launches = launches;
         stats->body_iterations = st.body_iters;
+        if (o.timing) {
+            stats->select_seconds = t_scan;
+            stats->level_seconds = t_scan + t_push + t_send;
+            stats->recompute_seconds = t_res;
+            stats->level_launches = timed_rounds;
+            stats->recompute_launches = st.recomputes;
+        }
     }
     return rc;
 }

@@ -118,3 +118,37 @@ def test_rejects_unsupported_arguments(web10k):
             di.di_solve_partitioned(g, B, D, 1e-8, H, K, kind, None, di.opts_default(**opt))
         assert e.value.status == di.DI_EINVAL
     g.close()
+
+
+def test_repeated_calls_on_one_graph_switch_ranges(web10k):
+    # the ranges, buffers and round graph stay on the graph between calls:
+    # changing K or the partition kind reloads the tables, and a plain solve
+    # in between (another exact-residual form) rebuilds the round graph
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    g = di.Graph.create(rp, col)
+    B = dev(b)
+    for K, kind, plain in ((4, 0, False), (4, 1, False), (2, 0, False), (2, 0, True), (64, 1, False),
+                           (4, 0, False), (4, 0, False)):
+        if plain:
+            Hp = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+            di.di_solve(g, B, D, tol, Hp, None, di.opts_default(exact_residual=1))
+        H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        rc, st, ops, sends = di.di_solve_partitioned(g, B, D, tol, H, K, kind, None, di.opts_default())
+        h = H.cpu().numpy()
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum(), (K, kind, plain)
+        check_stop(rp, col, b, h, st, tol)
+        assert len(ops) == K and all(o > 0 for o in ops)
+    g.close()
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_host_driven_rounds_match_and_time_the_kernels(web10k, K):
+    rp, col, b, x = web10k
+    tol = 1e-8 * b.sum()
+    h, st, ops, sends, f = run(rp, col, b, tol, K, 0, timing=1)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop(rp, col, b, h, st, tol)
+    assert 0 < st.select_seconds < st.level_seconds
+    assert st.recompute_seconds > 0 and st.level_launches >= st.body_iterations
+    assert st.recompute_launches == st.recomputes >= 1
