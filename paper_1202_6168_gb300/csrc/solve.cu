@@ -535,6 +535,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     __shared__ int32_t s_qb[kPushThreads], s_qe[kPushThreads];
     __shared__ FT s_qw[kPushThreads];
     __shared__ double s_dang;    // fluid drained from dangling nodes (1/N completion)
+    double my_dang = 0.0;        // this thread's share, added to s_dang once per warp at the end
 
     FT *__restrict__ F = static_cast<FT *>(desc->F);
     double *__restrict__ H = desc->H;
@@ -713,7 +714,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             if (kSlice) {
                 if (f != FT(0)) {
                     atomicAdd(H + i, fd);   // a node may be drained twice in a level
-                    if (e == b && desc->dangling) atomicAdd(&s_dang, fd);
+                    if (e == b && desc->dangling) my_dang += fd;
                     my_nodes += 1;
                     my_edges += static_cast<unsigned long long>(e - b);
                     my_slice += src == 1 ? 1u : 0u;
@@ -722,7 +723,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
                 }
             } else {
                 __stcs(H + i, ld_mut<kCG>(H + i) + fd);   // i appears once per frontier
-                if (e == b && desc->dangling) atomicAdd(&s_dang, fd);   // 1/N completion
+                if (e == b && desc->dangling) my_dang += fd;   // 1/N completion
                 my_nodes += 1;
                 my_edges += static_cast<unsigned long long>(e - b);
             }
@@ -777,6 +778,8 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             if (go) red_add_keep(F + wnode, v, keep);
         }
     }
+    my_dang = warp_sum(my_dang);   // 1/N completion: one shared add per warp
+    if ((threadIdx.x & 31) == 0 && my_dang != 0.0) atomicAdd(&s_dang, my_dang);
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
         const FT v = s_hot[sl];
@@ -926,6 +929,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FT *s_hot = reinterpret_cast<FT *>(smem_raw);
     __shared__ double s_dang;    // fluid drained from dangling nodes (1/N completion)
+    double my_dang = 0.0;        // this thread's share, added to s_dang once per warp at the end
     if (threadIdx.x == 0) s_dang = 0.0;
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
     __syncthreads();
@@ -963,7 +967,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
                 w = f * __ldcs(scale + i);
                 my_nodes += 1;
                 my_edges += static_cast<unsigned long long>(e - b);
-                if (e == b && desc->dangling) atomicAdd(&s_dang, static_cast<double>(f));   // 1/N completion
+                if (e == b && desc->dangling) my_dang += static_cast<double>(f);   // 1/N completion
             }
             const int deg = e - b;
             if (deg <= thread_max) {
@@ -981,6 +985,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_warp(const SolveDesc *__r
             }
         }
     }
+    my_dang = warp_sum(my_dang);   // 1/N completion: one shared add per warp
+    if ((threadIdx.x & 31) == 0 && my_dang != 0.0) atomicAdd(&s_dang, my_dang);
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
         const FT v = s_hot[sl];
@@ -1036,6 +1042,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
     const FT u = dangling ? static_cast<FT>(desc->d * st->dang_acc / (double)n) : FT(0);
     __shared__ double s_dang;
     if (threadIdx.x == 0) s_dang = 0.0;
+    double my_dang = 0.0;        // this thread's share, added to s_dang once per warp at the end
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max;
     auto push1 = [&](int32_t c, FT w) {
@@ -1069,7 +1076,7 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
                 w = f * __ldcs(scale + idx);
                 my_nodes += 1;
                 my_edges += static_cast<unsigned long long>(e - b);
-                if (e == b && dangling) atomicAdd(&s_dang, static_cast<double>(f));
+                if (e == b && dangling) my_dang += static_cast<double>(f);
             }
             const int deg = e - b;
             if (deg <= thread_max) {
@@ -1087,6 +1094,8 @@ __global__ void __launch_bounds__(kPushThreads) k_level_fused(
             }
         }
     }
+    my_dang = warp_sum(my_dang);   // 1/N completion: one shared add per warp
+    if ((threadIdx.x & 31) == 0 && my_dang != 0.0) atomicAdd(&s_dang, my_dang);
     __syncthreads();
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) {
         const FT hv = s_hot[sl];
