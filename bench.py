@@ -810,6 +810,8 @@ def run_batch(args, world, rank, local):
     stream = torch.cuda.current_stream()
     prec = "f64" if args.fp64 else "f32"
     opts = di.opts_default(fluid_fp64=1 if args.fp64 else 0, stream=stream.cuda_stream)
+    if args.slice_sweeps is not None:
+        opts.slice_sweeps = args.slice_sweeps
     graphs = [di.Graph.create(rp, col, stream=stream) for rp, col in csrs]
     batch = di.Batch(graphs, [4] * len(graphs), stream=stream)
     B, H, tols = [], [], []

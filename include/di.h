@@ -358,7 +358,12 @@ DI_API di_status di_batch_info(const di_batch *b, int *n_items, int64_t *n_union
  * L1 tolerance on |B + P H - H|_1 (host array).  d in (0, 1).  opts as for
  * di_solve (warm_start must be 0; timing = 1 runs the levels host-driven;
  * dangling = 1 completes the dangling columns of each item's graph by 1/n_g,
- * n_g the nodes of that graph).
+ * n_g the nodes of that graph; slice_sweeps: 0 .. 4 sweeps of each push
+ * CTA's slice of the union at each item's selection threshold after the
+ * frontier, as in di_solve, on the items whose frontier holds at least 1/32
+ * of their nodes; -1 (default) none: with mostly sparse frontiers the
+ * per-level wait costs more than it saves; spin_limit bounds the push's wait
+ * for the frontier before a sweep).
  * item_stats (host array of n_items, may be NULL) receives each item's
  * statistics; total (may be NULL) the sums (levels = max over items,
  * gpu_launches and seconds of the whole call).  Returns DI_OK when every

@@ -561,7 +561,9 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
     for (unsigned q = threadIdx.x; q < span; q += kPushThreads) s_win[q] = FT(0);
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max, warp_max = desc->warp_max;
-    const int sweeps = kSlice ? desc->slice_sweeps : 0;
+    // sweeps only after a dense frontier (at least 1/kSliceDensity of the nodes):
+    // on a sparse one the fluid that crossed T is scarce and a sweep reads all of F
+    const int sweeps = kSlice && (int64_t)count * kSliceDensity >= n ? desc->slice_sweeps : 0;
     const FT Tc = kSlice ? thr_cast(__ldcg(&st->T_push), FT(0)) : FT(0);
     unsigned long long my_edges = 0, my_nodes = 0, my_reds = 0, my_slice = 0;
     int64_t wlo = 0;

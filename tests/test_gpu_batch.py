@@ -59,7 +59,8 @@ def rhs_for(n, k, rng):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-def test_batch_matches_oracle_item_by_item(mixed_graphs, fp64):
+@pytest.mark.parametrize("sweeps", [-1, 0, 2])
+def test_batch_matches_oracle_item_by_item(mixed_graphs, fp64, sweeps):
     rng = np.random.default_rng(5)
     graphs = [di.Graph.create(rp, col) for rp, col in mixed_graphs]
     nrhs = [3, 2, 1, 3, 1, 2, 3]
@@ -74,7 +75,9 @@ def test_batch_matches_oracle_item_by_item(mixed_graphs, fp64):
     tols = [(1e-11 * (1 - D) if fp64 else 1e-8) * b.sum() for _, _, b in items]
     B = [dev(b) for _, _, b in items]
     H = [torch.full((len(b),), float("nan"), dtype=torch.float64, device="cuda") for _, _, b in items]
-    rc, st, tot = di.di_solve_batched(batch, B, D, tols, H, di.opts_default(fluid_fp64=1 if fp64 else 0))
+    # slice sweeps (-1: the default, one) change the order of the diffusions, not the limit
+    rc, st, tot = di.di_solve_batched(batch, B, D, tols, H,
+                                      di.opts_default(fluid_fp64=1 if fp64 else 0, slice_sweeps=sweeps))
     torch.cuda.synchronize()
     rel = 1e-11 if fp64 else 1e-6
     for t, ((rp, col, b), h, s, tol) in enumerate(zip(items, H, st, tols)):
@@ -256,4 +259,38 @@ def test_batch_dangling_completion_matches_the_completed_oracle(fp64):
         assert abs(s.resid_l1 - r_cpu) <= 1e-9 * max(r_cpu, tol) + floor
     batch.close()
     for g in gs:
+        g.close()
+
+
+def test_batch_slice_sweeps_cut_the_diffusions(mixed_graphs):
+    # the batched push sweeps its CTA slices at each item's threshold after
+    # the frontier, as the single-graph push does: fewer elementary
+    # diffusions to the same tolerances, and the per-item counts add up
+    rng = np.random.default_rng(9)
+    graphs = [di.Graph.create(rp, col) for rp, col in mixed_graphs]
+    nrhs = [2] * len(graphs)
+    batch = di.Batch(graphs, nrhs)
+    items = []
+    for (rp, col), r in zip(mixed_graphs, nrhs):
+        for k in range(r):
+            items.append((rp, col, rhs_for(len(rp) - 1, k, rng)))
+    tols = [1e-8 * b.sum() for _, _, b in items]
+    B = [dev(b) for _, _, b in items]
+    edges = {}
+    for sweeps in (0, 1):
+        H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
+        rc, st, tot = di.di_solve_batched(batch, B, D, tols, H, di.opts_default(slice_sweeps=sweeps))
+        for (rp, col, b), h, s, tol in zip(items, H, st, tols):
+            stop_ok(rp, col, b, h.cpu().numpy(), tol, s.resid_l1)
+            assert s.node_diffusions > 0   # (a source at a dangling node diffuses no edge)
+        assert tot.edge_diffusions == sum(s.edge_diffusions for s in st)
+        edges[sweeps] = tot.edge_diffusions
+    assert edges[1] < 0.85 * edges[0], edges
+    for bad in (-2, 5):
+        H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
+        with pytest.raises(di.DiError) as e:
+            di.di_solve_batched(batch, B, D, tols, H, di.opts_default(slice_sweeps=bad))
+        assert e.value.status == di.DI_EINVAL
+    batch.close()
+    for g in graphs:
         g.close()
