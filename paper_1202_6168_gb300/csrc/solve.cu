@@ -800,6 +800,9 @@ __global__ void __launch_bounds__(kPushThreads, 6)
     k_push_async(const SolveDesc *__restrict__ desc, SolveState *__restrict__ st, const int32_t *__restrict__ front,
                  const int32_t *__restrict__ rp, const int32_t *__restrict__ pcol,
                  const int32_t *__restrict__ hot_node, int n_hot, const FT *__restrict__ scale) {
+    // launched with programmatic dependence on the selection kernel: wait for
+    // it (and its writes) before anything is read; a no-op otherwise
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     push_frontier<FT, false, kSlice>(desc, st, front, rp, pcol, hot_node, n_hot, scale);
 }
 
@@ -1544,7 +1547,10 @@ const cudaAccessPolicyWindow *l2_window(di_graph *g, int which, int fp64, int en
     return g->win_ok[slot] ? &g->win[slot] : nullptr;
 }
 
-template <typename Kern, typename... Args>
+// kPDL: programmatic dependent launch - the kernel's CTAs may be scheduled
+// while the previous kernel on the stream finishes; the kernel itself waits
+// for that kernel's completion (griddep_wait) before it reads anything.
+template <bool kPDL = false, typename Kern, typename... Args>
 void launch_ex(Kern kernel, int grid, int block, size_t smem, cudaStream_t s, const cudaAccessPolicyWindow *win,
                Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -1552,13 +1558,20 @@ void launch_ex(Kern kernel, int grid, int block, size_t smem, cudaStream_t s, co
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    int na = 0;
     if (win) {
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow = *win;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na].val.accessPolicyWindow = *win;
+        ++na;
     }
+    if (kPDL) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = na ? attr : nullptr;
+    cfg.numAttrs = na;
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -1576,11 +1589,11 @@ void launch_async(di_graph *g, cudaStream_t s, cudaGraphConditionalHandle hw, cu
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
     else if (g->push_slice)
-        launch_ex(k_push_async<FT, true>, push_grid(g, true), kPushThreads, push_smem<FT>(g->n_hot, 0, true), s,
+        launch_ex<true>(k_push_async<FT, true>, push_grid(g, true), kPushThreads, push_smem<FT>(g->n_hot, 0, true), s,
                   win, (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
     else
-        launch_ex(k_push_async<FT, false>, push_grid(g), kPushThreads, push_smem<FT>(g->n_hot, g->push_R), s, win,
+        launch_ex<true>(k_push_async<FT, false>, push_grid(g), kPushThreads, push_smem<FT>(g->n_hot, g->push_R), s, win,
                   (const SolveDesc *)ws.desc, ws.st, (const int32_t *)ws.front, (const int32_t *)g->rp,
                   (const int32_t *)g->pcol, (const int32_t *)g->hot_node, g->n_hot, scale);
 }
