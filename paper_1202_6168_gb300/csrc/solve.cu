@@ -736,14 +736,42 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             auto pw = [&](int32_t c) { push1(c, w); };
             push_range<8>(pcol, b, e, 1, pw);
         }
-        unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
-        while (wm) {
-            const int src_lane = __ffs(wm) - 1;
-            wm &= wm - 1;
-            const int32_t mb = __shfl_sync(0xffffffffu, b, src_lane), me = __shfl_sync(0xffffffffu, e, src_lane);
-            const FT mw = __shfl_sync(0xffffffffu, w, src_lane);
-            auto pw = [&](int32_t c) { push1(c, mw); };
-            push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
+        const bool wrow = deg > thread_max && deg <= warp_max;
+        if (__any_sync(0xffffffffu, wrow)) {
+            // the warp's medium rows as one edge-parallel range: lane L's row holds
+            // the edges [ex_L, ex_L + len_L) of the concatenation, and each lane
+            // finds the row of its edge by a binary search over the offsets, so
+            // the rows' column loads are in flight together (4 per lane)
+            const int len = wrow ? deg : 0;
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int ex = incl - len, total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int q0 = 0; q0 < total; q0 += 4 * 32) {
+                int32_t c[4];
+                FT cw[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = q0 + 32 * k + lane;
+                    int owner = 0;   // the last lane whose offset is <= q (rows are non-empty)
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int cand = owner + step;
+                        const int cex = __shfl_sync(0xffffffffu, ex, cand & 31);
+                        if (cand < 32 && cex <= q) owner = cand;
+                    }
+                    const int32_t ob = __shfl_sync(0xffffffffu, b, owner);
+                    const int oex = __shfl_sync(0xffffffffu, ex, owner);
+                    cw[k] = __shfl_sync(0xffffffffu, w, owner);
+                    c[k] = q < total ? __ldcs(pcol + (int64_t)ob + (q - oex)) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (q0 + 32 * k + lane < total) push1(c[k], cw[k]);
+            }
         }
         if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
