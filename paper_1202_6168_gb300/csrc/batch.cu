@@ -345,7 +345,10 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
 // atomic add.  The control counts the frontier's diffusions at its
 // selection; the push counts those of its sweeps, per thread over runs of
 // the same item (a slice is consecutive nodes) and summed over the warp
-// before the items' counters.
+// before the items' counters.  A sweep starts when half the frontier's
+// tiles are done, so a frontier node it drains before its own tile is
+// counted twice: with sweeps the items' counts can overstate the work a
+// little.
 constexpr int kBSliceCap = 1536;   // slice-sweep queue entries per CTA (>= 1024 + kBThreads)
 
 template <typename FT>
@@ -436,7 +439,9 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
                         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(done_tiles) : "l"(&st->tiles_done)
                                      : "memory");
                         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                        if (done_tiles >= ntiles || now - t0 > limit || ++polls > max_polls) break;
+                        if ((unsigned long long)done_tiles * 100ull >= (unsigned long long)ntiles * kSliceWaitPct ||
+                            now - t0 > limit || ++polls > max_polls)
+                            break;
                         __nanosleep(64);
                     }
                     s_waited = 1;

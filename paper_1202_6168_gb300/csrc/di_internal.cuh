@@ -60,6 +60,7 @@ constexpr int kMaxWinR = 32 << (kWinBins - 1);
 constexpr int kPushWin = 1024;      // frontier push: nodes of a tile's fluid window beyond its radius
 constexpr int kSliceQueueCap = 1536;   // frontier push: entries of a CTA's slice-sweep queue
 constexpr int kSliceDensity = 32;      // slice sweeps follow frontiers of at least 1/32 of the nodes
+constexpr int kSliceWaitPct = 50;      // a slice sweep starts once this share of the frontier's tiles is done
 
 // ------------------------------------------------------------------ solver state
 

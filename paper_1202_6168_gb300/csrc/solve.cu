@@ -503,10 +503,11 @@ __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
 // fluid crossed T while the level pushed, which the sequential sweep of
 // Sec. 2.4 diffuses in the same sweep.  No CTA waits for another: a node
 // that crosses T after its slice was swept keeps its fluid for the next
-// selection.  A CTA starts its first sweep once the pushes of every
-// frontier tile are done (a counter the tiles' CTAs advance after a fence):
-// all tiles are claimed by then, so every CTA it waits for is running, and
-// the wait gives up after desc->wait_ns, sweeping what has landed.  A node
+// selection.  A CTA starts its first sweep once the pushes of half the
+// frontier's tiles are done (a counter the tiles' CTAs advance after a
+// fence; kSliceWaitPct): all tiles are claimed by then, so every CTA it waits
+// for is running, and the wait gives up after desc->wait_ns, sweeping what
+// has landed.  A node
 // may be drained twice in a level (a frontier tile still running and a slice
 // sweep; the second drain takes what arrived since, often nothing), so H_i
 // is updated with an FP64 atomic add.
@@ -625,12 +626,15 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             }
             if (kSlice && src == 2 && s_gdone) {
                 if (!s_waited && sweeps > 0) {
-                    // the frontier's pushes first (bounded by the timer and a poll count)
+                    // half of the frontier's pushes first (bounded by the timer and a poll
+                    // count): the sweep then overlaps the frontier's tail, and a node the
+                    // tail pushes over T later keeps its fluid for the next selection
                     const unsigned ntiles = (unsigned)((count + kPushThreads - 1) / kPushThreads);
                     const unsigned long long t0 = global_ns(), limit = desc->wait_ns;
                     const unsigned long long max_polls = (limit >> 5) + 1024ull;
                     unsigned long long polls = 0;
-                    while (ld_acquire_gpu(&st->tiles_done) < ntiles && global_ns() - t0 <= limit &&
+                    while ((unsigned long long)ld_acquire_gpu(&st->tiles_done) * 100ull < (unsigned long long)ntiles * kSliceWaitPct &&
+                           global_ns() - t0 <= limit &&
                            ++polls <= max_polls)
                         __nanosleep(64);
                     s_waited = 1;
