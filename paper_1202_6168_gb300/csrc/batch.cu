@@ -183,12 +183,15 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
     FT *__restrict__ F = static_cast<FT *>(desc->F);
     const int dangling = desc->dangling;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    __shared__ int s_cnt[kBItems * (kBThreads / 32)];
-    __shared__ int s_base, s_total;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    // one warp per 2048-node chunk, no block barrier: lane l reads nodes
+    // c0 + 128 j + 4 l + v (j = 0..15, v = 0..3) with vector loads, and
+    // the selected ids go to the frontier in node order (a warp scan per j)
+    // after one atomic per chunk reserves the chunk's slice
+    constexpr int kJ = kBChunk / 128;
+    const int64_t nwarps = (int64_t)gridDim.x * (kBThreads / 32);
+    for (int64_t c = (int64_t)blockIdx.x * (kBThreads / 32) + warp; c < nchunks; c += nwarps) {
         const int t = item_of_chunk[c];
-        if (items[t].done) continue;                 // uniform over the block
+        if (items[t].done) continue;                 // uniform over the warp
         const FT Tc = bthr(items[t].T, FT(0));
         const int64_t c0 = c << kBChunkShift;
         // 1/N completion (Sec. 2.2): the fluid the item's dangling nodes drained
@@ -196,58 +199,80 @@ __global__ void __launch_bounds__(kBThreads) k_bscan_level(
         // (not the padding after its last node); added and stored before the test
         const int64_t b0 = base[t], nl = nloc[t];
         const FT u = dangling ? static_cast<FT>(desc->d * items[t].dang_acc / (double)nl) : FT(0);
-        unsigned masks[kBItems];
-        double acc = 0.0, mx = 0.0;
+        unsigned long long msk = 0;                  // 4 bits per j
+        FT part = FT(0), mx = FT(0);
         unsigned long long esel = 0;
 #pragma unroll
-        for (int k = 0; k < kBItems; ++k) {
-            const int64_t idx = c0 + k * kBThreads + threadIdx.x;
-            if (u != FT(0) && idx - b0 < nl) F[idx] += u;
-            const FT v = fabs(F[idx]);
-            const bool sel = v >= Tc && v > FT(0);
-            masks[k] = __ballot_sync(0xffffffffu, sel);
-            acc += static_cast<double>(v);
-            mx = fmax(mx, static_cast<double>(v));
-            if (sel) esel += static_cast<unsigned long long>(outdeg[idx]);
-            if (lane == 0) s_cnt[k * (kBThreads / 32) + warp] = __popc(masks[k]);
-        }
-        __syncthreads();
-        if (warp == 0) {   // exclusive scan of the 64 counts in node order
-            const int a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
-            int incl = a + b;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int q = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += q;
+        for (int jj = 0; jj < kJ; ++jj) {
+            const int64_t i0 = c0 + 128 * jj + 4 * lane;
+            FT v[4];
+            if (sizeof(FT) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(F + i0);
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+                const double2 q0 = reinterpret_cast<const double2 *>(F + i0)[0];
+                const double2 q1 = reinterpret_cast<const double2 *>(F + i0)[1];
+                v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
             }
-            const int excl = incl - a - b;
-            s_cnt[2 * lane] = excl;
-            s_cnt[2 * lane + 1] = excl + a;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane == 0) {
-                s_total = total;
-                s_base = total ? atomicAdd(&st->nfront, total) : 0;
+            if (u != FT(0)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (i0 + k - b0 < nl) {
+                        v[k] += u;
+                        F[i0 + k] = v[k];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const FT a = fabs(v[k]);
+                part += a;
+                mx = a > mx ? a : mx;
+                if (a >= Tc && a > FT(0)) msk |= 1ull << (4 * jj + k);
             }
         }
-        __syncthreads();
-        const int fbase = s_base;
+        const int mine = __popcll(msk);
+        const int total = warp_sum(mine);
+        int fbase = 0;
+        if (total) {
+            if (lane == 0) fbase = atomicAdd(&st->nfront, total);
+            fbase = __shfl_sync(0xffffffffu, fbase, 0);
+            // node order: j-blocks in turn, lanes in turn inside a block
+            int run = fbase;
 #pragma unroll
-        for (int k = 0; k < kBItems; ++k) {
-            if ((masks[k] >> lane) & 1u)
-                front[fbase + s_cnt[k * (kBThreads / 32) + warp] + __popc(masks[k] & lt_mask)] =
-                    static_cast<int32_t>(c0 + k * kBThreads + threadIdx.x);
+            for (int jj = 0; jj < kJ; ++jj) {
+                const unsigned m4 = (unsigned)(msk >> (4 * jj)) & 15u;
+                const int cnt = __popc(m4);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int q = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += q;
+                }
+                int pos = run + incl - cnt;
+                const int64_t i0 = c0 + 128 * jj + 4 * lane;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((m4 >> k) & 1u) {
+                        front[pos++] = static_cast<int32_t>(i0 + k);
+                        esel += static_cast<unsigned long long>(outdeg[i0 + k]);
+                    }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
         }
-        block_reduce3(acc, mx, esel);
-        if (threadIdx.x == 0) {
+        // the chunk's sums (in the fluid's precision within the warp, FP64 across chunks)
+        double acc = static_cast<double>(warp_sum(part));
+        const double wmx = static_cast<double>(warp_max(mx));
+        esel = warp_sum(esel);
+        if (lane == 0) {
             BItem &it = items[t];
             atomicAdd(&it.acc_sum, acc);
-            atomic_max_nonneg(&it.acc_max, mx);
-            if (s_total) {
-                atomicAdd(&it.acc_nsel, static_cast<unsigned long long>(s_total));
+            atomic_max_nonneg(&it.acc_max, wmx);
+            if (total) {
+                atomicAdd(&it.acc_nsel, static_cast<unsigned long long>(total));
                 atomicAdd(&it.acc_esel, esel);
             }
         }
-        __syncthreads();   // s_cnt / s_total reused by the next chunk
     }
     __shared__ unsigned int s_last;
     __threadfence();
@@ -556,14 +581,41 @@ __global__ void __launch_bounds__(kBThreads) k_bpush(const BDesc *__restrict__ d
             auto pw = [&](int32_t c) { push1(c, w); };
             push_range<8>(pcol, b, e, 1, pw);
         }
-        unsigned wm = __ballot_sync(0xffffffffu, deg > thread_max && deg <= warp_max);
-        while (wm) {
-            const int src_lane = __ffs(wm) - 1;
-            wm &= wm - 1;
-            const int32_t mb = __shfl_sync(0xffffffffu, b, src_lane), me = __shfl_sync(0xffffffffu, e, src_lane);
-            const FT mw = __shfl_sync(0xffffffffu, w, src_lane);
-            auto pw = [&](int32_t c) { push1(c, mw); };
-            push_range<4>(pcol, (int64_t)mb + lane, me, 32, pw);
+        const bool wrow = deg > thread_max && deg <= warp_max;
+        if (__any_sync(0xffffffffu, wrow)) {
+            // the warp's medium rows as one edge-parallel range (as in the
+            // single-graph push): each lane finds the row of its edge by a
+            // binary search over the lanes' offsets, 4 column loads in flight
+            const int len = wrow ? deg : 0;
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int ex = incl - len, total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int q0 = 0; q0 < total; q0 += 4 * 32) {
+                int32_t c[4];
+                FT cw[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = q0 + 32 * k + lane;
+                    int owner = 0;   // the last lane whose offset is <= q
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int cand = owner + step;
+                        const int cex = __shfl_sync(0xffffffffu, ex, cand & 31);
+                        if (cand < 32 && cex <= q) owner = cand;
+                    }
+                    const int32_t ob = __shfl_sync(0xffffffffu, b, owner);
+                    const int oex = __shfl_sync(0xffffffffu, ex, owner);
+                    cw[k] = __shfl_sync(0xffffffffu, w, owner);
+                    c[k] = q < total ? __ldcs(pcol + (int64_t)ob + (q - oex)) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (q0 + 32 * k + lane < total) push1(c[k], cw[k]);
+            }
         }
         if (deg > warp_max) {
             const int slot = atomicAdd(&s_qn, 1);
