@@ -286,6 +286,11 @@ def test_batch_slice_sweeps_cut_the_diffusions(mixed_graphs):
         assert tot.edge_diffusions == sum(s.edge_diffusions for s in st)
         edges[sweeps] = tot.edge_diffusions
     assert edges[1] < 0.85 * edges[0], edges
+    # the wait for the frontier given up at once (spin_limit = 0): still exact to tol
+    H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
+    rc, st, tot = di.di_solve_batched(batch, B, D, tols, H, di.opts_default(slice_sweeps=2, spin_limit=0))
+    for (rp, col, b), h, s, tol in zip(items, H, st, tols):
+        stop_ok(rp, col, b, h.cpu().numpy(), tol, s.resid_l1)
     for bad in (-2, 5):
         H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for _, _, b in items]
         with pytest.raises(di.DiError) as e:

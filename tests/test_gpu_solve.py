@@ -496,6 +496,21 @@ def test_slice_sweeps_turn_the_fluid_window_off(web10k):
     assert st.slice_nodes > 0 and st.red_ops > 0
 
 
+def test_slice_sweeps_without_the_wait(web10k):
+    # spin_limit = 0: the push's wait for the frontier gives up at once, so
+    # the sweeps run while frontier tiles are still pushing (nodes drained
+    # twice, crossings missed): the result must not change beyond the tolerance
+    rp, col, b, x = web10k
+    for fp64, rel in ((False, 1e-6), (True, 1e-11)):
+        tol = (1e-11 * (1 - D) if fp64 else 1e-8) * b.sum()
+        for prop in (3, 7):
+            opts = dict(slice_sweeps=2) if prop == 3 else dict(slice_sweeps=1)   # propagation 7's barriers need time
+            h, st, _, _ = solve(rp, col, b, tol, fp64=fp64, propagation=prop, spin_limit=0 if prop == 3 else 1 << 20,
+                                **opts)
+            assert np.abs(h - x).sum() <= rel * np.abs(x).sum(), (fp64, prop)
+            check_stop(rp, col, b, h, st, tol)
+
+
 def test_slice_sweeps_rejections(web10k):
     rp, col, b, _ = web10k
     g = di.Graph.create(rp, col)
