@@ -61,6 +61,7 @@ constexpr int kPushWin = 1024;      // frontier push: nodes of a tile's fluid wi
 constexpr int kSliceQueueCap = 1536;   // frontier push: entries of a CTA's slice-sweep queue
 constexpr int kSliceDensity = 32;      // slice sweeps follow frontiers of at least 1/32 of the nodes
 constexpr int kSliceWaitPct = 50;      // a slice sweep starts once this share of the frontier's tiles is done
+constexpr int kLevelsPerIter = 2;      // propagations 3, 4: levels per WHILE iteration of the level graph
 
 // ------------------------------------------------------------------ solver state
 
@@ -151,6 +152,7 @@ struct SolverGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle h_while = 0, h_if = 0, h_p2 = 0;
+    cudaGraphConditionalHandle h_ifk[kLevelsPerIter - 1] = {};   // propagations 3, 4: the body's later levels
     bool built = false;
     int l2 = 0;           // built with the L2 window
     int prop = 0;         // built with this propagation option

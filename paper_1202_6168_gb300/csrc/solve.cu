@@ -1855,6 +1855,24 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
     cudaGraphNode_t inode;
     DI_CUDA_TRY(cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip));
     DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // propagations 3 and 4: kLevelsPerIter levels per WHILE iteration (fewer
+    // conditional re-evaluations); when the loop ends at an earlier level, the
+    // later levels' kernels return at once (their selection sees the stop)
+    cudaGraphNodeParams ipk[kLevelsPerIter - 1] = {};
+    const int extra_levels = (prop == 3 || prop == 4) ? kLevelsPerIter - 1 : 0;
+    for (int q = 0; q < extra_levels; ++q) {
+        DI_CUDA_TRY(cudaGraphConditionalHandleCreate(&sg.h_ifk[q], body, 0, 0));
+        if (fp64) launch_async<double>(g, cs, sg.h_while, sg.h_ifk[q], 1, win, prop);
+        else launch_async<float>(g, cs, sg.h_while, sg.h_ifk[q], 1, win, prop);
+        DI_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
+        ipk[q].type = cudaGraphNodeTypeConditional;
+        ipk[q].conditional.handle = sg.h_ifk[q];
+        ipk[q].conditional.type = cudaGraphCondTypeIf;
+        ipk[q].conditional.size = 1;
+        cudaGraphNode_t inode_q;
+        DI_CUDA_TRY(cudaGraphAddNode(&inode_q, capg, deps, nullptr, ndeps, &ipk[q]));
+        DI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &inode_q, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
     DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
 
     if (prop < 3) {
@@ -1871,6 +1889,12 @@ di_status build_level_graph(di_graph *g, int fp64, int l2, int prop) {
                                               cudaStreamCaptureModeThreadLocal));
     launch_residual(g, fp64, RES_LEVEL, cs);
     DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
+    for (int q = 0; q < extra_levels; ++q) {
+        DI_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ipk[q].conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+        launch_residual(g, fp64, RES_LEVEL, cs);
+        DI_CUDA_TRY(cudaStreamEndCapture(cs, &ended));
+    }
 
     DI_CUDA_TRY(cudaGetLastError());
     DI_CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
@@ -2227,6 +2251,9 @@ di_status solve_impl(di_graph *g, const double *B, double d, double tol, double 
             // finds the loop finished; the exact residuals
             if (o.propagation == 7)   // one persistent launch per segment between exact residuals, plus the last
                 launches += (long long)st.recomputes + 1 + 1 + (long long)rk * st.recomputes;
+            else if (o.propagation == 3 || o.propagation == 4)   // kLevelsPerIter levels (2 kernels each) per iteration
+                launches += 2LL * kLevelsPerIter * ((st.body_iters + kLevelsPerIter) / kLevelsPerIter) +
+                            (long long)rk * st.recomputes;
             else
                 launches += (o.propagation >= 5 ? 1LL : 2LL) * st.body_iters + 1 + (long long)rk * st.recomputes;
         }
