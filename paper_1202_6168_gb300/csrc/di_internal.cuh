@@ -53,7 +53,7 @@ constexpr int kResThreads = 256;
 constexpr int kResSeg = 8192;       // in-rows longer than this are split in segments (allocation-free path)
 constexpr int kResFine = 256;       // segment length of the exact residual's long in-rows
 constexpr int kMaxHot = 2048;       // privatised hot targets (shared-memory slots)
-constexpr int kHotMinIndeg = 512;   // a hot target has at least this in-degree
+constexpr int kHotMinIndeg = 2048;  // a hot target has at least this in-degree (about 2x the push CTAs)
 constexpr int kSrcBlockShift = 22;  // exact residual: sources in blocks of 2^22 nodes (32 MB of FP64 gathers)
 constexpr int kWinBins = 4;         // tiled level kernel: window radii 32 .. 256 (powers of two)
 constexpr int kMaxWinR = 32 << (kWinBins - 1);
