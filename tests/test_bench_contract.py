@@ -56,3 +56,17 @@ def test_kpid_simulation_line_covers_the_papers_grid():
     assert {r["delay_proba"] for r in rows} == {0.0, 0.5, 0.8}
     assert all(r["status"] == 0 and 0.0 <= r["idle_share"] < 1.0 for r in rows)
     assert all(r["speedup"] > 1 for r in rows if r["K"] > 1 and r["delay_proba"] == 0.0)
+
+
+def test_level_traffic_lookup_reads_the_committed_captures():
+    # the roofline's "traffic" comes from profiles/level_traffic.txt, keyed by
+    # workload, precision, propagation and slice sweeps per level; a
+    # configuration without a capture reports null
+    sys.path.insert(0, REPO)
+    import bench
+    with_sweeps = bench.level_traffic("web-1m", "f32", 3, 1)
+    without = bench.level_traffic("web-1m", "f32", 3, 0)
+    assert with_sweeps is not None and without is not None
+    assert 1e7 < with_sweeps < 2e8 and 1e7 < without < 2e8
+    assert bench.level_traffic("stress-16m", "f32", 3, 1) is None
+    assert bench.level_traffic("web-1m", "f64", 3, 1) is None
