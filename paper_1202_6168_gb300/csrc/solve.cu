@@ -559,7 +559,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
         s_pos = s_lo;
     }
     for (int sl = threadIdx.x; sl < n_hot; sl += kPushThreads) s_hot[sl] = FT(0);
-    for (unsigned q = threadIdx.x; q < span; q += kPushThreads) s_win[q] = FT(0);
+    for (unsigned q = threadIdx.x; !kSlice && q < span; q += kPushThreads) s_win[q] = FT(0);   // (no window with slice sweeps)
     const uint64_t keep = l2_keep_policy();
     const int thread_max = desc->thread_max, warp_max = desc->warp_max;
     // sweeps only after a dense frontier (at least 1/kSliceDensity of the nodes):
@@ -575,7 +575,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
             return;
         }
         const uint64_t o = (uint64_t)((int64_t)c - wlo);
-        if (o < span) {
+        if (!kSlice && o < span) {
             atomicAdd(&s_win[o], w);
         } else {
             red_add_keep(F + c, w, keep);
@@ -798,7 +798,7 @@ __device__ __forceinline__ void push_frontier(const SolveDesc *__restrict__ desc
         }
         // flush the window and clear it: consecutive threads, consecutive nodes
         // (coalesced reductions, eight FP32 or four FP64 words per sector)
-        for (unsigned q = threadIdx.x; q < span; q += kPushThreads) {
+        for (unsigned q = threadIdx.x; !kSlice && q < span; q += kPushThreads) {
             const FT v = s_win[q];
             s_win[q] = FT(0);
             const int64_t wnode = wlo + q;
