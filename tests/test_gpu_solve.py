@@ -284,10 +284,13 @@ def test_warm_start_fallback_on_garbage(web10k):
     assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
 
 
-def test_level_cap_reports_no_convergence(web10k):
+@pytest.mark.parametrize("cap", [1, 3, 4])
+def test_level_cap_reports_no_convergence(web10k, cap):
+    # the level graph runs two levels per WHILE iteration: caps that stop the
+    # loop at the first and at the second level of an iteration
     rp, col, b, x = web10k
-    h, st, f, rc = solve(rp, col, b, 1e-12, max_levels=3, allow=(di.DI_ENOCONV,))
-    assert rc == di.DI_ENOCONV and st.levels == 3
+    h, st, f, rc = solve(rp, col, b, 1e-12, max_levels=cap, allow=(di.DI_ENOCONV,))
+    assert rc == di.DI_ENOCONV and st.levels == cap
     f_cpu, r_cpu = od.residual(rp, col, b, D, h)
     assert st.resid_l1 == pytest.approx(r_cpu, rel=1e-12)
     assert_residual_close(f, f_cpu, rp, col, b, h)
