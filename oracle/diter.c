@@ -172,16 +172,24 @@ int oracle_diter(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
  *     is skipped by dividing T_k by alpha first (as in the one-PID oracle); a
  *     PID without fluid idles;
  *   - the stop test is the exact residual |B + P H - H|_1 <= tol after each
- *     round: it includes the fluid still waiting for transmission.
+ *     round: it includes the fluid still waiting for transmission;
+ *   - with dangling != 0 (the 1/N completion of Sec. 2.2) the column of a
+ *     node without out-edges is d/N in every row: its part in the PID's own
+ *     range is local (added to every node of Omega_k when the node diffuses)
+ *     and the rest is owed to the other ranges like any external edge
+ *     (counted in s_k, transmitted from H - H_old to every node outside
+ *     Omega_k).
  * Costs (Sec. 2.4): ops[k] counts PID k's elementary diffusions, one per local
- * child in its sweeps and one per external edge it transmits.
+ * child in its sweeps and one per external edge it transmits (a completed
+ * column has n_k local and N - n_k external children).
  * Returns 0 on convergence, 4 when max_rounds was reached, 1 on invalid
  * arguments, 2 when a scratch allocation failed.
  */
 int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *B, double d,
                 double tol, double alpha, int K, const int64_t *bounds, int64_t max_rounds,
                 double *H, double *F, double *H_old, int64_t *ops, int64_t *sends,
-                int64_t *rounds_out, double *resid_out, double *trace, int64_t trace_cap, double *T_out) {
+                int64_t *rounds_out, double *resid_out, double *trace, int64_t trace_cap, double *T_out,
+                int dangling) {
     if (n < 0 || K < 1 || !(alpha > 1.0) || !(tol >= 0.0) || max_rounds < 0) return 1;
     if (bounds[0] != 0 || bounds[K] != n) return 1;
     for (int k = 0; k < K; ++k)
@@ -211,7 +219,7 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
     int64_t round = 0;
     double resid = 0.0;
     for (;;) {
-        resid = oracle_residual(n, row_ptr, col, B, d, H, scratch, 0);
+        resid = oracle_residual(n, row_ptr, col, B, d, H, scratch, dangling);
         if (resid <= tol) { status = 0; break; }
         if (round >= max_rounds) { status = 4; break; }
         /* every PID sweeps its own nodes, diffusing to local children only */
@@ -227,7 +235,13 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
                 F[i] = 0.0;
                 H[i] += sent;
                 int64_t deg = row_ptr[i + 1] - row_ptr[i];
-                if (deg == 0) continue;
+                if (deg == 0) {
+                    if (dangling) {                     /* the completed column's local part */
+                        for (int64_t c = bounds[k]; c < bounds[k + 1]; ++c) F[c] += sent * (d / (double)n);
+                        ops[k] += bounds[k + 1] - bounds[k];
+                    }
+                    continue;
+                }
                 double p = d / (double)deg;
                 for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                     if (part[col[e]] != k) continue;    /* external: left in H - H_old */
@@ -246,6 +260,8 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
                 r[k] += fabs(F[i]);
                 double dh = H[i] - H_old[i];
                 int64_t deg = row_ptr[i + 1] - row_ptr[i];
+                if (dh != 0.0 && deg == 0 && dangling)  /* completed column: N - n_k external rows */
+                    s[k] += fabs(d / (double)n * dh) * (double)(n - (bounds[k + 1] - bounds[k]));
                 if (dh == 0.0 || deg == 0) continue;
                 double p = d / (double)deg;
                 for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
@@ -260,6 +276,15 @@ int oracle_kpid(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
                 double dh = H[i] - H_old[i];
                 int64_t deg = row_ptr[i + 1] - row_ptr[i];
                 H_old[i] = H[i];
+                if (dh != 0.0 && deg == 0 && dangling) {   /* completed column: every node outside */
+                    double q = d / (double)n * dh;
+                    for (int64_t j = 0; j < n; ++j) {
+                        if (part[j] == k) continue;
+                        F[j] += q;
+                        recv[part[j]] += fabs(q);
+                    }
+                    ops[k] += n - (bounds[k + 1] - bounds[k]);
+                }
                 if (dh == 0.0 || deg == 0) continue;
                 double p = d / (double)deg;
                 for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {

@@ -6,7 +6,9 @@
 * ``kpid`` - the sequential emulation of K PIDs in ``diter.c``: lock-step
   rounds of one threshold sweep per PID, local diffusion only (algorithm (*)),
   transmission of P (H - H_old) to external nodes when s_k > r_k / K
-  (Eq. send), threshold rescaling on reception (Sec. 2.6).
+  (Eq. send), threshold rescaling on reception (Sec. 2.6); with ``dangling``
+  the columns of nodes without out-edges are completed by d/N (Sec. 2.2), their
+  own range's part local and the rest owed like external edges.
 """
 from __future__ import annotations
 
@@ -63,13 +65,13 @@ def _lib():
         vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         lib.oracle_kpid.restype = ci
         lib.oracle_kpid.argtypes = [i64, vp, vp, vp, dbl, dbl, dbl, ci, vp, i64, vp, vp, vp, vp, vp,
-                                    ctypes.POINTER(i64), ctypes.POINTER(dbl), vp, i64, vp]
+                                    ctypes.POINTER(i64), ctypes.POINTER(dbl), vp, i64, vp, ci]
         lib._kpid_ready = True
     return lib
 
 
 def kpid(row_ptr, col, B, d: float = 0.85, tol: float = 1e-14, alpha: float = 1.5, bounds=None,
-         K: int = 1, max_rounds: int = 100_000, trace: bool = False) -> KpidResult:
+         K: int = 1, max_rounds: int = 100_000, trace: bool = False, dangling: bool = False) -> KpidResult:
     rp, cl = _d._csr(row_ptr, col)
     n = len(rp) - 1
     bnd = np.ascontiguousarray(uniform_bounds(n, K) if bounds is None else bounds, dtype=np.int64)
@@ -87,7 +89,8 @@ def kpid(row_ptr, col, B, d: float = 0.85, tol: float = 1e-14, alpha: float = 1.
     status = _lib().oracle_kpid(n, rp.ctypes.data, cl.ctypes.data, B.ctypes.data, d, tol, alpha, K,
                                 bnd.ctypes.data, max_rounds, H.ctypes.data, F.ctypes.data, Ho.ctypes.data,
                                 ops.ctypes.data, sends.ctypes.data, ctypes.byref(rounds), ctypes.byref(resid),
-                                tr.ctypes.data if trace else None, max_rounds if trace else 0, T.ctypes.data)
+                                tr.ctypes.data if trace else None, max_rounds if trace else 0, T.ctypes.data,
+                                1 if dangling else 0)
     if status == 1:
         raise ValueError("oracle rejected its arguments")
     if status == 2:

@@ -189,3 +189,79 @@ def test_hand_trace_empty_receiver_takes_the_received_amount():
     np.testing.assert_array_equal(r2.F, [0.0, 0.0, 0.0])
     np.testing.assert_allclose(r2.T, [1.0 / 1.5, 0.85 / 1.5 ** 3], rtol=1e-15)
     assert list(r2.ops) == [2, 0] and list(r2.sends) == [1, 0]
+
+
+# ---------------------------------------------------------------- 1/N completion (Sec. 2.2)
+
+from test_oracle_pins import exact_solve_completed
+
+
+def dense_completed(rp, col, n):
+    """P with every column without out-edges completed by d/N."""
+    P = dense(rp, col, n)
+    for j in range(n):
+        if rp[j + 1] == rp[j]:
+            P[:, j] = D / n
+    return P
+
+
+@pytest.mark.parametrize("rounds", [1, 4, 11])
+def test_one_pid_with_completion_is_the_plain_completed_sweep(rounds):
+    # one range holds every node: a completed column is all local, so the
+    # rounds are the plain sweeps of the completed D-iteration, bit for bit
+    rp, col = gg.generate(gg.GraphSpec(n=1500, mean_deg=6.0, seed=7, p_dangling=0.1))
+    assert np.sum(np.diff(rp) == 0) > 50
+    b = np.random.default_rng(2).random(1500)
+    plain = od.d_iteration(rp, col, b, D, tol=0.0, max_levels=rounds, dangling=True)
+    r = ok.kpid(rp, col, b, D, tol=0.0, K=1, max_rounds=rounds, dangling=True)
+    assert r.status == 4 and r.rounds == rounds
+    assert np.array_equal(r.H, plain.H) and np.array_equal(r.F, plain.F)
+    assert r.sends[0] == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("K,kind", [(2, "uniform"), (3, "cb"), (5, "uniform")])
+def test_any_partition_reaches_the_exact_completed_solution(seed, K, kind):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(K + 3, 14))
+    rp, col = random_graph(n, rng, p_dangling=0.3)
+    b = [Fraction(int(rng.integers(0, 7)), 100) for _ in range(n)]
+    b[0] += Fraction(1, 50)
+    x = np.array([float(v) for v in exact_solve_completed(rp, col, b)])
+    bounds = ok.uniform_bounds(n, K) if kind == "uniform" else ok.cb_bounds(rp, K)
+    bf = np.array([float(v) for v in b])
+    r = ok.kpid(rp, col, bf, D, tol=1e-14 * bf.sum(), bounds=bounds, dangling=True)
+    assert r.status == 0
+    assert np.abs(r.H - x).sum() <= 1e-13 * np.abs(x).sum()
+
+
+@pytest.mark.parametrize("rounds", [1, 2, 5, 9])
+def test_pending_fluid_invariant_with_completion(rounds):
+    # F plus the fluid still owed to other ranges - including the completed
+    # columns' rows outside the owner's range - is the residual of the
+    # completed P after every round
+    rng = np.random.default_rng(78)
+    rp, col = random_graph(80, rng, p_dangling=0.25)
+    b = rng.random(80)
+    bounds = ok.uniform_bounds(80, 3)
+    part = np.repeat(np.arange(3), np.diff(bounds))
+    P = dense_completed(rp, col, 80)
+    ext = P * (part[:, None] != part[None, :])
+    r = ok.kpid(rp, col, b, D, tol=0.0, bounds=bounds, max_rounds=rounds, dangling=True)
+    np.testing.assert_allclose(r.F + ext @ (r.H - r.H_old), b + P @ r.H - r.H, atol=1e-13)
+
+
+def test_hand_trace_dangling_node_transmits_to_every_other_range():
+    # nodes 0..3, ranges {0, 1} and {2, 3}; node 0 is dangling and holds the
+    # only fluid.  Round 1: PID 0 diffuses node 0 (H_0 = 1); its completed
+    # column adds d/4 to nodes 0 and 1 (local) and owes d/4 to each of 2, 3:
+    # s_0 = d/2 > r_0 / 2 = d/4, so it transmits d/4 to nodes 2 and 3
+    rp, col = csr_from_edges(4, [(1, 0), (2, 3), (3, 2)])
+    b = np.array([1.0, 0.0, 0.0, 0.0])
+    r = ok.kpid(rp, col, b, D, tol=0.0, bounds=np.array([0, 2, 4]), max_rounds=1, dangling=True)
+    q = D / 4
+    assert r.H[0] == 1.0
+    np.testing.assert_array_equal(r.F, [q, q, q, q])
+    np.testing.assert_array_equal(r.H_old, [1.0, 0.0, 0.0, 0.0])
+    assert r.sends.tolist() == [1, 0]
+    assert r.ops.tolist() == [2 + 2, 0]   # two local rows, two transmitted rows
