@@ -311,9 +311,13 @@ DI_API di_status di_residual_noalloc(const di_graph *g, const double *B, double 
  * round, all PIDs make one threshold level in the same launches; the stop is
  * decided on the exact FP64 residual, which includes the fluid still owed.
  * B, H (out), F (out, may be NULL) are device vectors of n doubles as in
- * di_solve.  Supports FP32 fluid, a cold start, the plain selection and zero
- * dangling columns; opts->alpha, max_levels, recompute_drop, timing and
- * stream apply (NULL opts = defaults).  timing = 1 runs the rounds
+ * di_solve.  Supports FP32 fluid, a cold start and the plain selection;
+ * opts->alpha, max_levels, recompute_drop, dangling, timing and stream apply
+ * (NULL opts = defaults).  dangling = 1 completes the columns of nodes
+ * without out-edges by 1/N (Sec. 2.2): such a column has n_k rows in its own
+ * range, diffused locally as a uniform add to the range's nodes at their next
+ * selection, and N - n_k rows outside, owed and transmitted like external
+ * edges (pid_ops counts both); the exact residual then uses the completed P.  timing = 1 runs the rounds
  * host-driven, one synchronisation per round, with CUDA events that fill
  * stats->select_seconds (k_pscan), level_seconds (selection, push and
  * transmission) and recompute_seconds (the IF body's kernels).  pid_ops / pid_sends (host, K entries, may be

@@ -48,6 +48,11 @@ struct PartState {
     unsigned long long ops[kMaxParts];   // elementary diffusions of the range's PID
     unsigned long long sends[kMaxParts]; // transmissions of the range's PID
     int send[kMaxParts];                 // this round: transmit
+    // 1/N completion (Sec. 2.2): the per-node amount every node of range k gets
+    // at its next selection (completed columns' local parts and received
+    // parts), and the sending ranges' sum of H - H_old over their dangling nodes
+    double pend[kMaxParts];
+    double dsend[kMaxParts];
     int any_send;
     int K;
     unsigned int scan_blocks, send_blocks, init_blocks;
@@ -154,6 +159,7 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         return;
     }
     __shared__ float s_T[kMaxParts];
+    __shared__ float s_u[kMaxParts];   // 1/N completion: the range's pending uniform add
     __shared__ double s_r[kMaxParts];
     __shared__ unsigned s_m[kMaxParts], s_sel[kMaxParts];   // max |F| as float bits (non-negative floats order like integers)
     __shared__ int s_warp[kPThreads / 32];
@@ -161,12 +167,14 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_T[k] = __double2float_ru(ps->T[k]);   // |F_i| >= T in FP32: T rounded up to a float
+        s_u[k] = static_cast<float>(ps->pend[k]);
         s_r[k] = 0.0;
         s_m[k] = 0u;
         s_sel[k] = 0u;
     }
     __syncthreads();
-    const float *__restrict__ F = static_cast<const float *>(desc->F);
+    // not __restrict__: with the 1/N completion pass 1 writes F and pass 2 reads it back
+    float *F = static_cast<float *>(desc->F);
     const int64_t span = cta_span(n), lo = (int64_t)blockIdx.x * span;
     const int64_t hi = lo + span < n ? lo + span : n;
     // pass 1: sums and counts, per thread for its current range; a range
@@ -193,7 +201,12 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
             flush();
             cur = k;
         }
-        const float a = fabsf(F[i]);
+        float v = F[i];
+        if (s_u[k] != 0.f) {   // the range's completed columns, added before the test
+            v += s_u[k];
+            F[i] = v;
+        }
+        const float a = fabsf(v);
         r += a;
         mx = fmaxf(mx, a);
         if (a >= s_T[k] && a > 0.f) {
@@ -265,6 +278,7 @@ __global__ void __launch_bounds__(kPThreads) k_pscan(const SolveDesc *__restrict
         ps->r[k] = 0.0;
         ps->m[k] = 0ull;
         ps->sel[k] = 0ull;
+        ps->pend[k] = 0.0;                              // added by every CTA of this selection
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -336,6 +350,8 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
     __shared__ float s_s[kMaxParts];
     __shared__ unsigned s_ops[kMaxParts];
     __shared__ int64_t s_b[kMaxParts + 1];
+    __shared__ float s_dang[kMaxParts];     // 1/N completion: fluid drained from the range's dangling nodes
+    __shared__ unsigned s_dcnt[kMaxParts];  // ... and their number
     // targets of very high in-degree (hot slots, encoded -1 - slot in pcol)
     // are accumulated per CTA in shared memory and flushed once, as in the
     // main push: hot-node ranges, then the sums
@@ -346,8 +362,12 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_s[k] = 0.f;
         s_ops[k] = 0u;
+        s_dang[k] = 0.f;
+        s_dcnt[k] = 0u;
     }
     for (int k = threadIdx.x; k <= K; k += blockDim.x) s_b[k] = bounds[k];
+    const bool dangling = desc->dangling != 0;
+    const double dN = desc->d / (double)desc->n_nodes;
     for (int sl = threadIdx.x; sl < n_hot; sl += blockDim.x) {
         s_hot[sl] = 0.f;
         s_hot_part[sl] = part_of[hot_node[sl]];
@@ -381,7 +401,7 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
         const int64_t idx = base + lane;
         int32_t b = 0, e = 0;
         int k = 0;
-        float w = 0.f;
+        float w = 0.f, w_dang = 0.f;
         if (idx < count) {
             const int32_t i = front[idx];
             k = part_of[i];
@@ -390,10 +410,15 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
             const float f = atomicExch(F + i, 0.f);
             H[i] += static_cast<double>(f);
             w = f * scale[i];
+            w_dang = f;
             my_nodes += 1;
         }
         const int deg = e - b;
         unsigned loc = 0, ext = 0;
+        // a drained dangling node with the 1/N completion: its column's part in
+        // the range is a pending uniform add, the rest (N - n_k rows of d/N) is owed
+        float dl = idx < count && deg == 0 && dangling ? w_dang : 0.f;
+        unsigned dc = dl != 0.f ? 1u : 0u;
         if (deg <= kPThreadRow) {
             // the row by its thread, 8 column loads in flight
             const int64_t lo = s_b[k], hi = s_b[k + 1];
@@ -410,16 +435,23 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
             // the thread rows' counts (all lanes; zero for the others), reduced
             // over the warp first when its lanes share a range
             float owed = fabsf(w) * static_cast<float>(ext);
+            if (dl != 0.f) owed += fabsf(dl) * static_cast<float>(dN * (double)(desc->n_nodes - (s_b[k + 1] - s_b[k])));
             int kk = k;
             const int k0 = __shfl_sync(0xffffffffu, k, 0);
             if (__all_sync(0xffffffffu, k == k0)) {
                 loc = warp_sum(loc);
                 owed = warp_sum(owed);
+                dl = warp_sum(dl);
+                dc = warp_sum(dc);
                 if (lane != 0) kk = -1;
             }
             if (kk >= 0) {
                 if (loc) atomicAdd(&s_ops[kk], loc);
                 if (owed != 0.f) atomicAdd(&s_s[kk], owed);
+                if (dc) {
+                    atomicAdd(&s_dang[kk], dl);
+                    atomicAdd(&s_dcnt[kk], dc);
+                }
                 my_edges += loc;
             }
         }
@@ -462,8 +494,13 @@ __global__ void __launch_bounds__(kPThreads) k_ppush(const SolveDesc *__restrict
         if (v != 0.f) red_add(F + hot_node[sl], v);
     }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        unsigned long long ops = s_ops[k];
+        if (s_dcnt[k]) {   // completed columns: n_k local rows, a pending uniform add
+            atomicAdd(&ps->pend[k], dN * static_cast<double>(s_dang[k]));
+            ops += (unsigned long long)s_dcnt[k] * (unsigned long long)(s_b[k + 1] - s_b[k]);
+        }
         if (s_s[k] != 0.f) atomicAdd(&ps->s[k], static_cast<double>(s_s[k]));
-        if (s_ops[k]) atomicAdd(&ps->ops[k], (unsigned long long)s_ops[k]);
+        if (ops) atomicAdd(&ps->ops[k], ops);
     }
 }
 
@@ -482,12 +519,17 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
     __shared__ float s_recv[kMaxParts];       // received per range (FP32 in the CTA, FP64 across CTAs)
     __shared__ unsigned s_ops[kMaxParts];
     __shared__ int64_t s_b[kMaxParts + 1];
+    __shared__ double s_dh[kMaxParts];        // 1/N completion: H - H_old over the range's dangling nodes
+    __shared__ unsigned s_dcnt[kMaxParts];
     const int K = ps->K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         s_send[k] = ps->send[k];
         s_recv[k] = 0.f;
         s_ops[k] = 0u;
+        s_dh[k] = 0.0;
+        s_dcnt[k] = 0u;
     }
+    const bool dangling = desc->dangling != 0;
     for (int k = threadIdx.x; k <= K; k += blockDim.x) s_b[k] = bounds[k];
     __syncthreads();
     float *__restrict__ F = static_cast<float *>(desc->F);
@@ -522,6 +564,7 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
         int32_t b = 0, e = 0;
         int k = 0;
         float w = 0.f;
+        double ddh = 0.0;   // a dangling node's H - H_old (1/N completion)
         if (i < n) {
             k = part_of[i];
             if (s_send[k]) {
@@ -531,7 +574,24 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
                     w = static_cast<float>(scale64[i] * dh);
                     b = rp[i];
                     e = rp[i + 1];
+                    if (b == e && dangling) ddh = dh;
                 }
+            }
+        }
+        if (dangling && __any_sync(0xffffffffu, ddh != 0.0)) {
+            // the completed columns' owed rows: summed per range over the warp
+            // when its lanes share one (their rows go to every node outside it)
+            unsigned dc = ddh != 0.0 ? 1u : 0u;
+            int kk = k;
+            const int k0 = __shfl_sync(0xffffffffu, k, 0);
+            if (__all_sync(0xffffffffu, k == k0)) {
+                ddh = warp_sum(ddh);
+                dc = warp_sum(dc);
+                if (lane != 0) kk = -1;
+            }
+            if (kk >= 0 && dc) {
+                atomicAdd(&s_dh[kk], ddh);
+                atomicAdd(&s_dcnt[kk], dc);
             }
         }
         const int deg = e - b;
@@ -579,9 +639,32 @@ __global__ void __launch_bounds__(kPThreads) k_psend(const SolveDesc *__restrict
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         if (s_recv[k] != 0.f) atomicAdd(&ps->recv[k], static_cast<double>(s_recv[k]));
-        if (s_ops[k]) atomicAdd(&ps->ops[k], (unsigned long long)s_ops[k]);
+        unsigned long long ops = s_ops[k];
+        if (s_dcnt[k]) {   // N - n_k transmitted rows per completed column
+            atomicAdd(&ps->dsend[k], s_dh[k]);
+            ops += (unsigned long long)s_dcnt[k] * (unsigned long long)(n - (s_b[k + 1] - s_b[k]));
+        }
+        if (ops) atomicAdd(&ps->ops[k], ops);
     }
     if (!last_block(&ps->send_blocks)) return;
+    if (dangling) {
+        // the completed columns' transmissions land on every node outside the
+        // sender's range: a pending uniform add per receiving range
+        if (threadIdx.x == 0) {
+            const double dN = desc->d / (double)n;
+            for (int k = 0; k < K; ++k) {
+                const double q = dN * ps->dsend[k];
+                if (q == 0.0) continue;
+                for (int k2 = 0; k2 < K; ++k2) {
+                    if (k2 == k) continue;
+                    ps->pend[k2] += q;
+                    ps->recv[k2] += fabs(q) * (double)(s_b[k2 + 1] - s_b[k2]);
+                }
+                ps->dsend[k] = 0.0;
+            }
+        }
+        __syncthreads();
+    }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         if (ps->send[k]) {
             ps->sends[k] += 1;
@@ -612,7 +695,11 @@ __global__ void __launch_bounds__(kPThreads) k_phold(const SolveDesc *__restrict
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) H_old[i] = H[i];
     if (blockIdx.x == 0)
-        for (int k = threadIdx.x; k < ps->K; k += blockDim.x) ps->s[k] = 0.0;
+        for (int k = threadIdx.x; k < ps->K; k += blockDim.x) {
+            ps->s[k] = 0.0;
+            ps->pend[k] = 0.0;   // the exact residual holds the pending completed parts as well
+            ps->dsend[k] = 0.0;
+        }
 }
 
 // Range boundaries (host): uniform w_k = floor(k N / K), or the first node at
@@ -683,10 +770,10 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
     if (!(o.alpha > 1.0) || !std::isfinite(o.alpha)) { set_error("di_solve_partitioned: alpha = %g must be > 1", o.alpha); return DI_EINVAL; }
     if (K < 1 || K > kMaxParts) { set_error("di_solve_partitioned: K = %d outside [1, %d]", K, kMaxParts); return DI_EINVAL; }
     if (kind < 0 || kind > 1) { set_error("di_solve_partitioned: kind = %d outside [0, 1]", kind); return DI_EINVAL; }
-    if (o.fluid_fp64 || o.warm_start || o.dangling || o.selection || o.max_levels < 0 ||
+    if (o.fluid_fp64 || o.warm_start || o.dangling < 0 || o.dangling > 1 || o.selection || o.max_levels < 0 ||
         !(o.recompute_drop == 0.0 || (o.recompute_drop > 1.0 && std::isfinite(o.recompute_drop)))) {
         set_error("di_solve_partitioned: supports FP32 fluid from a cold start with the plain selection and "
-                  "zero dangling columns; recompute_drop must be 0 or > 1");
+                  "dangling 0 or 1; recompute_drop must be 0 or > 1");
         return DI_EINVAL;
     }
     if (g->n > (int64_t)INT32_MAX) { set_error("di_solve_partitioned: too many nodes"); return DI_EINVAL; }
@@ -748,6 +835,7 @@ extern "C" DI_API di_status di_solve_partitioned(di_graph *g, const double *B, d
     dh.recompute_drop = o.recompute_drop;
     dh.max_body_iters = (int)std::min<long long>(4LL * o.max_levels + 1000, INT32_MAX);
     dh.n_nodes = n;
+    dh.dangling = o.dangling;
     DI_CUDA_TRY(cudaEventRecord(ws.ev0, s));
     DI_CUDA_TRY(cudaMemcpyAsync(ws.desc, ws.desc_h, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
     DI_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(SolveState), s));

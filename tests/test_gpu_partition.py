@@ -113,7 +113,7 @@ def test_rejects_unsupported_arguments(web10k):
     B = dev(b)
     H = torch.zeros(len(b), dtype=torch.float64, device="cuda")
     for K, kind, opt in ((0, 0, {}), (65, 0, {}), (2, 2, {}), (2, 0, dict(fluid_fp64=1)),
-                         (2, 0, dict(warm_start=1)), (2, 0, dict(dangling=1)), (2, 0, dict(selection=1))):
+                         (2, 0, dict(warm_start=1)), (2, 0, dict(dangling=2)), (2, 0, dict(selection=1))):
         with pytest.raises(di.DiError) as e:
             di.di_solve_partitioned(g, B, D, 1e-8, H, K, kind, None, di.opts_default(**opt))
         assert e.value.status == di.DI_EINVAL
@@ -152,3 +152,81 @@ def test_host_driven_rounds_match_and_time_the_kernels(web10k, K):
     assert 0 < st.select_seconds < st.level_seconds
     assert st.recompute_seconds > 0 and st.level_launches >= st.body_iterations
     assert st.recompute_launches == st.recomputes >= 1
+
+
+# ---------------------------------------------------------------- 1/N completion of dangling columns (Sec. 2.2)
+
+@pytest.fixture(scope="module")
+def web10k_completed():
+    rp, col = gg.generate(gg.SMALL_10K)
+    b = gg.uniform_b(gg.SMALL_10K.n, D)
+    r = od.d_iteration(rp, col, b, D, tol=1e-14 * b.sum(), dangling=True)
+    assert r.status == 0
+    return rp, col, b, r.H
+
+
+def check_stop_completed(rp, col, b, h, st, tol):
+    """check_stop for the completed P: the one sum over the dangling nodes that
+    every row shares adds 2 d n_dangling eps sum_dangling |H_j| to the
+    rounding allowance of |F|_1."""
+    _, r_cpu = od.residual(rp, col, b, D, h, dangling=True)
+    eps = np.finfo(np.float64).eps
+    dang = np.diff(rp) == 0
+    floor = 64 * eps * (np.abs(b).sum() + 2 * np.abs(h).sum())
+    floor += 2 * D * dang.sum() * eps * np.abs(h[dang]).sum()
+    assert r_cpu <= tol * (1 + 1e-9) + floor
+    assert abs(st.resid_l1 - r_cpu) <= 1e-9 * max(r_cpu, tol) + floor
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 64])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_dangling_completion_every_partition(web10k_completed, K, kind):
+    # a completed column has n_k rows in its PID's range (local) and N - n_k
+    # outside (transmitted from H - H_old): every K reaches the completed X
+    rp, col, b, x = web10k_completed
+    assert np.sum(np.diff(rp) == 0) > 500
+    tol = 1e-8 * b.sum()
+    h, st, ops, sends, f = run(rp, col, b, tol, K, kind, dangling=1)
+    assert st.status == di.DI_OK
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop_completed(rp, col, b, h, st, tol)
+    # the completed columns are stochastic: 1'H is within the error bound of 1'X = 1
+    assert abs(h.sum() - 1.0) <= st.resid_l1 / (1 - D) * 1.001 + 1e-12
+    # the completed rows are elementary diffusions too (n_k local + N - n_k sent)
+    assert ops.sum() > st.edge_diffusions
+    if K > 1:
+        assert sends.min() >= 1
+
+
+def test_dangling_completion_matches_kpid_oracle():
+    # all of one half's fluid leaves through dangling nodes: only the completed
+    # columns' transmissions reach the other half
+    n = 3000
+    rng = np.random.default_rng(11)
+    edges = [(j, int(rng.integers(1500, 3000))) for j in range(1500) for _ in range(2)]
+    edges += [(j, int(rng.integers(1500, 3000))) for j in range(1500, 2500) for _ in range(3)]
+    rp, col = csr_from_edges(n, edges)               # nodes 2500..2999 dangling
+    b = gg.personalised_b(n, 5)
+    tol = 1e-9 * b.sum()
+    ref = ok.kpid(rp, col, b, D, tol=1e-13 * b.sum(), K=2, dangling=True)
+    assert ref.status == 0
+    for kind in (0, 1):
+        h, st, ops, sends, _ = run(rp, col, b, tol, 2, kind, dangling=1)
+        assert st.status == di.DI_OK
+        assert np.abs(h - ref.H).sum() <= 1e-6 * np.abs(ref.H).sum()
+        check_stop_completed(rp, col, b, h, st, tol)
+        assert h[:1500].min() > 0                    # reached only by the 1/N rows
+        assert sends.min() >= 1
+
+
+def test_dangling_completion_all_dangling_and_tiny():
+    # no edges at all: X = B + d (1'X / N) 1, so 1'X = 1'B / (1 - d)
+    n = 37
+    rp = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(0, dtype=np.int32)
+    b = np.linspace(0.01, 0.05, n)
+    x = b + D / n * b.sum() / (1 - D)
+    for K in (1, 3, 8):
+        h, st, _, _, _ = run(rp, col, b, 1e-13, K, dangling=1)
+        assert st.status == di.DI_OK
+        assert np.abs(h - x).max() <= 1e-6 * np.abs(x).max()
