@@ -1000,7 +1000,7 @@ def run_kpid(args, world, rank, local):
     B = torch.from_numpy(b).cuda()
     H = torch.zeros(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    opts = di.opts_default(stream=stream.cuda_stream)
+    opts = di.opts_default(stream=stream.cuda_stream, dangling=1 if args.dangling else 0)
     rows = []
     for K, kind in ((1, 0), (2, 0), (2, 1), (4, 0), (4, 1), (8, 0), (8, 1)):
         times = []
@@ -1026,6 +1026,7 @@ def run_kpid(args, world, rank, local):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "n": n, "nnz": nnz, "tol": "1e-8 |B|_1", "best": {"K": best["K"],
                        "partition": best["partition"]}, "level_loop": "CUDA graph (WHILE/IF nodes), one round per level",
+                       "dangling": ["zero columns", "uniform 1/N completion"][opts.dangling],
                        "timed": "wall clock around each di_solve_partitioned (synchronous)",
                        "l2": "flushed (256 MiB write) before each timed solve"},
             "one_pid_cost": one, "cost_split": best["max_pid_cost"] / one, "rows": rows,
