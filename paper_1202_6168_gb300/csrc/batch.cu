@@ -709,13 +709,16 @@ __global__ void __launch_bounds__(kBThreads) k_bres_flat(const BDesc *__restrict
     const double *__restrict__ g = desc->g;
     double *__restrict__ tmp = desc->tmp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t wtid = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);   // the warp's first thread
     for (int t = 0; t < nitems; ++t) {
         if (!items[t].rec) continue;
         const int64_t eb = e_off[t], ee = e_off[t + 1];
         if (eb >= ee) continue;
         const int64_t cb = eb / kBFlatEdges, ce = (ee + kBFlatEdges - 1) / kBFlatEdges;
-        for (int64_t c = cb + tid; c < ce; c += stride) {
+        // warp-uniform: lanes past ce hold no edge and still join warp_runs_add
+        for (int64_t c0 = cb + wtid; c0 < ce; c0 += stride) {
+            const int64_t c = c0 + lane;
             const int64_t e0 = c * kBFlatEdges;
             int32_t col[kBFlatEdges], row[kBFlatEdges];
             if (e0 + kBFlatEdges <= nnz) {
@@ -741,19 +744,7 @@ __global__ void __launch_bounds__(kBThreads) k_bres_flat(const BDesc *__restrict
                 if (!on) row[k] = -1;
                 val[k] = on ? g[col[k]] : 0.0;
             }
-            int32_t cur = row[0];
-            double acc = val[0];
-#pragma unroll
-            for (int k = 1; k < kBFlatEdges; ++k) {
-                if (row[k] != cur) {
-                    if (cur >= 0) red_add(tmp + cur, acc);
-                    cur = row[k];
-                    acc = val[k];
-                } else {
-                    acc += val[k];
-                }
-            }
-            if (cur >= 0) red_add(tmp + cur, acc);
+            warp_runs_add<kBFlatEdges>(row, val, tmp, lane);
         }
     }
 }

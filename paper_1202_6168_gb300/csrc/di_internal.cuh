@@ -266,6 +266,63 @@ __device__ __forceinline__ void red_add(double *addr, double v) {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(v) : "memory");
 }
 
+// Adds each thread's kE (destination, value) pairs into acc, for pairs sorted
+// by destination along the warp (lane l holds the l-th group of kE consecutive
+// edges; destination -1 = no edge, value 0, skipped wherever it is).  Runs of equal
+// destination are summed in registers; a thread's first run, when it
+// continues the previous lane's last run, goes to that lane, and the last runs
+// are summed over lanes of equal destination: a destination whose in-edges
+// span many lanes (a hub) takes one reduction per warp, not one per thread
+// on the same L2 address.  All 32 lanes must call it together.
+template <int kE>
+__device__ __forceinline__ void warp_runs_add(const int32_t (&row)[kE], const double (&val)[kE], double *acc,
+                                              int lane) {
+    constexpr unsigned kFull = 0xffffffffu;
+    int32_t kA = -1, kB = row[0];
+    double sA = 0.0, sB = val[0];
+    bool first_open = true;
+#pragma unroll
+    for (int k = 1; k < kE; ++k) {
+        if (row[k] != kB) {
+            if (first_open) {   // the first run closes (a key of -1 is then dropped below)
+                kA = kB;
+                sA = sB;
+                first_open = false;
+            } else if (kB >= 0) {
+                red_add(acc + kB, sB);
+            }
+            kB = row[k];
+            sB = val[k];
+        } else {
+            sB += val[k];
+        }
+    }
+    const int32_t kA_next = __shfl_down_sync(kFull, kA, 1);
+    const double sA_next = __shfl_down_sync(kFull, sA, 1);
+    const int32_t kB_prev = __shfl_up_sync(kFull, kB, 1);
+    if (lane < 31 && kA_next >= 0 && kA_next == kB) sB += sA_next;
+    if (kA >= 0 && !(lane > 0 && kA == kB_prev)) red_add(acc + kA, sA);
+    // segmented sum of the last runs; segments are numbered from their heads,
+    // so only neighbouring lanes merge.  The steps stop once no segment is
+    // longer than the distance (FP64 adds are scarce on this part): none when
+    // every lane heads its own segment
+    const bool head = lane == 0 || kB != kB_prev;
+    const unsigned heads = __ballot_sync(kFull, head);
+    double v = sB;
+    if (heads != kFull) {
+        const int seg = __popc(heads & (kFull >> (31 - lane)));
+#pragma unroll 1
+        for (int o = 1; o < 32; o <<= 1) {
+            const double w = __shfl_down_sync(kFull, v, o);
+            const int s2 = __shfl_down_sync(kFull, seg, o);
+            const bool same = lane + o < 32 && s2 == seg;
+            if (same) v += w;
+            if (!__any_sync(kFull, same)) break;
+        }
+    }
+    if (head && kB >= 0) red_add(acc + kB, v);
+}
+
 // L2 policy "evict last" for the fluid vector: the scatter target stays in
 // L2 while the column indices, offsets and histories stream past it.
 __device__ __forceinline__ uint64_t l2_keep_policy() {

@@ -154,8 +154,12 @@ __global__ void __launch_bounds__(kResThreads) k_resb_init(const SolveDesc *__re
 // time the grid works inside one block of 2^22 sources, whose 32 MB of g stay
 // in L2 while the edge arrays stream.  8 consecutive edges per thread (two
 // int4 loads of each index array, 8 independent gathers; few registers, so
-// 6 CTAs of 256 fit per SM to hide the latency); runs of equal destination
-// are summed and added with one red.global.add.f64.
+// 6 CTAs of 256 fit per SM to hide the latency).  Runs of equal destination
+// are summed in registers, and the runs that cross lane boundaries are summed
+// over the warp before their red.global.add.f64 (warp_runs_add): a
+// destination of very high in-degree (a hub, up to millions of in-edges)
+// would otherwise take one reduction per thread, all on one L2 address at the
+// same time.
 constexpr int kResbEdges = 8;
 
 __global__ void __launch_bounds__(kResThreads, 6) k_resb_flat(const SolveState *__restrict__ st, int mode,
@@ -165,10 +169,13 @@ __global__ void __launch_bounds__(kResThreads, 6) k_resb_flat(const SolveState *
                                                               int64_t nnz) {
     if (mode == RES_LEVEL && !st->do_recompute) return;
     constexpr int kE = kResbEdges;
+    const int lane = threadIdx.x & 31;
     const int64_t nch = (nnz + kE - 1) / kE;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += stride) {
-        const int64_t e0 = c * kE;
+    // warp-uniform loop: the chunks of a warp are consecutive, lanes past the
+    // end hold no edge (destination -1) and still take part in the shuffles
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nch; c0 += stride) {
+        const int64_t e0 = (c0 + lane) * kE;
         int32_t col[kE], row[kE];
         if (e0 + kE <= nnz) {
 #pragma unroll
@@ -189,19 +196,7 @@ __global__ void __launch_bounds__(kResThreads, 6) k_resb_flat(const SolveState *
         double val[kE];
 #pragma unroll
         for (int k = 0; k < kE; ++k) val[k] = row[k] >= 0 ? g[col[k]] : 0.0;
-        int32_t cur = row[0];
-        double sum = val[0];
-#pragma unroll
-        for (int k = 1; k < kE; ++k) {
-            if (row[k] != cur) {
-                if (cur >= 0) red_add(acc + cur, sum);
-                cur = row[k];
-                sum = val[k];
-            } else {
-                sum += val[k];
-            }
-        }
-        if (cur >= 0) red_add(acc + cur, sum);
+        warp_runs_add<kE>(row, val, acc, lane);
     }
 }
 
