@@ -117,6 +117,36 @@ def test_batch_agrees_with_single_solves():
         g.close()
 
 
+def test_batch_hub_destinations_match_oracle():
+    # items whose in-edges funnel into a few hubs: the batched residual's runs
+    # of equal destination span many warps, summed over the warp before each
+    # reduction, and an item's range starts mid-chunk
+    csrs = []
+    for n, seed in ((50_001, 1), (120_003, 2)):
+        rng = np.random.default_rng(seed)
+        col = np.stack([np.zeros(n, dtype=np.int64), 1 + np.arange(n) % 3, rng.integers(0, n, size=n)], axis=1)
+        csrs.append((np.arange(0, 3 * n + 1, 3, dtype=np.int64), col.reshape(-1).astype(np.int32)))
+    graphs = [di.Graph.create(rp, col) for rp, col in csrs]
+    batch = di.Batch(graphs, [2, 2])
+    bs, xs, gi = [], [], []
+    for k, (rp, col) in enumerate(csrs):
+        n = len(rp) - 1
+        for src in gg.batch_sources(n, 2, seed=n):
+            b = gg.personalised_b(n, int(src))
+            bs.append(b)
+            xs.append(oracle_x(rp, col, b))
+            gi.append(k)
+    H = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in bs]
+    _, st, _ = di.di_solve_batched(batch, [dev(b) for b in bs], D, [1e-8 * b.sum() for b in bs], H)
+    for t, (h, x, b, k) in enumerate(zip(H, xs, bs, gi)):
+        h = h.cpu().numpy()
+        assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+        stop_ok(*csrs[k], b, h, 1e-8 * b.sum(), st[t].resid_l1)
+    batch.close()
+    for g in graphs:
+        g.close()
+
+
 def test_batch_level_cap_and_zero_rhs():
     rp, col = gg.generate(gg.GraphSpec(n=9000, mean_deg=8.0, seed=9))
     g = di.Graph.create(rp, col)

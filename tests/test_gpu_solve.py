@@ -596,6 +596,43 @@ def test_blocked_residual_ragged_edge_counts(nnz):
     g.close()
 
 
+def hub_csr(n, seed):
+    """Every node j links to node 0, to hub 1 + j % 3 and to one random node
+    (self-loops and duplicates kept): destination runs of n and n / 3 edges."""
+    rng = np.random.default_rng(seed)
+    col = np.stack([np.zeros(n, dtype=np.int64), 1 + np.arange(n) % 3, rng.integers(0, n, size=n)], axis=1)
+    return np.arange(0, 3 * n + 1, 3, dtype=np.int64), col.reshape(-1).astype(np.int32)
+
+
+@pytest.mark.parametrize("n", [200_000, (1 << 22) + 5000])
+def test_blocked_residual_hub_destinations(n):
+    # the runs of equal destination span thousands of lanes and warps (and,
+    # above 2^22 nodes, both source blocks): the residual sums them over the
+    # warp before each reduction; every value must still be added once
+    rp, col = hub_csr(n, n)
+    rng = np.random.default_rng(n + 1)
+    h, b = rng.random(n), rng.random(n)
+    g = di.Graph.create(rp, col)
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    f_cpu, r_cpu = od.residual(rp, col, b, D, h)
+    for _ in range(2):
+        r = di.di_residual(g, dev(b), D, dev(h), F)
+        assert_residual_close(F.cpu().numpy(), f_cpu, rp, col, b, h)
+        assert r == pytest.approx(r_cpu, rel=1e-13)
+    g.close()
+
+
+def test_hub_destinations_solve_matches_oracle():
+    rp, col = hub_csr(60_000, 3)
+    b = gg.uniform_b(60_000, D)
+    tol = 1e-8 * b.sum()
+    h, st, f, _ = solve(rp, col, b, tol)
+    x = oracle_x(rp, col, b)
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    f_cpu = check_stop(rp, col, b, h, st, tol)
+    assert_residual_close(f, f_cpu, rp, col, b, h)
+
+
 @pytest.mark.parametrize("edges_per_node", [5.6, 11.2])
 def test_blocked_residual_many_grid_strides(edges_per_node):
     # uniformly random in-edges (no locality) and enough of them that every
