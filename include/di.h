@@ -111,7 +111,8 @@ typedef struct {
     int exact_residual;    /* form of the exact FP64 residual B + P H - H: 1 gather over the
                               in-rows binned by length (no atomics, fixed summation order);
                               2 in-edges in source-blocked order (blocks of 2^22 sources,
-                              so the gathered H stays in L2), runs added with FP64 reds;
+                              so the gathered H stays in L2), runs of equal destination
+                              summed over the warp and added with FP64 reds;
                               0 (default) = 2 */
     int selection;         /* frontier rule: 0 (default) |F_i| >= T; 1 the weighted score
                               |F_i| / ((#in_i + 1)(#out_i + 1)) >= T that Sec. 2.4 names as
@@ -260,8 +261,10 @@ DI_API di_status di_solve_host(di_graph *g, const double *B, double d, double to
  * imply): F = B + P H - H in FP64 for device vectors B, H (n doubles) into
  * the device vector F (n doubles); *r_l1 (host, may be NULL) receives
  * |F|_1.  Gathers over the in-edges in source-blocked order (form 2 of
- * di_opts.exact_residual) and adds runs of equal destination with FP64
- * reds.  Synchronous when r_l1 != NULL.
+ * di_opts.exact_residual); runs of equal destination are summed in
+ * registers and over the warp, then added with FP64 reds, so the summation
+ * order (not the set of terms) varies between runs.  Synchronous when
+ * r_l1 != NULL.
  */
 DI_API di_status di_residual(di_graph *g, const double *B, double d, const double *H,
                              double *F, double *r_l1, void *stream);
