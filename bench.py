@@ -271,9 +271,12 @@ def run_reference(args, world, rank):
 
 def run_reference_kpid(args, desc):
     """Reference arm of the K-PID workload: the oracle's emulation of 8 PIDs
-    (cost-balanced ranges) on a bounded sample, a web-like graph of N = 1e5."""
+    (cost-balanced ranges) on a bounded sample, a web-like graph of N = 1e5
+    (N = 2e4 with the 1/N completion, whose completed columns cost the
+    sequential emulation O(N) each)."""
     from oracle import kpid as ok
-    sp = gg.GraphSpec(n=100_000, mean_deg=10.0, window=64, seed=0)
+    n_sample = 20_000 if args.dangling else 100_000
+    sp = gg.GraphSpec(n=n_sample, mean_deg=10.0, window=64, seed=0)
     rp, col = gg.generate(sp)
     b = gg.uniform_b(sp.n, D)
     tol = 1e-8 * b.sum()
@@ -281,7 +284,7 @@ def run_reference_kpid(args, desc):
     costs, secs = [], 0.0
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = ok.kpid(rp, col, b, D, tol=tol, bounds=ok.cb_bounds(rp, 8))
+        r = ok.kpid(rp, col, b, D, tol=tol, bounds=ok.cb_bounds(rp, 8), dangling=bool(args.dangling))
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             secs += dt
@@ -291,10 +294,11 @@ def run_reference_kpid(args, desc):
             "unit": "iterations (ops/L)", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "sample": "web-like N=1e5, m=10, K=8 cost-balanced ranges",
-                       "oracle": "sequential emulation of K PIDs, FP64, 1 core"},
+            "config": {"workload": desc, "sample": f"web-like N={n_sample:.0e}, m=10, K=8 cost-balanced ranges",
+                       "oracle": "sequential emulation of K PIDs, FP64, 1 core",
+                       "dangling": ["zero columns", "uniform 1/N completion"][int(bool(args.dangling))]},
             "cpu_baseline": {"value": value, "unit": "iterations (ops/L)", "cores": 1, "kind": "oracle",
-                             "sample": "K=8 cost-balanced ranges on a web-like N=1e5 graph"},
+                             "sample": f"K=8 cost-balanced ranges on a web-like N={n_sample:.0e} graph"},
             "e2e": {"value": value, "unit": "iterations (ops/L)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
