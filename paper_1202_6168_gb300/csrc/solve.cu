@@ -315,16 +315,17 @@ __device__ __forceinline__ void scan_select(const SolveDesc *__restrict__ desc, 
     my_sel = warp_sum(my_sel);
     if (lane == 0) s_wcount[warp] = my_sel;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int total = 0;
-        for (int w = 0; w < kWarps; ++w) total += s_wcount[w];
-        s_base = total ? atomicAdd(&st->nfront, total) : -1;
-    }
-    __syncthreads();
+    int total = 0;   // the CTA's selected count, the same in every thread
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) total += s_wcount[w];
     // pass 2 (only if this CTA selected anything): the same reads, now from
-    // L2, write the selected ids in node order into the reserved slice
-    int base = s_base;
-    if (base >= 0) {
+    // L2, write the selected ids in node order into the CTA's slice.  Thread 0
+    // reserves the slice with one atomic and waits for its result only in the
+    // first chunk's serial step, so the round trip overlaps the reloads
+    if (total > 0) {
+        const int reserved = threadIdx.x == 0 ? atomicAdd(&st->nfront, total) : 0;
+        int base = 0;
+        bool first = true;
         for (int64_t c0 = (int64_t)blockIdx.x * kScanChunk; c0 < n; c0 += (int64_t)gridDim.x * kScanChunk) {
             unsigned msk[kVItems];
             int excl[kVItems];
@@ -358,8 +359,13 @@ __device__ __forceinline__ void scan_select(const SolveDesc *__restrict__ desc, 
                     run += v;
                 }
                 s_wcount[0] = run;
+                if (first) s_base = reserved;
             }
             __syncthreads();
+            if (first) {
+                base = s_base;
+                first = false;
+            }
 #pragma unroll
             for (int k = 0; k < kVItems; ++k) {
                 int pos = base + s_off[k * kWarps + warp] + excl[k];
