@@ -10,10 +10,10 @@ import pytest
 REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def reference_line(workload):
+def reference_line(workload, *extra):
     out = subprocess.run([sys.executable, os.path.join(REPO, "bench.py"), "--impl", "reference", "--workload",
-                          workload, "--steps", "1", "--warmup", "0"], cwd=REPO, capture_output=True, text=True,
-                         timeout=600)
+                          workload, "--steps", "1", "--warmup", "0", *extra], cwd=REPO, capture_output=True,
+                         text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -34,6 +34,18 @@ def test_reference_arm_prints_one_contract_line(workload):
     if workload == "web-10k":
         # the native line's headline: solves per second to the tolerance
         assert d["metric"] == "solves_per_s_to_tol" and d["unit"] == "solves/s" and d["higher_is_better"] is True
+
+
+def test_kpid_reference_with_the_completion():
+    # the oracle's K-PID emulation with completed dangling columns, on its
+    # smaller sample; the line names the completion
+    plain = reference_line("kpid-1m")
+    d = reference_line("kpid-1m", "--dangling")
+    assert d["config"]["dangling"] == "uniform 1/N completion"
+    assert plain["config"]["dangling"] == "zero columns"
+    assert "N=2e+04" in d["config"]["sample"] and "N=1e+05" in plain["config"]["sample"]
+    # a completed column counts N elementary diffusions: far above the plain cost
+    assert d["value"] > 10 * plain["value"]
 
 
 def test_warm_start_reference_uses_the_native_metric():
