@@ -230,3 +230,16 @@ def test_dangling_completion_all_dangling_and_tiny():
         h, st, _, _, _ = run(rp, col, b, 1e-13, K, dangling=1)
         assert st.status == di.DI_OK
         assert np.abs(h - x).max() <= 1e-6 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_dangling_completion_host_driven_rounds(web10k_completed, K):
+    # the same kernels launched one round at a time: the pending uniform
+    # shares survive between launches and the completed X is reached
+    rp, col, b, x = web10k_completed
+    tol = 1e-8 * b.sum()
+    h, st, ops, sends, _ = run(rp, col, b, tol, K, 1, dangling=1, timing=1)
+    assert st.status == di.DI_OK
+    assert np.abs(h - x).sum() <= 1e-6 * np.abs(x).sum()
+    check_stop_completed(rp, col, b, h, st, tol)
+    assert 0 < st.select_seconds < st.level_seconds
